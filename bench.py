@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of the GLM-MHD RK2 hot path on GB300.
+
+Workload (one GPU): 3-D Orszag-Tang vortex, 256^3 periodic, FP64, MC limiter,
+HLLD + GLM, RK2, CFL 0.8.  A bench step is one full RK2 step of the whole
+grid (ghost remap, cons->prim, PLM, GLM + HLLD, flux divergence, both RK
+stages, GLM damping, the max-wave-speed reduction and the device-side dt).
+Metric: zone-updates/s = interior cells x steps / time.  The state (1.2 GB
+per array) is far larger than L2 (129 MB), so no flush is needed between
+steps.
+
+Also reported on the same line: the FP32-bulk sweep (turbulent box 512^3),
+per-kernel CUDA-event times, roofline fractions against MEASURED_PEAKS.json,
+end-to-end throughput through the C ABI with pinned host buffers, SM clocks
+sampled during the timed region, and the CPU oracle timed on the host cores.
+
+--impl reference times the CPU FP64 oracle (there is no runnable reference
+code for this paper) on bounded samples of the same workload.
+
+N > 1 ranks (torchrun): every rank advances its own replica of the workload
+(independent problems, no data-path collective); value = all zone-updates
+over the max time across ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# FP64 operations per cell and RK stage executed by the stage kernel
+# (DADD + DMUL + 2 x DFMA, thread-level, from ncu instruction counters on the
+# 256^3 workload; see profiles/).  Used for the ALU roofline of the FP64 path.
+FP64_OPS_PER_CELL_STAGE = None
+# Nominal FP64 peak of GB300 (CUDA cores): 1.25 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.25
+# Algorithmic HBM bytes per cell: stage 1 reads U^n and writes U1 (18 words),
+# stage 2 reads U1 and U^n and writes U^{n+1} (27 words).
+WORDS_STAGE = {1: 18, 2: 27}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="edge of the FP64 OT grid")
+    ap.add_argument("--n32", type=int, default=512, help="edge of the FP32 turbulent grid")
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(self.idx), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# -------------------------------------------------------------- CPU oracle --
+def cpu_oracle_sample(target_s: float = 12.0):
+    """Times the CPU FP64 oracle (single thread, as it stands) on one RK2 step
+    of the 3-D Orszag-Tang problem at 48^3, repeated until ~target_s."""
+    import oracle as orc
+    from paper_2510_24175_gb300 import inputs
+    pb = inputs.orszag_tang_3d(48)
+    g = orc.Grid(n=pb.n, dx=pb.dx, gamma=pb.gamma, glm_alpha=pb.glm_alpha,
+                 limiter=pb.limiter, bc=pb.bc, cfl=pb.cfl)
+    U0 = orc.prim_to_cons(pb.prim(), pb.gamma)
+    reps, t = 0, 0.0
+    while t < target_s:
+        t0 = time.perf_counter()
+        orc.run(U0, g, 1)
+        t += time.perf_counter() - t0
+        reps += 1
+    return {"value": pb.ncell * reps / t, "unit": "zone-updates/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{reps} x one RK2 step of 3-D Orszag-Tang at 48^3 (FP64, MC, HLLD+GLM), "
+                      f"single thread, {t:.1f} s", "host_cores": os.cpu_count()}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as orc
+    from paper_2510_24175_gb300 import inputs
+    pb = inputs.orszag_tang_3d(48)
+    g = orc.Grid(n=pb.n, dx=pb.dx, gamma=pb.gamma, glm_alpha=pb.glm_alpha,
+                 limiter=pb.limiter, bc=pb.bc, cfl=pb.cfl)
+    U = orc.prim_to_cons(pb.prim(), pb.gamma)
+    for _ in range(args.warmup):
+        orc.run(U, g, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U = orc.run(U, g, 1).U
+    el = time.perf_counter() - t0
+    val = pb.ncell * args.steps / el
+    sample = (f"one RK2 step per bench step of 3-D Orszag-Tang at 48^3 (FP64), the 256^3 "
+              f"workload's problem at a size the single-threaded oracle finishes quickly")
+    print(json.dumps({
+        "impl": "reference", "metric": "zone-updates/s", "value": val,
+        "unit": "zone-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "orszag_tang_3d_48_cpu_oracle",
+                                        "n": [48, 48, 48]},
+        "cpu_baseline": {"value": val, "unit": "zone-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "zone-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+# ------------------------------------------------------------------- GPU --
+def timed_steps(s, torch, K, dist, world):
+    stream = torch.cuda.current_stream()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    s.profile(True)
+    s.profile_read()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        s.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = s.profile_read()
+    s.profile(False)
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    return ms, prof
+
+
+def roofline_of(prof, ncell, esize, hbm_peak, peak_kind, fp64_ops):
+    """Roofline of the stage kernel (both RK stages) from its CUDA-event times."""
+    n1, ms1 = prof["stage1"]
+    n2, ms2 = prof["stage2"]
+    avg_ms = (ms1 + ms2) / max(n1 + n2, 1)
+    bytes_launch = ncell * esize * (WORDS_STAGE[1] + WORDS_STAGE[2]) / 2.0
+    hbm = {"bound": "hbm", "achieved": bytes_launch / (avg_ms * 1e-3) / 1e9, "peak": hbm_peak,
+           "unit": "GB/s", "traffic": None, "kernel": "rk_stage_kernel",
+           "avg_launch_ms": avg_ms, "bytes_per_launch": bytes_launch,
+           "peak_source": peak_kind}
+    hbm["frac"] = hbm["achieved"] / hbm_peak
+    if fp64_ops is None:
+        return hbm, None
+    flops = ncell * fp64_ops / (avg_ms * 1e-3) / 1e12
+    alu = {"bound": "alu", "achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+           "frac": flops / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "rk_stage_kernel",
+           "avg_launch_ms": avg_ms, "fp64_ops_per_cell_stage": fp64_ops,
+           "peak_source": "nominal GB300 FP64 (CUDA cores), 152 SMs"}
+    return hbm, alu
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import paper_2510_24175_gb300 as m
+    from paper_2510_24175_gb300 import inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    K, W = args.steps, args.warmup
+    hbm_peak, peak_kind = peaks()
+
+    # ---- FP64: 3-D Orszag-Tang 256^3 ------------------------------------
+    pb = inputs.orszag_tang_3d(args.n)
+    N = pb.ncell
+    s = m.MHD(m.Config.from_problem(pb))
+    V0 = torch.from_numpy(pb.prim()).cuda()
+    s.set_state(V0, kind=m.MHD_PRIM)
+    for _ in range(W):
+        s.step()
+    s.step_info()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, prof = timed_steps(s, torch, K, dist, world)
+    clk = clocks.stop()
+    info = s.step_info()
+    value = world * N * K / (ms * 1e-3)
+    hbm, alu = roofline_of(prof, N, 8, hbm_peak, peak_kind, FP64_OPS_PER_CELL_STAGE)
+    launches = sum(c for c, _ in prof.values())
+    kernels = {k: {"launches": c, "total_ms": t, "avg_ms": (t / c if c else 0.0)}
+               for k, (c, t) in prof.items()}
+
+    # ---- end to end through the C ABI with pinned host buffers -------------
+    e2e = None
+    if not args.no_e2e:
+        U_host = torch.empty((9,) + tuple(V0.shape[1:]), dtype=torch.float64, pin_memory=True)
+        s.get_state(U_host.numpy())
+        out_host = torch.empty_like(U_host)
+        Kx = max(3, min(K, 10))
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(Kx):
+            s.set_state(U_host.numpy())
+            s.step()
+            s.get_state(out_host.numpy())
+        el = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([el], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * N * Kx / el, "unit": "zone-updates/s",
+               "h2d_bytes_per_step": int(U_host.numel() * 8),
+               "d2h_bytes_per_step": int(out_host.numel() * 8), "steps": Kx,
+               "api": "mhd_set_state(host) + mhd_step + mhd_get_state(host)"}
+    del s, V0
+    torch.cuda.empty_cache()
+
+    # ---- FP32 bulk: turbulent box 512^3 ----------------------------------
+    fp32 = None
+    if not args.no_fp32:
+        pb32 = inputs.turbulent_box(args.n32)
+        N32 = pb32.ncell
+        s32 = m.MHD(m.Config.from_problem(pb32))
+        V32 = torch.from_numpy(pb32.prim()).cuda()
+        s32.set_state(V32, kind=m.MHD_PRIM)
+        del V32
+        for _ in range(W):
+            s32.step()
+        s32.step_info()
+        ms32, prof32 = timed_steps(s32, torch, K, dist, world)
+        s32.step_info()
+        hbm32, _ = roofline_of(prof32, N32, 4, hbm_peak, peak_kind, None)
+        fp32 = {"workload": f"turbulent_box_{args.n32}^3_fp32", "value": world * N32 * K / (ms32 * 1e-3),
+                "unit": "zone-updates/s", "ms_per_step": ms32 / K, "roofline": hbm32,
+                "kernels": {k: {"launches": c, "total_ms": t} for k, (c, t) in prof32.items()},
+                "dtype": "f32 (FP64 dt reduction, sums, pressure-floor branch)"}
+        launches += sum(c for c, _ in prof32.values())
+        del s32
+        torch.cuda.empty_cache()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if not args.no_cpu and world == 1:
+        cpu = cpu_oracle_sample()
+
+    line = {
+        "metric": "zone-updates/s", "value": value, "unit": "zone-updates/s",
+        "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (closed-form Orszag-Tang initial condition)",
+        "config": {"workload": f"orszag_tang_3d_{args.n}^3_fp64", "n": list(pb.n),
+                   "limiter": "MC", "riemann": "HLLD+GLM", "time": "RK2", "cfl": pb.cfl,
+                   "l2": "state arrays (1.2 GB each) larger than L2; no flush",
+                   "parallelism": f"{world} independent replica(s)",
+                   "t_reached": info["t"]},
+        "roofline": alu if alu is not None else hbm,
+        "roofline_hbm": hbm,
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e2e": e2e,
+        "fp32": fp32,
+        "fp32_over_fp64": (fp32["value"] / value) if fp32 else None,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

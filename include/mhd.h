@@ -1,0 +1,170 @@
+/*
+ * mhd.h -- C ABI of the GB300 GLM-MHD hot path.
+ *
+ * One call of mhd_step() advances a 3-D Cartesian grid of the 9-variable
+ * ideal-MHD + GLM system by one two-stage Runge-Kutta step.  Each stage runs
+ * the five per-stage steps of the paper (Section 3.2, "Porting of gPLUTO"):
+ * boundary calculation (ghost zones), conservative->primitive map,
+ * reconstruction of interface values (PLM, minmod or MC limiter), Riemann
+ * solver (HLLD, Section 4.2) and the right-hand side of the conservation law,
+ * with divergence cleaning (GLM, Section 4.2 strong-scaling paragraph) as the
+ * div-B control.  The CFL time step is a global max-wavespeed reduction.
+ *
+ * Conventions shared by every entry point
+ *   - Variables: conservative U = (rho, mx, my, mz, Bx, By, Bz, E, psi),
+ *     primitive V = (rho, vx, vy, vz, Bx, By, Bz, p, psi);
+ *     E = p/(gamma-1) + rho|v|^2/2 + |B|^2/2 (4 pi absorbed into B).
+ *   - User arrays are interior-only SoA float64, index
+ *     [var][z][y][x] with x fastest, shape 9 x nz x ny x nx (no ghosts).
+ *   - Dimensions with n == 1 are inactive: no ghosts, no fluxes, no dt term.
+ *   - The library never allocates device memory.  The caller passes one
+ *     device workspace of mhd_workspace_bytes() bytes (256-byte aligned) that
+ *     holds the state; the library keeps no pointer to user arrays after a
+ *     call returns.
+ *   - All device work is enqueued on the context's CUDA stream and is
+ *     asynchronous, except the calls documented as synchronising.
+ *   - Return value: MHD_OK (0) or a negative MHD_ERR_* code; the context keeps
+ *     a message for mhd_last_error().  Device-side faults of the numerics
+ *     (non-finite state or time step) are recorded in a device status word and
+ *     reported as MHD_ERR_NONFINITE by the next synchronising call.  No kernel
+ *     traps.
+ */
+#ifndef MHD_H
+#define MHD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  MHD_OK = 0,
+  MHD_ERR_INVALID = -1,   /* bad argument or configuration */
+  MHD_ERR_NOMEM = -2,     /* workspace too small */
+  MHD_ERR_CUDA = -3,      /* a CUDA runtime call failed */
+  MHD_ERR_NONFINITE = -4, /* the device saw a non-finite state or time step */
+  MHD_ERR_TIMEOUT = -5,   /* a bounded device wait gave up */
+  MHD_ERR_STATE = -6      /* call out of order (e.g. step before set_state) */
+};
+
+enum { MHD_LIM_FLAT = 0, MHD_LIM_MINMOD = 1, MHD_LIM_MC = 2 };
+enum { MHD_BC_PERIODIC = 0, MHD_BC_OUTFLOW = 1 };
+/* MHD_FP64: all arithmetic in FP64.  MHD_FP32: FP32 state and stage
+ * arithmetic; FP64 for the time-step reduction result and dt, the
+ * conservation sums, and the pressure-floor branch of cons->prim. */
+enum { MHD_FP64 = 0, MHD_FP32 = 1 };
+enum { MHD_HOST = 0, MHD_DEVICE = 1 };
+enum { MHD_CONS = 0, MHD_PRIM = 1 };
+/* mhd_config.flags */
+enum { MHD_FLAG_ADJOINT = 1 };
+
+typedef struct mhd_config {
+  int n[3];              /* nx, ny, nz >= 1; active dims need n >= 2          */
+  double xmin[3], xmax[3]; /* domain; dx_d = (xmax_d - xmin_d) / n_d          */
+  double gamma;          /* adiabatic index > 1                               */
+  double cfl;            /* Courant number of the dt rule (0, 1]              */
+  double glm_alpha;      /* GLM damping: psi *= exp(-alpha c_h dt / dh_min)   */
+  double rho_floor;      /* absolute floors of cons->prim (counted)           */
+  double p_floor;
+  double t_end;          /* > 0: CFL steps are clamped to end exactly at t_end */
+  int limiter;           /* MHD_LIM_*                                         */
+  int bc[6];             /* MHD_BC_* for x-, x+, y-, y+, z-, z+ (periodic must
+                            be set on both sides of a dimension)              */
+  int precision;         /* MHD_FP64 or MHD_FP32                              */
+  int flags;             /* MHD_FLAG_* (ADJOINT reserves adjoint buffers)     */
+} mhd_config;
+
+typedef struct mhd_ctx mhd_ctx;
+
+/* Fills *cfg with defaults: gamma 5/3, cfl 0.8, glm_alpha 0.1, floors 1e-12,
+ * MC limiter, periodic BCs, FP64, unit domain, n = (1,1,1). */
+int mhd_config_default(mhd_config* cfg);
+
+/* Device workspace the context needs for cfg (bytes, before alignment). */
+int mhd_workspace_bytes(const mhd_config* cfg, size_t* bytes);
+
+/* Creates a context over the caller's device workspace (256-byte aligned,
+ * at least mhd_workspace_bytes()).  stream: a cudaStream_t (NULL = legacy
+ * default stream).  The context does not own the workspace; it must outlive
+ * the context.  Host memory for the context object is allocated here and
+ * released by mhd_destroy(). */
+int mhd_create(const mhd_config* cfg, void* d_workspace, size_t bytes, void* stream,
+               mhd_ctx** out);
+
+/* Replaces the stream later calls enqueue on. */
+int mhd_set_stream(mhd_ctx* ctx, void* stream);
+
+/* Sets the state from a float64 array U (where = MHD_HOST or MHD_DEVICE),
+ * kind = MHD_CONS (conservative) or MHD_PRIM (primitive, converted on the
+ * device).  In FP32 mode values are rounded to FP32 (primitive input from the
+ * host is rounded before the conversion).  Resets the time to 0. */
+int mhd_set_state(mhd_ctx* ctx, const double* U, int where, int kind);
+
+/* Copies the state out as float64 (conservative; kind = MHD_PRIM converts on
+ * the device and needs where = MHD_DEVICE).  where = MHD_HOST synchronises. */
+int mhd_get_state(mhd_ctx* ctx, double* U, int where, int kind);
+
+/* CFL time step of the current state (Section 3.2's explicit scheme; the rule
+ * is lambda = max over cells and active d of |v_d| + c_f,d, c_h = lambda,
+ * dt = cfl / (c_h sum_d 1/dx_d)).  Synchronises.  Either pointer may be NULL. */
+int mhd_dt(mhd_ctx* ctx, double* dt, double* ch);
+
+/* One RK2 step:  U1 = U + dt L(U);  U' = (U + U1 + dt L(U1)) / 2;  then
+ * psi' *= exp(-glm_alpha c_h dt / dh_min).  dt > 0 and ch > 0 are used as
+ * given; dt <= 0 uses the CFL rule on the device (clamped to t_end when
+ * t_end > 0); ch <= 0 uses c_h = lambda of the current state.  Does not
+ * synchronise: dt and c_h stay on the device (see mhd_step_info). */
+int mhd_step(mhd_ctx* ctx, double dt, double ch);
+
+/* out[0] = time t, out[1] = dt and out[2] = c_h of the last step,
+ * out[3] = steps taken since set_state.  Synchronises; reports
+ * MHD_ERR_NONFINITE if the device flagged a non-finite dt or state. */
+int mhd_step_info(mhd_ctx* ctx, double out[4]);
+
+/* Floor activations since set_state: counters[0] = rho floor hits,
+ * counters[1] = p floor hits; counters[2] = device status bits.
+ * Synchronises. */
+int mhd_counters(mhd_ctx* ctx, long long counters[3]);
+
+/* Conservation sums: sum over cells of (rho, mx, my, mz, E, Bx, By, Bz) times
+ * the cell volume, accumulated in FP64 in a fixed order (deterministic).
+ * Synchronises. */
+int mhd_conserved_sums(mhd_ctx* ctx, double out[8]);
+
+/* Interface flux for nface primitive face pairs along direction dir
+ * (0 = x, 1 = y, 2 = z): GLM interface step (Dedner et al. 2002) then HLLD
+ * (Miyoshi & Kusano 2005).  VL, VR, F: device arrays [9][nface] of float64
+ * (precision = MHD_FP64) or float32 (MHD_FP32).  Enqueued on stream. */
+int mhd_flux_batch(const void* VL, const void* VR, void* F, long long nface, int dir,
+                   double ch, double gamma, int precision, void* stream);
+
+/* Discrete adjoint of one RK2 step (reverse-mode derivative of mhd_step with
+ * dt and c_h frozen):  lam_n = (dU^{n+1}/dU^n)^T lam_np1.
+ * U_n: the step's input state; lam_np1, lam_n: adjoints; all device float64
+ * arrays [9][nz][ny][nx].  lam_n may not alias lam_np1.  Needs a context
+ * created with MHD_FLAG_ADJOINT and MHD_FP64.  Does not change the context's
+ * state. */
+int mhd_adjoint_step(mhd_ctx* ctx, const double* U_n, const double* lam_np1, double* lam_n,
+                     double dt, double ch);
+
+/* Per-kernel timing of the context's launches with CUDA events recorded on
+ * the context's stream (off by default; the events are created on the host
+ * when enabled).  Kernel classes: 0 = step prepare, 1 = RK stage 1,
+ * 2 = RK stage 2, 3 = max-wave-speed reduction.  mhd_profile_read()
+ * synchronises, returns the launch count and total milliseconds per class
+ * since the last read, and clears the record. */
+int mhd_profile_enable(mhd_ctx* ctx, int enable);
+int mhd_profile_read(mhd_ctx* ctx, long long counts[4], double ms[4]);
+
+/* Message of the last failing call on ctx (never NULL). */
+const char* mhd_last_error(const mhd_ctx* ctx);
+
+/* Releases the context (not the workspace). */
+int mhd_destroy(mhd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MHD_H */

@@ -1,1 +1,314 @@
-"""GB300-native GLM-MHD hot path (placeholder; binding added below)."""
+"""GB300-native GLM-MHD hot path: Python binding of the C ABI in include/mhd.h.
+
+The binding only marshals arguments: every step of the method runs in the
+CUDA kernels of ``libmhd_gb300.so`` (built in-tree by ``build.py``).  PyTorch
+provides device memory (the workspace and user tensors) and the CUDA stream.
+If the library is missing, every call raises: there is no CPU fallback.
+
+Functions with the ABI's names (``mhd_create``, ``mhd_set_state``,
+``mhd_step``, ``mhd_dt``, ``mhd_adjoint_step``, ``mhd_destroy`` ...) take the
+same arguments as the C functions (device pointers as torch tensors); the
+``MHD`` class wraps one context and owns its workspace tensor.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import inputs  # noqa: F401  (seeded input generators, no method arithmetic)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmhd_gb300.so")
+
+MHD_OK, MHD_ERR_INVALID, MHD_ERR_NOMEM, MHD_ERR_CUDA = 0, -1, -2, -3
+MHD_ERR_NONFINITE, MHD_ERR_TIMEOUT, MHD_ERR_STATE = -4, -5, -6
+MHD_LIM_FLAT, MHD_LIM_MINMOD, MHD_LIM_MC = 0, 1, 2
+MHD_BC_PERIODIC, MHD_BC_OUTFLOW = 0, 1
+MHD_FP64, MHD_FP32 = 0, 1
+MHD_HOST, MHD_DEVICE = 0, 1
+MHD_CONS, MHD_PRIM = 0, 1
+MHD_FLAG_ADJOINT = 1
+
+EXPORTED = ["mhd_config_default", "mhd_workspace_bytes", "mhd_create", "mhd_set_stream",
+            "mhd_set_state", "mhd_get_state", "mhd_dt", "mhd_step", "mhd_step_info",
+            "mhd_counters", "mhd_conserved_sums", "mhd_flux_batch", "mhd_adjoint_step",
+            "mhd_profile_enable", "mhd_profile_read", "mhd_last_error", "mhd_destroy"]
+
+
+class MHDError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"MHD error {code}: {msg}")
+        self.code = code
+
+
+class mhd_config(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("xmin", ctypes.c_double * 3),
+                ("xmax", ctypes.c_double * 3), ("gamma", ctypes.c_double),
+                ("cfl", ctypes.c_double), ("glm_alpha", ctypes.c_double),
+                ("rho_floor", ctypes.c_double), ("p_floor", ctypes.c_double),
+                ("t_end", ctypes.c_double), ("limiter", ctypes.c_int),
+                ("bc", ctypes.c_int * 6), ("precision", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"CUDA library {LIB_PATH} is missing: run paper_2510_24175_gb300/build.py "
+                "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        cfgp = ctypes.POINTER(mhd_config)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.mhd_config_default.argtypes = [cfgp]
+        L.mhd_workspace_bytes.argtypes = [cfgp, ctypes.POINTER(ctypes.c_size_t)]
+        L.mhd_create.argtypes = [cfgp, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+        L.mhd_set_stream.argtypes = [vp, vp]
+        L.mhd_set_state.argtypes = [vp, vp, i, i]
+        L.mhd_get_state.argtypes = [vp, vp, i, i]
+        L.mhd_dt.argtypes = [vp, dp, dp]
+        L.mhd_step.argtypes = [vp, d, d]
+        L.mhd_step_info.argtypes = [vp, dp]
+        L.mhd_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+        L.mhd_conserved_sums.argtypes = [vp, dp]
+        L.mhd_flux_batch.argtypes = [vp, vp, vp, ctypes.c_longlong, i, d, d, i, vp]
+        L.mhd_adjoint_step.argtypes = [vp, vp, vp, vp, d, d]
+        L.mhd_profile_enable.argtypes = [vp, i]
+        L.mhd_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), dp]
+        L.mhd_last_error.argtypes = [vp]
+        L.mhd_last_error.restype = ctypes.c_char_p
+        L.mhd_destroy.argtypes = [vp]
+        for name in EXPORTED:
+            if name != "mhd_last_error":
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, ctx=None, what: str = ""):
+    if rc != MHD_OK:
+        msg = lib().mhd_last_error(ctx).decode() if ctx else what
+        raise MHDError(rc, f"{what}: {msg}")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr():
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------ ABI functions --
+def mhd_config_default() -> mhd_config:
+    c = mhd_config()
+    _check(lib().mhd_config_default(ctypes.byref(c)), what="mhd_config_default")
+    return c
+
+
+def mhd_workspace_bytes(cfg: mhd_config) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().mhd_workspace_bytes(ctypes.byref(cfg), ctypes.byref(b)),
+           what="mhd_workspace_bytes")
+    return b.value
+
+
+def mhd_create(cfg: mhd_config, workspace, stream=None) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    s = stream if stream is not None else _stream_ptr()
+    _check(lib().mhd_create(ctypes.byref(cfg), _ptr(workspace), workspace.numel(), s,
+                            ctypes.byref(ctx)), what="mhd_create")
+    return ctx
+
+
+def mhd_set_state(ctx, U, where=MHD_DEVICE, kind=MHD_CONS):
+    p = _ptr(U) if where == MHD_DEVICE else U.ctypes.data_as(ctypes.c_void_p)
+    _check(lib().mhd_set_state(ctx, p, where, kind), ctx, "mhd_set_state")
+
+
+def mhd_get_state(ctx, U, where=MHD_DEVICE, kind=MHD_CONS):
+    p = _ptr(U) if where == MHD_DEVICE else U.ctypes.data_as(ctypes.c_void_p)
+    _check(lib().mhd_get_state(ctx, p, where, kind), ctx, "mhd_get_state")
+
+
+def mhd_dt(ctx):
+    dt, ch = ctypes.c_double(), ctypes.c_double()
+    _check(lib().mhd_dt(ctx, ctypes.byref(dt), ctypes.byref(ch)), ctx, "mhd_dt")
+    return dt.value, ch.value
+
+
+def mhd_step(ctx, dt: float = 0.0, ch: float = 0.0):
+    _check(lib().mhd_step(ctx, float(dt), float(ch)), ctx, "mhd_step")
+
+
+def mhd_adjoint_step(ctx, U_n, lam_np1, lam_n, dt: float, ch: float):
+    _check(lib().mhd_adjoint_step(ctx, _ptr(U_n), _ptr(lam_np1), _ptr(lam_n), float(dt),
+                                  float(ch)), ctx, "mhd_adjoint_step")
+
+
+def mhd_destroy(ctx):
+    _check(lib().mhd_destroy(ctx), what="mhd_destroy")
+
+
+def mhd_flux_batch(VL, VR, F, direction: int, ch: float, gamma: float):
+    """GLM + HLLD fluxes of face pairs; VL, VR, F: CUDA tensors (9, nface),
+    float64 or float32."""
+    torch = _torch()
+    prec = MHD_FP64 if VL.dtype == torch.float64 else MHD_FP32
+    for t in (VL, VR, F):
+        assert t.is_cuda and t.is_contiguous() and t.shape[0] == 9 and t.dtype == VL.dtype
+    _check(lib().mhd_flux_batch(_ptr(VL), _ptr(VR), _ptr(F), VL.shape[1], direction, ch, gamma,
+                                prec, _stream_ptr()), what="mhd_flux_batch")
+
+
+# ----------------------------------------------------------------- wrapper --
+@dataclass
+class Config:
+    n: tuple
+    xmin: tuple = (0.0, 0.0, 0.0)
+    xmax: tuple = (1.0, 1.0, 1.0)
+    gamma: float = 5.0 / 3.0
+    cfl: float = 0.8
+    glm_alpha: float = 0.1
+    rho_floor: float = 1e-12
+    p_floor: float = 1e-12
+    t_end: float = 0.0
+    limiter: int = MHD_LIM_MC
+    bc: tuple = (MHD_BC_PERIODIC,) * 6
+    precision: int = MHD_FP64
+    flags: int = 0
+
+    @classmethod
+    def from_problem(cls, pb, precision=None, flags: int = 0) -> "Config":
+        return cls(n=tuple(pb.n), xmin=tuple(pb.xmin), xmax=tuple(pb.xmax), gamma=pb.gamma,
+                   cfl=pb.cfl, glm_alpha=pb.glm_alpha, rho_floor=pb.rho_floor,
+                   p_floor=pb.p_floor, t_end=pb.t_end, limiter=pb.limiter, bc=tuple(pb.bc),
+                   precision=pb.precision if precision is None else precision, flags=flags)
+
+    def c(self) -> mhd_config:
+        c = mhd_config()
+        for d in range(3):
+            c.n[d] = int(self.n[d])
+            c.xmin[d] = float(self.xmin[d])
+            c.xmax[d] = float(self.xmax[d])
+        c.gamma, c.cfl, c.glm_alpha = self.gamma, self.cfl, self.glm_alpha
+        c.rho_floor, c.p_floor, c.t_end = self.rho_floor, self.p_floor, self.t_end
+        c.limiter, c.precision, c.flags = int(self.limiter), int(self.precision), int(self.flags)
+        for s in range(6):
+            c.bc[s] = int(self.bc[s])
+        return c
+
+
+class MHD:
+    """One solver context on the current CUDA device and stream."""
+
+    def __init__(self, config: Config, stream=None):
+        torch = _torch()
+        self.config = config
+        self._c = config.c()
+        nbytes = mhd_workspace_bytes(self._c)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        off = (-self.workspace.data_ptr()) % 256
+        self._ws = self.workspace[off:off + nbytes]
+        s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else _stream_ptr()
+        self.ctx = ctypes.c_void_p()
+        _check(lib().mhd_create(ctypes.byref(self._c), _ptr(self._ws), nbytes, s,
+                                ctypes.byref(self.ctx)), what="mhd_create")
+        nx, ny, nz = config.n
+        self.shape = (9, nz, ny, nx)
+
+    def __del__(self):
+        try:
+            if getattr(self, "ctx", None) and self.ctx.value:
+                lib().mhd_destroy(self.ctx)
+                self.ctx = None
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        _check(lib().mhd_set_stream(self.ctx, ctypes.c_void_p(stream.cuda_stream)), self.ctx,
+               "mhd_set_stream")
+
+    def set_state(self, U, kind=MHD_CONS):
+        """U: float64 CUDA tensor or numpy array of shape (9, nz, ny, nx)."""
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.float64)
+            assert U.shape == self.shape
+            mhd_set_state(self.ctx, U, MHD_HOST, kind)
+        else:
+            torch = _torch()
+            assert U.is_cuda and U.dtype == torch.float64 and U.is_contiguous()
+            assert tuple(U.shape) == self.shape
+            mhd_set_state(self.ctx, U, MHD_DEVICE, kind)
+
+    def get_state(self, out=None, kind=MHD_CONS):
+        """Returns the state as a float64 CUDA tensor (or fills ``out``; a
+        numpy ``out`` receives a host copy)."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        if isinstance(out, np.ndarray):
+            mhd_get_state(self.ctx, out, MHD_HOST, kind)
+        else:
+            mhd_get_state(self.ctx, out, MHD_DEVICE, kind)
+        return out
+
+    def dt(self):
+        return mhd_dt(self.ctx)
+
+    def step(self, dt: float = 0.0, ch: float = 0.0):
+        mhd_step(self.ctx, dt, ch)
+
+    def step_info(self):
+        out = (ctypes.c_double * 4)()
+        _check(lib().mhd_step_info(self.ctx, out), self.ctx, "mhd_step_info")
+        return {"t": out[0], "dt": out[1], "ch": out[2], "steps": int(out[3])}
+
+    def counters(self):
+        out = (ctypes.c_longlong * 3)()
+        _check(lib().mhd_counters(self.ctx, out), self.ctx, "mhd_counters")
+        return {"rho_floor": out[0], "p_floor": out[1], "status": out[2]}
+
+    def conserved_sums(self) -> np.ndarray:
+        out = (ctypes.c_double * 8)()
+        _check(lib().mhd_conserved_sums(self.ctx, out), self.ctx, "mhd_conserved_sums")
+        return np.array(out[:])
+
+    def profile(self, enable: bool = True):
+        _check(lib().mhd_profile_enable(self.ctx, int(enable)), self.ctx, "mhd_profile_enable")
+
+    def profile_read(self):
+        """{kernel class: (launches, total ms)} since the last read."""
+        cnt = (ctypes.c_longlong * 4)()
+        ms = (ctypes.c_double * 4)()
+        _check(lib().mhd_profile_read(self.ctx, cnt, ms), self.ctx, "mhd_profile_read")
+        names = ("prep", "stage1", "stage2", "max_speed")
+        return {names[k]: (int(cnt[k]), float(ms[k])) for k in range(4)}
+
+    def adjoint_step(self, U_n, lam_np1, lam_n, dt: float, ch: float):
+        mhd_adjoint_step(self.ctx, U_n, lam_np1, lam_n, dt, ch)
+
+    def run(self, nsteps: int, t_end: float = 0.0):
+        """Advances up to nsteps CFL steps (stopping at t_end when the config
+        sets one); returns the step info."""
+        for _ in range(nsteps):
+            self.step()
+            if t_end > 0.0:
+                info = self.step_info()
+                if info["t"] >= t_end:
+                    break
+        return self.step_info()

@@ -1,0 +1,598 @@
+// C ABI of the GLM-MHD hot path (declared in include/mhd.h).  Host code only:
+// validates arguments, carves the caller's workspace, and enqueues the
+// kernels of mhd_aux.cu / mhd_stage_*.cu / mhd_adjoint.cu on the context's
+// stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/mhd.h"
+#include "mhd_internal.h"
+
+namespace {
+
+constexpr int kSumBlocks = 1024;
+
+struct Scalars {  // device block at the start of the scalar region
+  mhd::StepScalars sc;
+  unsigned long long lam_bits;
+  unsigned long long floor_cnt[2];
+  unsigned int status;
+  unsigned int pad;
+  double sums[8];
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct mhd_ctx {
+  mhd_config cfg;
+  mhd::Grid grid;
+  size_t esize;          // bytes per state element (8 or 4)
+  size_t state_bytes;    // 9 * ncell * esize
+  char* ws;
+  size_t ws_bytes;
+  void* Ua;              // U^n (and U^{n+1}, in place)
+  void* Ub;              // U1 / staging
+  Scalars* scal;
+  double* partials;
+  void* adj;             // adjoint scratch (MHD_FLAG_ADJOINT)
+  size_t adj_bytes;
+  cudaStream_t stream;
+  bool have_state;
+  bool lam_valid;
+  double inv_dx_sum, dh_min;
+  // CUDA-event timing (mhd_profile_enable)
+  bool prof_on;
+  struct Rec { cudaEvent_t a, b; int kind; };
+  std::vector<Rec> prof_recs;
+  std::vector<cudaEvent_t> prof_pool;
+  char err[512];
+};
+
+static cudaEvent_t prof_event(mhd_ctx* c) {
+  if (!c->prof_pool.empty()) {
+    cudaEvent_t e = c->prof_pool.back();
+    c->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Brackets one launch with events when profiling is on.
+struct ProfScope {
+  mhd_ctx* c;
+  cudaEvent_t a = nullptr, b = nullptr;
+  int kind;
+  ProfScope(mhd_ctx* ctx, int k) : c(ctx), kind(k) {
+    if (!c->prof_on) return;
+    a = prof_event(c);
+    b = prof_event(c);
+    if (a) cudaEventRecord(a, c->stream);
+  }
+  ~ProfScope() {
+    if (!c->prof_on || !a || !b) return;
+    cudaEventRecord(b, c->stream);
+    c->prof_recs.push_back({a, b, kind});
+  }
+};
+
+static int fail(mhd_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CK(ctx, call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail((ctx), MHD_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+static int validate(const mhd_config* c, char* msg, size_t len) {
+  if (!c) {
+    snprintf(msg, len, "null config");
+    return MHD_ERR_INVALID;
+  }
+  for (int d = 0; d < 3; ++d) {
+    if (c->n[d] < 1) {
+      snprintf(msg, len, "n[%d] = %d < 1", d, c->n[d]);
+      return MHD_ERR_INVALID;
+    }
+    if (!(c->xmax[d] > c->xmin[d])) {
+      snprintf(msg, len, "empty domain in dimension %d", d);
+      return MHD_ERR_INVALID;
+    }
+  }
+  if (c->n[0] < 2) {
+    snprintf(msg, len, "x must be active (nx >= 2)");
+    return MHD_ERR_INVALID;
+  }
+  if (c->n[2] > 1 && c->n[1] < 2) {
+    snprintf(msg, len, "inactive dimensions must be trailing (ny = 1 needs nz = 1)");
+    return MHD_ERR_INVALID;
+  }
+  if ((long long)c->n[0] * c->n[1] * c->n[2] > (1ll << 34)) {
+    snprintf(msg, len, "grid too large");
+    return MHD_ERR_INVALID;
+  }
+  if (!(c->gamma > 1.0) || !(c->cfl > 0.0 && c->cfl <= 1.0) || !(c->glm_alpha >= 0.0) ||
+      !(c->rho_floor >= 0.0) || !(c->p_floor >= 0.0) || !(c->t_end >= 0.0)) {
+    snprintf(msg, len, "bad physics constant (gamma > 1, 0 < cfl <= 1, alpha/floors >= 0)");
+    return MHD_ERR_INVALID;
+  }
+  if (c->limiter < MHD_LIM_FLAT || c->limiter > MHD_LIM_MC) {
+    snprintf(msg, len, "bad limiter %d", c->limiter);
+    return MHD_ERR_INVALID;
+  }
+  for (int d = 0; d < 3; ++d) {
+    const int lo = c->bc[2 * d], hi = c->bc[2 * d + 1];
+    if ((lo != MHD_BC_PERIODIC && lo != MHD_BC_OUTFLOW) ||
+        (hi != MHD_BC_PERIODIC && hi != MHD_BC_OUTFLOW) ||
+        ((lo == MHD_BC_PERIODIC) != (hi == MHD_BC_PERIODIC))) {
+      snprintf(msg, len, "bad boundary conditions in dimension %d", d);
+      return MHD_ERR_INVALID;
+    }
+  }
+  if (c->precision != MHD_FP64 && c->precision != MHD_FP32) {
+    snprintf(msg, len, "bad precision %d", c->precision);
+    return MHD_ERR_INVALID;
+  }
+  if ((c->flags & MHD_FLAG_ADJOINT) && c->precision != MHD_FP64) {
+    snprintf(msg, len, "the adjoint needs MHD_FP64");
+    return MHD_ERR_INVALID;
+  }
+  return MHD_OK;
+}
+
+// Adjoint scratch bytes (mhd_adjoint.cu).
+namespace mhd {
+size_t adjoint_scratch_bytes(const Grid& g);
+int adjoint_step(const Grid& g, double dt, double ch, double glm_alpha, double dh_min,
+                 const double* U_n, const double* lam_np1, double* lam_n, void* scratch,
+                 size_t scratch_bytes, cudaStream_t stream, char* err, size_t errlen);
+}  // namespace mhd
+
+static void fill_grid(const mhd_config* c, mhd::Grid* g) {
+  memset(g, 0, sizeof(*g));
+  g->ndim = 0;
+  g->ncell = 1;
+  for (int d = 0; d < 3; ++d) {
+    g->n[d] = c->n[d];
+    g->ncell *= c->n[d];
+    g->dx[d] = (c->xmax[d] - c->xmin[d]) / c->n[d];
+    g->bc_lo[d] = c->bc[2 * d];
+    g->bc_hi[d] = c->bc[2 * d + 1];
+    if (c->n[d] > 1) g->ndim++;
+  }
+  g->limiter = c->limiter;
+  g->gamma = c->gamma;
+  g->rho_floor = c->rho_floor;
+  g->p_floor = c->p_floor;
+}
+
+// z planes per CTA: minimise (waves of CTAs) x (planes + prologue weight).
+static int choose_tz(const mhd::Grid& g, int ctas_per_sm, int ty) {
+  if (g.ndim < 3) return 1;
+  const long long cols = (long long)((g.n[0] + 31) / 32) * ((g.n[1] + ty - 1) / ty);
+  const long long slots = (long long)g.nsm * ctas_per_sm;
+  int best = g.n[2];
+  double best_cost = 1e300;
+  const int cands[] = {4, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256};
+  for (int tz : cands) {
+    if (tz > g.n[2] && tz != cands[0]) continue;
+    const long long ctas = cols * ((g.n[2] + tz - 1) / tz);
+    const long long waves = (ctas + slots - 1) / slots;
+    const double cost = (double)waves * (tz + 1.0);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = tz;
+    }
+  }
+  return best;
+}
+
+extern "C" {
+
+int mhd_config_default(mhd_config* cfg) {
+  if (!cfg) return MHD_ERR_INVALID;
+  memset(cfg, 0, sizeof(*cfg));
+  for (int d = 0; d < 3; ++d) {
+    cfg->n[d] = 1;
+    cfg->xmin[d] = 0.0;
+    cfg->xmax[d] = 1.0;
+  }
+  cfg->gamma = 5.0 / 3.0;
+  cfg->cfl = 0.8;
+  cfg->glm_alpha = 0.1;
+  cfg->rho_floor = 1e-12;
+  cfg->p_floor = 1e-12;
+  cfg->t_end = 0.0;
+  cfg->limiter = MHD_LIM_MC;
+  for (int s = 0; s < 6; ++s) cfg->bc[s] = MHD_BC_PERIODIC;
+  cfg->precision = MHD_FP64;
+  cfg->flags = 0;
+  return MHD_OK;
+}
+
+int mhd_workspace_bytes(const mhd_config* cfg, size_t* bytes) {
+  char msg[256];
+  int rc = validate(cfg, msg, sizeof(msg));
+  if (rc != MHD_OK || !bytes) return MHD_ERR_INVALID;
+  mhd::Grid g;
+  fill_grid(cfg, &g);
+  const size_t es = cfg->precision == MHD_FP64 ? 8 : 4;
+  const size_t state = align256((size_t)9 * g.ncell * es);
+  size_t total = 2 * state + align256(sizeof(Scalars)) + align256(kSumBlocks * 8 * sizeof(double));
+  if (cfg->flags & MHD_FLAG_ADJOINT) total += align256(mhd::adjoint_scratch_bytes(g));
+  *bytes = total;
+  return MHD_OK;
+}
+
+int mhd_create(const mhd_config* cfg, void* d_workspace, size_t bytes, void* stream,
+               mhd_ctx** out) {
+  if (!out) return MHD_ERR_INVALID;
+  *out = nullptr;
+  char msg[256] = "";
+  int rc = validate(cfg, msg, sizeof(msg));
+  if (rc != MHD_OK) {
+    fprintf(stderr, "mhd_create: %s\n", msg);
+    return rc;
+  }
+  size_t need = 0;
+  mhd_workspace_bytes(cfg, &need);
+  if (!d_workspace || bytes < need || ((uintptr_t)d_workspace & 255)) {
+    fprintf(stderr, "mhd_create: workspace %p of %zu bytes (need %zu, 256-byte aligned)\n",
+            d_workspace, bytes, need);
+    return MHD_ERR_NOMEM;
+  }
+  mhd_ctx* c = new (std::nothrow) mhd_ctx();
+  if (!c) return MHD_ERR_NOMEM;
+  c->cfg = *cfg;
+  fill_grid(cfg, &c->grid);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      nsm <= 0) {
+    delete c;
+    return MHD_ERR_CUDA;
+  }
+  c->grid.nsm = nsm;
+  c->esize = cfg->precision == MHD_FP64 ? 8 : 4;
+  c->state_bytes = (size_t)9 * c->grid.ncell * c->esize;
+  c->ws = static_cast<char*>(d_workspace);
+  c->ws_bytes = bytes;
+  size_t off = 0;
+  c->Ua = c->ws + off;
+  off += align256(c->state_bytes);
+  c->Ub = c->ws + off;
+  off += align256(c->state_bytes);
+  c->scal = reinterpret_cast<Scalars*>(c->ws + off);
+  off += align256(sizeof(Scalars));
+  c->partials = reinterpret_cast<double*>(c->ws + off);
+  off += align256(kSumBlocks * 8 * sizeof(double));
+  c->adj = nullptr;
+  c->adj_bytes = 0;
+  if (cfg->flags & MHD_FLAG_ADJOINT) {
+    c->adj = c->ws + off;
+    c->adj_bytes = mhd::adjoint_scratch_bytes(c->grid);
+    off += align256(c->adj_bytes);
+  }
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->inv_dx_sum = 0.0;
+  c->dh_min = 1e300;
+  for (int d = 0; d < 3; ++d)
+    if (c->grid.n[d] > 1) {
+      c->inv_dx_sum += 1.0 / c->grid.dx[d];
+      c->dh_min = fmin(c->dh_min, c->grid.dx[d]);
+    }
+  size_t smem;
+  int threads, ty;
+  if (c->esize == 8)
+    mhd::stage_shape<double>(c->grid, &smem, &threads, &ty);
+  else
+    mhd::stage_shape<float>(c->grid, &smem, &threads, &ty);
+  const int per_sm = (int)(228 * 1024 / (smem + 1024));
+  c->grid.tz = choose_tz(c->grid, per_sm < 1 ? 1 : per_sm, ty);
+  c->have_state = false;
+  c->lam_valid = false;
+  snprintf(c->err, sizeof(c->err), "no error");
+  cudaError_t e = cudaMemsetAsync(c->scal, 0, sizeof(Scalars), c->stream);
+  if (e != cudaSuccess) {
+    delete c;
+    return MHD_ERR_CUDA;
+  }
+  *out = c;
+  return MHD_OK;
+}
+
+int mhd_set_stream(mhd_ctx* c, void* stream) {
+  if (!c) return MHD_ERR_INVALID;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return MHD_OK;
+}
+
+int mhd_set_state(mhd_ctx* c, const double* U, int where, int kind) {
+  if (!c) return MHD_ERR_INVALID;
+  if (!U || (where != MHD_HOST && where != MHD_DEVICE) ||
+      (kind != MHD_CONS && kind != MHD_PRIM))
+    return fail(c, MHD_ERR_INVALID, "mhd_set_state: bad argument");
+  const long long n = 9 * c->grid.ncell;
+  const cudaMemcpyKind mk = where == MHD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (c->esize == 8) {
+    double* A = static_cast<double*>(c->Ua);
+    if (kind == MHD_CONS) {
+      CK(c, cudaMemcpyAsync(A, U, n * 8, mk, c->stream));
+    } else {
+      const double* src = U;
+      if (where == MHD_HOST) {
+        CK(c, cudaMemcpyAsync(c->Ub, U, n * 8, mk, c->stream));
+        src = static_cast<const double*>(c->Ub);
+      }
+      CK(c, mhd::launch_prim_to_cons<double>(c->grid, src, A, c->stream));
+    }
+  } else {
+    float* A = static_cast<float*>(c->Ua);
+    if (where == MHD_DEVICE) {
+      if (kind == MHD_CONS)
+        CK(c, mhd::launch_f64_to_f32(U, A, n, c->stream));
+      else
+        CK(c, mhd::launch_prim_to_cons<float>(c->grid, U, A, c->stream));
+    } else {
+      // stage FP64 host data through Ub (half the FP64 bytes) in chunks
+      const long long chunk = (long long)(c->state_bytes / 8);
+      double* B = static_cast<double*>(c->Ub);
+      for (long long o = 0; o < n; o += chunk) {
+        const long long m = n - o < chunk ? n - o : chunk;
+        CK(c, cudaMemcpyAsync(B, U + o, m * 8, cudaMemcpyHostToDevice, c->stream));
+        CK(c, mhd::launch_f64_to_f32(B, A + o, m, c->stream));
+      }
+      if (kind == MHD_PRIM) CK(c, mhd::launch_prim_to_cons_inplace<float>(c->grid, A, c->stream));
+    }
+  }
+  CK(c, cudaMemsetAsync(c->scal, 0, sizeof(Scalars), c->stream));
+  c->have_state = true;
+  c->lam_valid = false;
+  return MHD_OK;
+}
+
+int mhd_get_state(mhd_ctx* c, double* U, int where, int kind) {
+  if (!c) return MHD_ERR_INVALID;
+  if (!U || (where != MHD_HOST && where != MHD_DEVICE) ||
+      (kind != MHD_CONS && kind != MHD_PRIM) || (kind == MHD_PRIM && where != MHD_DEVICE))
+    return fail(c, MHD_ERR_INVALID, "mhd_get_state: bad argument");
+  if (!c->have_state) return fail(c, MHD_ERR_STATE, "mhd_get_state before mhd_set_state");
+  const long long n = 9 * c->grid.ncell;
+  if (kind == MHD_PRIM) {
+    if (c->esize == 8)
+      CK(c, mhd::launch_cons_to_prim<double>(c->grid, static_cast<const double*>(c->Ua), U,
+                                             c->stream));
+    else
+      CK(c, mhd::launch_cons_to_prim<float>(c->grid, static_cast<const float*>(c->Ua), U,
+                                            c->stream));
+    return MHD_OK;
+  }
+  if (c->esize == 8) {
+    CK(c, cudaMemcpyAsync(U, c->Ua, n * 8,
+                          where == MHD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                          c->stream));
+  } else if (where == MHD_DEVICE) {
+    CK(c, mhd::launch_f32_to_f64(static_cast<const float*>(c->Ua), U, n, c->stream));
+  } else {
+    const long long chunk = (long long)(c->state_bytes / 8);
+    double* B = static_cast<double*>(c->Ub);
+    const float* A = static_cast<const float*>(c->Ua);
+    for (long long o = 0; o < n; o += chunk) {
+      const long long m = n - o < chunk ? n - o : chunk;
+      CK(c, mhd::launch_f32_to_f64(A + o, B, m, c->stream));
+      CK(c, cudaMemcpyAsync(U + o, B, m * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+  }
+  if (where == MHD_HOST) CK(c, cudaStreamSynchronize(c->stream));
+  return MHD_OK;
+}
+
+static int ensure_lambda(mhd_ctx* c) {
+  if (c->lam_valid) return MHD_OK;
+  ProfScope ps(c, 3);
+  if (c->esize == 8)
+    CK(c, mhd::launch_max_speed<double>(c->grid, static_cast<const double*>(c->Ua),
+                                        &c->scal->lam_bits, c->scal->floor_cnt, c->stream));
+  else
+    CK(c, mhd::launch_max_speed<float>(c->grid, static_cast<const float*>(c->Ua),
+                                       &c->scal->lam_bits, c->scal->floor_cnt, c->stream));
+  c->lam_valid = true;
+  return MHD_OK;
+}
+
+int mhd_dt(mhd_ctx* c, double* dt, double* ch) {
+  if (!c) return MHD_ERR_INVALID;
+  if (!c->have_state) return fail(c, MHD_ERR_STATE, "mhd_dt before mhd_set_state");
+  int rc = ensure_lambda(c);
+  if (rc != MHD_OK) return rc;
+  unsigned long long bits = 0;
+  CK(c, cudaMemcpyAsync(&bits, &c->scal->lam_bits, sizeof(bits), cudaMemcpyDeviceToHost,
+                        c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  double lam;
+  memcpy(&lam, &bits, sizeof(lam));
+  if (!(lam > 0.0) || !std::isfinite(lam))
+    return fail(c, MHD_ERR_NONFINITE, "max wave speed is %g", lam);
+  if (ch) *ch = lam;
+  if (dt) *dt = c->cfg.cfl / (lam * c->inv_dx_sum);
+  return MHD_OK;
+}
+
+int mhd_step(mhd_ctx* c, double dt, double ch) {
+  if (!c) return MHD_ERR_INVALID;
+  if (!c->have_state) return fail(c, MHD_ERR_STATE, "mhd_step before mhd_set_state");
+  if (std::isnan(dt) || std::isnan(ch) || std::isinf(dt) || std::isinf(ch))
+    return fail(c, MHD_ERR_INVALID, "mhd_step: non-finite dt or ch");
+  if (!(dt > 0.0) || !(ch > 0.0)) {
+    int rc = ensure_lambda(c);
+    if (rc != MHD_OK) return rc;
+  }
+  mhd::PrepArgs a;
+  a.dt_req = dt;
+  a.ch_req = ch;
+  a.cfl = c->cfg.cfl;
+  a.inv_dx_sum = c->inv_dx_sum;
+  a.t_end = c->cfg.t_end;
+  a.glm_alpha = c->cfg.glm_alpha;
+  a.dh_min = c->dh_min;
+  for (int d = 0; d < 3; ++d) {
+    a.dx[d] = c->grid.dx[d];
+    a.active[d] = c->grid.n[d] > 1;
+  }
+  {
+    ProfScope ps(c, 0);
+    CK(c, mhd::launch_prep(a, &c->scal->sc, &c->scal->lam_bits, &c->scal->status, c->stream));
+  }
+  for (int stage = 1; stage <= 2; ++stage) {
+    ProfScope ps(c, stage);
+    if (c->esize == 8) {
+      double* A = static_cast<double*>(c->Ua);
+      double* B = static_cast<double*>(c->Ub);
+      CK(c, mhd::launch_stage<double>(c->grid, stage, stage == 1 ? A : B,
+                                      stage == 1 ? nullptr : A, stage == 1 ? B : A,
+                                      &c->scal->sc, &c->scal->lam_bits, c->scal->floor_cnt,
+                                      c->stream));
+    } else {
+      float* A = static_cast<float*>(c->Ua);
+      float* B = static_cast<float*>(c->Ub);
+      CK(c, mhd::launch_stage<float>(c->grid, stage, stage == 1 ? A : B,
+                                     stage == 1 ? nullptr : A, stage == 1 ? B : A,
+                                     &c->scal->sc, &c->scal->lam_bits, c->scal->floor_cnt,
+                                     c->stream));
+    }
+  }
+  c->lam_valid = true;
+  return MHD_OK;
+}
+
+int mhd_step_info(mhd_ctx* c, double out[4]) {
+  if (!c || !out) return MHD_ERR_INVALID;
+  Scalars h;
+  CK(c, cudaMemcpyAsync(&h, c->scal, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  out[0] = h.sc.t;
+  out[1] = h.sc.dt;
+  out[2] = h.sc.ch;
+  out[3] = h.sc.steps;
+  if (h.status) return fail(c, MHD_ERR_NONFINITE, "device flagged a non-finite dt or c_h");
+  double lam;
+  memcpy(&lam, &h.lam_bits, sizeof(lam));
+  if (c->lam_valid && std::isnan(lam))
+    return fail(c, MHD_ERR_NONFINITE, "non-finite state after the last step");
+  return MHD_OK;
+}
+
+int mhd_counters(mhd_ctx* c, long long counters[3]) {
+  if (!c || !counters) return MHD_ERR_INVALID;
+  Scalars h;
+  CK(c, cudaMemcpyAsync(&h, c->scal, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  counters[0] = (long long)h.floor_cnt[0];
+  counters[1] = (long long)h.floor_cnt[1];
+  counters[2] = (long long)h.status;
+  return MHD_OK;
+}
+
+int mhd_conserved_sums(mhd_ctx* c, double out[8]) {
+  if (!c || !out) return MHD_ERR_INVALID;
+  if (!c->have_state) return fail(c, MHD_ERR_STATE, "mhd_conserved_sums before mhd_set_state");
+  if (c->esize == 8)
+    CK(c, mhd::launch_sums<double>(c->grid, static_cast<const double*>(c->Ua), c->partials,
+                                   kSumBlocks, c->scal->sums, c->stream));
+  else
+    CK(c, mhd::launch_sums<float>(c->grid, static_cast<const float*>(c->Ua), c->partials,
+                                  kSumBlocks, c->scal->sums, c->stream));
+  CK(c, cudaMemcpyAsync(out, c->scal->sums, 8 * sizeof(double), cudaMemcpyDeviceToHost,
+                        c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return MHD_OK;
+}
+
+int mhd_flux_batch(const void* VL, const void* VR, void* F, long long nface, int dir, double ch,
+                   double gamma, int precision, void* stream) {
+  if (!VL || !VR || !F || nface < 0 || dir < 0 || dir > 2 || !(ch > 0.0) || !(gamma > 1.0) ||
+      (precision != MHD_FP64 && precision != MHD_FP32))
+    return MHD_ERR_INVALID;
+  if (nface == 0) return MHD_OK;
+  cudaError_t e;
+  if (precision == MHD_FP64)
+    e = mhd::launch_flux_batch<double>(static_cast<const double*>(VL),
+                                       static_cast<const double*>(VR), static_cast<double*>(F),
+                                       nface, dir, ch, gamma, static_cast<cudaStream_t>(stream));
+  else
+    e = mhd::launch_flux_batch<float>(static_cast<const float*>(VL),
+                                      static_cast<const float*>(VR), static_cast<float*>(F),
+                                      nface, dir, ch, gamma, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? MHD_OK : MHD_ERR_CUDA;
+}
+
+int mhd_adjoint_step(mhd_ctx* c, const double* U_n, const double* lam_np1, double* lam_n,
+                     double dt, double ch) {
+  if (!c) return MHD_ERR_INVALID;
+  if (!(c->cfg.flags & MHD_FLAG_ADJOINT) || c->esize != 8)
+    return fail(c, MHD_ERR_STATE, "context created without MHD_FLAG_ADJOINT / MHD_FP64");
+  if (!U_n || !lam_np1 || !lam_n || lam_n == lam_np1 || !(dt > 0.0) || !(ch > 0.0) ||
+      !std::isfinite(dt) || !std::isfinite(ch))
+    return fail(c, MHD_ERR_INVALID, "mhd_adjoint_step: bad argument");
+  return mhd::adjoint_step(c->grid, dt, ch, c->cfg.glm_alpha, c->dh_min, U_n, lam_np1, lam_n,
+                           c->adj, c->adj_bytes, c->stream, c->err, sizeof(c->err));
+}
+
+int mhd_profile_enable(mhd_ctx* c, int enable) {
+  if (!c) return MHD_ERR_INVALID;
+  c->prof_on = enable != 0;
+  return MHD_OK;
+}
+
+int mhd_profile_read(mhd_ctx* c, long long counts[4], double ms[4]) {
+  if (!c || !counts || !ms) return MHD_ERR_INVALID;
+  for (int k = 0; k < 4; ++k) {
+    counts[k] = 0;
+    ms[k] = 0.0;
+  }
+  CK(c, cudaStreamSynchronize(c->stream));
+  for (auto& r : c->prof_recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+      counts[r.kind] += 1;
+      ms[r.kind] += t;
+    }
+    c->prof_pool.push_back(r.a);
+    c->prof_pool.push_back(r.b);
+  }
+  c->prof_recs.clear();
+  return MHD_OK;
+}
+
+const char* mhd_last_error(const mhd_ctx* c) { return c ? c->err : "null context"; }
+
+int mhd_destroy(mhd_ctx* c) {
+  if (!c) return MHD_ERR_INVALID;
+  for (auto& r : c->prof_recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->prof_pool) cudaEventDestroy(e);
+  delete c;
+  return MHD_OK;
+}
+
+}  // extern "C"

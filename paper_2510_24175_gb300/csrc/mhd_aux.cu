@@ -1,0 +1,310 @@
+// Auxiliary kernels of the hot path: the per-step prepare kernel (CFL time
+// step from the reduced max wave speed, GLM c_h and damping factor), the
+// max-wave-speed reduction, deterministic FP64 conservation sums, state
+// conversions and the batched interface-flux kernel.
+#include "mhd_internal.h"
+
+namespace mhd {
+
+template <class T>
+Phys<T> make_phys(const Grid& g) {
+  Phys<T> ph;
+  ph.gamma = T(g.gamma);
+  ph.gm1 = T(g.gamma - 1.0);
+  ph.gm1i = T(1.0 / (g.gamma - 1.0));
+  ph.rho_floor = T(g.rho_floor);
+  ph.p_floor = T(g.p_floor);
+  ph.gamma_d = g.gamma;
+  ph.rho_floor_d = g.rho_floor;
+  ph.p_floor_d = g.p_floor;
+  return ph;
+}
+template Phys<double> make_phys<double>(const Grid&);
+template Phys<float> make_phys<float>(const Grid&);
+
+// ---------------------------------------------------------------- prepare --
+// One thread.  dt rule: c_h = lambda (max |v_d| + c_f,d of the state),
+// dt = cfl / (c_h sum_active 1/dx_d), clamped so the step ends at t_end.
+// A non-finite or non-positive dt / c_h sets status bit 1 and turns the step
+// into a no-op (dt = 0, damping 1), so the state is preserved for inspection.
+__global__ void prep_kernel(const PrepArgs a, StepScalars* sc, unsigned long long* lam_bits,
+                            unsigned int* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double lam = __longlong_as_double((long long)*lam_bits);
+  double ch = a.ch_req > 0.0 ? a.ch_req : lam;
+  double dt = a.dt_req;
+  const double t = sc->t;
+  if (!(dt > 0.0)) {
+    dt = a.cfl / (ch * a.inv_dx_sum);
+    if (a.t_end > 0.0) dt = fmin(dt, a.t_end - t);
+  }
+  bool bad = !(ch > 0.0) || !(ch < INFINITY) || !(dt >= 0.0) || !(dt < INFINITY);
+  if (bad) {
+    atomicOr(status, 1u);
+    dt = 0.0;
+    ch = 1.0;
+  }
+  sc->dt = dt;
+  sc->ch = ch;
+  for (int d = 0; d < 3; ++d) sc->dtdx[d] = a.active[d] ? dt / a.dx[d] : 0.0;
+  sc->damp = exp(-a.glm_alpha * ch * dt / a.dh_min);
+  sc->t = t + dt;
+  sc->lam = lam;
+  sc->steps += 1.0;
+  *lam_bits = 0ull;  // the stage-2 epilogue accumulates lambda of the new state
+}
+
+cudaError_t launch_prep(const PrepArgs& a, StepScalars* sc, unsigned long long* lam_bits,
+                        unsigned int* status, cudaStream_t stream) {
+  prep_kernel<<<1, 32, 0, stream>>>(a, sc, lam_bits, status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- max wave speed --
+template <class T>
+__global__ void __launch_bounds__(256) max_speed_kernel(const T* __restrict__ U, long long ncell,
+                                                        int ndim, Phys<T> ph,
+                                                        unsigned long long* lam_bits,
+                                                        unsigned long long* floor_cnt) {
+  unsigned flags = 0;
+  double lam = 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    T u[kNV];
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) u[k] = U[k * ncell + c];
+    const double s = (double)cell_max_speed(u, ph, ndim, flags);
+    if (!(s <= lam)) lam = s;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double other = __shfl_xor_sync(0xffffffffu, lam, o);
+    if (!(other <= lam)) lam = other;
+  }
+  __shared__ double w[8];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = lam;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = w[0];
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i)
+      if (!(w[i] <= m)) m = w[i];
+    unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+    if (m != m) bits = 0x7ff8000000000000ull;
+    atomicMax(lam_bits, bits);
+  }
+  if (flags & kFloorRho) atomicAdd(&floor_cnt[0], 1ull);
+  if (flags & kFloorP) atomicAdd(&floor_cnt[1], 1ull);
+}
+
+template <class T>
+cudaError_t launch_max_speed(const Grid& g, const T* U, unsigned long long* lam_bits,
+                             unsigned long long* floor_cnt, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(lam_bits, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return e;
+  long long blocks = (g.ncell + 255) / 256;
+  const long long cap = (long long)g.nsm * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  max_speed_kernel<T><<<(unsigned)blocks, 256, 0, stream>>>(U, g.ncell, g.ndim, make_phys<T>(g),
+                                                            lam_bits, floor_cnt);
+  return cudaGetLastError();
+}
+template cudaError_t launch_max_speed<double>(const Grid&, const double*, unsigned long long*,
+                                              unsigned long long*, cudaStream_t);
+template cudaError_t launch_max_speed<float>(const Grid&, const float*, unsigned long long*,
+                                             unsigned long long*, cudaStream_t);
+
+// ------------------------------------------------------ conservation sums --
+// Pass 1: CTA b sums the contiguous cell range [b*chunk, (b+1)*chunk) of the
+// eight conserved quantities in FP64, threads strided, then a fixed-shape
+// shared-memory tree.  Pass 2: one CTA reduces the partials the same way.
+// The order depends only on (ncell, nblocks): results are bitwise repeatable.
+__device__ __forceinline__ void tree_sum8(double (*s)[8], int tid) {
+  for (int h = 128; h > 0; h >>= 1) {
+    __syncthreads();
+    if (tid < h)
+      for (int q = 0; q < 8; ++q) s[tid][q] += s[tid + h][q];
+  }
+  __syncthreads();
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) sums_pass1(const T* __restrict__ U, long long ncell,
+                                                  long long chunk, double* partials) {
+  __shared__ double s[256][8];
+  const int vars[8] = {kRHO, kVX, kVY, kVZ, kPRS, kBX, kBY, kBZ};
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const long long lo = blockIdx.x * chunk;
+  const long long hi = min(lo + chunk, ncell);
+  for (long long c = lo + threadIdx.x; c < hi; c += 256)
+    for (int q = 0; q < 8; ++q) acc[q] += (double)U[vars[q] * ncell + c];
+  for (int q = 0; q < 8; ++q) s[threadIdx.x][q] = acc[q];
+  tree_sum8(s, threadIdx.x);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 8; ++q) partials[blockIdx.x * 8 + q] = s[0][q];
+}
+
+__global__ void __launch_bounds__(256) sums_pass2(const double* partials, int nblocks,
+                                                  double vol, double* out8) {
+  __shared__ double s[256][8];
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nblocks; b += 256)
+    for (int q = 0; q < 8; ++q) acc[q] += partials[b * 8 + q];
+  for (int q = 0; q < 8; ++q) s[threadIdx.x][q] = acc[q];
+  tree_sum8(s, threadIdx.x);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 8; ++q) out8[q] = s[0][q] * vol;
+}
+
+template <class T>
+cudaError_t launch_sums(const Grid& g, const T* U, double* partials, int nblocks, double* out8,
+                        cudaStream_t stream) {
+  const long long chunk = (g.ncell + nblocks - 1) / nblocks;
+  double vol = 1.0;
+  for (int d = 0; d < 3; ++d)
+    if (g.n[d] > 1) vol *= g.dx[d];
+  sums_pass1<T><<<nblocks, 256, 0, stream>>>(U, g.ncell, chunk, partials);
+  sums_pass2<<<1, 256, 0, stream>>>(partials, nblocks, vol, out8);
+  return cudaGetLastError();
+}
+template cudaError_t launch_sums<double>(const Grid&, const double*, double*, int, double*,
+                                         cudaStream_t);
+template cudaError_t launch_sums<float>(const Grid&, const float*, double*, int, double*,
+                                        cudaStream_t);
+
+// ------------------------------------------------------------ conversions --
+static inline unsigned grid_for(long long n, int nsm) {
+  long long b = (n + 255) / 256;
+  const long long cap = (long long)nsm * 16;
+  if (b > cap) b = cap;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+template <class T>
+__global__ void prim_to_cons_kernel(const double* __restrict__ V, T* __restrict__ U,
+                                    long long ncell, Phys<double> ph) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    double v[kNV], u[kNV];
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) v[k] = V[k * ncell + c];
+    prim_to_cons(v, u, ph);
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) U[k * ncell + c] = (T)u[k];
+  }
+}
+
+template <class T>
+__global__ void prim_to_cons_inplace_kernel(T* U, long long ncell, Phys<double> ph) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    double v[kNV], u[kNV];
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) v[k] = (double)U[k * ncell + c];
+    prim_to_cons(v, u, ph);
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) U[k * ncell + c] = (T)u[k];
+  }
+}
+
+template <class T>
+__global__ void cons_to_prim_kernel(const T* __restrict__ U, double* __restrict__ V,
+                                    long long ncell, Phys<T> ph) {
+  unsigned flags = 0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    T u[kNV], v[kNV];
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) u[k] = U[k * ncell + c];
+    cons_to_prim(u, v, ph, flags);
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) V[k * ncell + c] = (double)v[k];
+  }
+}
+
+template <class T>
+cudaError_t launch_prim_to_cons(const Grid& g, const double* V, T* U, cudaStream_t stream) {
+  prim_to_cons_kernel<T><<<grid_for(g.ncell, g.nsm), 256, 0, stream>>>(V, U, g.ncell,
+                                                                        make_phys<double>(g));
+  return cudaGetLastError();
+}
+template <class T>
+cudaError_t launch_prim_to_cons_inplace(const Grid& g, T* U, cudaStream_t stream) {
+  prim_to_cons_inplace_kernel<T><<<grid_for(g.ncell, g.nsm), 256, 0, stream>>>(
+      U, g.ncell, make_phys<double>(g));
+  return cudaGetLastError();
+}
+template <class T>
+cudaError_t launch_cons_to_prim(const Grid& g, const T* U, double* V, cudaStream_t stream) {
+  cons_to_prim_kernel<T><<<grid_for(g.ncell, g.nsm), 256, 0, stream>>>(U, V, g.ncell,
+                                                                        make_phys<T>(g));
+  return cudaGetLastError();
+}
+template cudaError_t launch_prim_to_cons<double>(const Grid&, const double*, double*,
+                                                 cudaStream_t);
+template cudaError_t launch_prim_to_cons<float>(const Grid&, const double*, float*,
+                                                cudaStream_t);
+template cudaError_t launch_prim_to_cons_inplace<double>(const Grid&, double*, cudaStream_t);
+template cudaError_t launch_prim_to_cons_inplace<float>(const Grid&, float*, cudaStream_t);
+template cudaError_t launch_cons_to_prim<double>(const Grid&, const double*, double*,
+                                                 cudaStream_t);
+template cudaError_t launch_cons_to_prim<float>(const Grid&, const float*, double*,
+                                                cudaStream_t);
+
+__global__ void f64_to_f32_kernel(const double* __restrict__ in, float* __restrict__ out,
+                                  long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+__global__ void f32_to_f64_kernel(const float* __restrict__ in, double* __restrict__ out,
+                                  long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+cudaError_t launch_f64_to_f32(const double* in, float* out, long long n, cudaStream_t stream) {
+  f64_to_f32_kernel<<<grid_for(n, 152), 256, 0, stream>>>(in, out, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_f32_to_f64(const float* in, double* out, long long n, cudaStream_t stream) {
+  f32_to_f64_kernel<<<grid_for(n, 152), 256, 0, stream>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ flux batch --
+template <class T>
+__global__ void flux_batch_kernel(const T* __restrict__ VL, const T* __restrict__ VR,
+                                  T* __restrict__ F, long long nface, int dir, T ch, T half_chi,
+                                  Phys<T> ph) {
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nface;
+       f += (long long)gridDim.x * blockDim.x) {
+    T vl[kNV], vr[kNV], out[kNV];
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) {
+      vl[k] = VL[k * nface + f];
+      vr[k] = VR[k * nface + f];
+    }
+    glm_hlld_flux(vl, vr, dir, ch, half_chi, ph, out);
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) F[k * nface + f] = out[k];
+  }
+}
+
+template <class T>
+cudaError_t launch_flux_batch(const T* VL, const T* VR, T* F, long long nface, int dir,
+                              double ch, double gamma, cudaStream_t stream) {
+  Grid g{};
+  g.gamma = gamma;
+  g.rho_floor = 0.0;
+  g.p_floor = 0.0;
+  flux_batch_kernel<T><<<grid_for(nface, 152), 256, 0, stream>>>(
+      VL, VR, F, nface, dir, T(ch), T(0.5 / ch), make_phys<T>(g));
+  return cudaGetLastError();
+}
+template cudaError_t launch_flux_batch<double>(const double*, const double*, double*, long long,
+                                               int, double, double, cudaStream_t);
+template cudaError_t launch_flux_batch<float>(const float*, const float*, float*, long long, int,
+                                              double, double, cudaStream_t);
+
+}  // namespace mhd

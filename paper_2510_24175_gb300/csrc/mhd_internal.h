@@ -1,0 +1,75 @@
+// Host-side launcher interface between the C ABI (mhd_api.cu) and the kernel
+// translation units.  Plain types only; every launcher enqueues on `stream`
+// and returns the cudaError_t of the launch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "mhd_stage.cuh"
+
+namespace mhd {
+
+// Geometry + physics of one context, shared by all launchers.
+struct Grid {
+  int n[3];
+  int ndim;              // number of active dims (prefix x, y, z)
+  long long ncell;       // nx * ny * nz
+  int bc_lo[3], bc_hi[3];
+  int limiter;
+  double gamma, rho_floor, p_floor;
+  double dx[3];
+  int tz;                // z planes per CTA of the stage kernel
+  int nsm;               // SM count of the device
+};
+
+template <class T>
+Phys<T> make_phys(const Grid& g);
+
+// Stage kernel (mhd_stage_f64.cu / mhd_stage_f32.cu).
+template <class T>
+cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T* uout,
+                         const StepScalars* sc, unsigned long long* lam_bits,
+                         unsigned long long* floor_cnt, cudaStream_t stream);
+
+// Shared-memory bytes and threads of the stage kernel for this grid.
+template <class T>
+void stage_shape(const Grid& g, size_t* smem, int* threads, int* ty);
+
+// Auxiliary kernels (mhd_aux.cu).
+struct PrepArgs {
+  double dt_req, ch_req;  // > 0: use as given
+  double cfl, inv_dx_sum, t_end, glm_alpha, dh_min;
+  double dx[3];
+  int active[3];
+};
+cudaError_t launch_prep(const PrepArgs& a, StepScalars* sc, unsigned long long* lam_bits,
+                        unsigned int* status, cudaStream_t stream);
+
+template <class T>
+cudaError_t launch_max_speed(const Grid& g, const T* U, unsigned long long* lam_bits,
+                             unsigned long long* floor_cnt, cudaStream_t stream);
+
+template <class T>
+cudaError_t launch_sums(const Grid& g, const T* U, double* partials, int nblocks,
+                        double* out8, cudaStream_t stream);
+
+// U (type T) <- V (double), prim -> cons computed in FP64 per cell.
+template <class T>
+cudaError_t launch_prim_to_cons(const Grid& g, const double* V, T* U, cudaStream_t stream);
+// In place: U (type T) holds primitives on entry, conservatives on exit.
+template <class T>
+cudaError_t launch_prim_to_cons_inplace(const Grid& g, T* U, cudaStream_t stream);
+// V (double) <- cons -> prim of U (type T).
+template <class T>
+cudaError_t launch_cons_to_prim(const Grid& g, const T* U, double* V, cudaStream_t stream);
+// Elementwise conversions.
+cudaError_t launch_f64_to_f32(const double* in, float* out, long long n, cudaStream_t stream);
+cudaError_t launch_f32_to_f64(const float* in, double* out, long long n, cudaStream_t stream);
+
+template <class T>
+cudaError_t launch_flux_batch(const T* VL, const T* VR, T* F, long long nface, int dir,
+                              double ch, double gamma, cudaStream_t stream);
+
+}  // namespace mhd

@@ -1,0 +1,332 @@
+// Device-side pointwise physics of the GLM-MHD hot path, templated on the
+// arithmetic type T (double for MHD_FP64, float for MHD_FP32).
+//
+// The stage structure is Section 3.2's (boundary calculation, cons->prim,
+// reconstruction, Riemann solver, right-hand side); HLLD is named in
+// Section 4.2 and divergence cleaning (GLM) in Section 4.2's strong-scaling
+// paragraph.  The formulas are the published methods:
+//   - HLLD: Miyoshi & Kusano (2005), J. Comput. Phys. 208: wave speeds
+//     (Eq. 67), S_M and p_t* (Eqs. 38, 41), single-star states (Eqs. 43-48),
+//     Alfven speeds S*_{L,R} (Eq. 51), double-star states (Eqs. 59-63),
+//     fan-region fluxes (Eqs. 64-66).
+//   - GLM interface values: Dedner et al. (2002), J. Comput. Phys. 175,
+//     Eq. 41 (exact solution of the 2x2 (B_n, psi) Riemann problem).
+//   - PLM slopes: minmod / monotonised-central limiters of van Leer (1977),
+//     applied to primitive variables, with a zero-slope fallback for a cell
+//     whose face density or pressure would be non-positive.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mhd {
+
+enum { kRHO = 0, kVX = 1, kVY = 2, kVZ = 3, kBX = 4, kBY = 5, kBZ = 6, kPRS = 7, kPSI = 8,
+       kNV = 9 };
+enum { kLimFlat = 0, kLimMinmod = 1, kLimMC = 2 };
+enum { kBcPeriodic = 0, kBcOutflow = 1 };
+enum { kFloorRho = 1u, kFloorP = 2u };
+
+template <class T>
+struct Phys {
+  T gamma;      // adiabatic index
+  T gm1;        // gamma - 1
+  T gm1i;       // 1 / (gamma - 1)
+  T rho_floor;
+  T p_floor;
+  double gamma_d, rho_floor_d, p_floor_d;  // FP64 copies for the floor branch
+};
+
+__device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double tabs(double x) { return fabs(x); }
+__device__ __forceinline__ float tabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
+
+// Pressure floor.  FP64: plain comparison.  FP32: when the FP32 pressure is
+// within the cancellation-dominated range (internal energy below 1e-3 of the
+// total, or below the floor) p is recomputed in FP64 from the promoted
+// conservative inputs and the floor decision is taken in FP64.
+__device__ __forceinline__ double pressure_floor(double p, const double u[kNV], double rho,
+                                                 const Phys<double>& ph, unsigned& flags) {
+  if (p < ph.p_floor) {
+    flags |= kFloorP;
+    return ph.p_floor;
+  }
+  return p;
+}
+__device__ __forceinline__ float pressure_floor(float p, const float u[kNV], float rho,
+                                                const Phys<float>& ph, unsigned& flags) {
+  if (p < ph.p_floor || p < 1e-3f * ph.gm1 * u[kPRS]) {
+    double r = rho;
+    double m2 = (double)u[kVX] * u[kVX] + (double)u[kVY] * u[kVY] + (double)u[kVZ] * u[kVZ];
+    double b2 = (double)u[kBX] * u[kBX] + (double)u[kBY] * u[kBY] + (double)u[kBZ] * u[kBZ];
+    double pd = (ph.gamma_d - 1.0) * ((double)u[kPRS] - 0.5 * m2 / r - 0.5 * b2);
+    if (pd < ph.p_floor_d) {
+      flags |= kFloorP;
+      return ph.p_floor;
+    }
+    return (float)pd;
+  }
+  return p;
+}
+
+// Conservative -> primitive (step 2 of the stage).  Floors by replacement,
+// density first, then pressure; activations are flagged.
+template <class T>
+__device__ __forceinline__ void cons_to_prim(const T u[kNV], T v[kNV], const Phys<T>& ph,
+                                             unsigned& flags) {
+  T rho = u[kRHO];
+  if (rho < ph.rho_floor) {
+    rho = ph.rho_floor;
+    flags |= kFloorRho;
+  }
+  const T ri = rcp(rho);
+  const T vx = u[kVX] * ri, vy = u[kVY] * ri, vz = u[kVZ] * ri;
+  const T kin = T(0.5) * (u[kVX] * vx + u[kVY] * vy + u[kVZ] * vz);
+  const T b2 = u[kBX] * u[kBX] + u[kBY] * u[kBY] + u[kBZ] * u[kBZ];
+  T p = ph.gm1 * (u[kPRS] - kin - T(0.5) * b2);
+  p = pressure_floor(p, u, rho, ph, flags);
+  v[kRHO] = rho;
+  v[kVX] = vx;
+  v[kVY] = vy;
+  v[kVZ] = vz;
+  v[kBX] = u[kBX];
+  v[kBY] = u[kBY];
+  v[kBZ] = u[kBZ];
+  v[kPRS] = p;
+  v[kPSI] = u[kPSI];
+}
+
+// Primitive -> conservative.
+template <class T>
+__device__ __forceinline__ void prim_to_cons(const T v[kNV], T u[kNV], const Phys<T>& ph) {
+  const T rho = v[kRHO];
+  const T v2 = v[kVX] * v[kVX] + v[kVY] * v[kVY] + v[kVZ] * v[kVZ];
+  const T b2 = v[kBX] * v[kBX] + v[kBY] * v[kBY] + v[kBZ] * v[kBZ];
+  u[kRHO] = rho;
+  u[kVX] = rho * v[kVX];
+  u[kVY] = rho * v[kVY];
+  u[kVZ] = rho * v[kVZ];
+  u[kBX] = v[kBX];
+  u[kBY] = v[kBY];
+  u[kBZ] = v[kBZ];
+  u[kPRS] = v[kPRS] * ph.gm1i + T(0.5) * rho * v2 + T(0.5) * b2;
+  u[kPSI] = v[kPSI];
+}
+
+// Fast magnetosonic speed from 1/rho, gamma p, |B|^2 and B_n^2:
+// c_f^2 = (a + sqrt(a^2 - 4 gamma p B_n^2 / rho^2)) / 2, a = (gamma p + |B|^2)/rho.
+template <class T>
+__device__ __forceinline__ T fast_speed(T rho_i, T gp, T b2, T bn2) {
+  const T a = (gp + b2) * rho_i;
+  T disc = a * a - T(4) * gp * bn2 * (rho_i * rho_i);
+  disc = tmax(disc, T(0));
+  return tsqrt(T(0.5) * (a + tsqrt(disc)));
+}
+
+// max over active directions of |v_d| + c_f,d for one conservative cell.
+template <class T>
+__device__ __forceinline__ T cell_max_speed(const T u[kNV], const Phys<T>& ph, int ndim,
+                                            unsigned& flags) {
+  T v[kNV];
+  cons_to_prim(u, v, ph, flags);
+  const T ri = rcp(v[kRHO]);
+  const T gp = ph.gamma * v[kPRS];
+  const T b2 = v[kBX] * v[kBX] + v[kBY] * v[kBY] + v[kBZ] * v[kBZ];
+  T lam = tabs(v[kVX]) + fast_speed(ri, gp, b2, v[kBX] * v[kBX]);
+  if (ndim > 1) lam = tmax(lam, tabs(v[kVY]) + fast_speed(ri, gp, b2, v[kBY] * v[kBY]));
+  if (ndim > 2) lam = tmax(lam, tabs(v[kVZ]) + fast_speed(ri, gp, b2, v[kBZ] * v[kBZ]));
+  // NaN anywhere in the cell (psi included) makes the speed NaN
+  if (!(v[kPSI] == v[kPSI]) || !(lam == lam)) lam = T(NAN);
+  return lam;
+}
+
+// Limited slope (van Leer 1977): 0 when the one-sided differences disagree in
+// sign; minmod = smaller magnitude; MC = min(2|dm|, 2|dp|, |dm+dp|/2).
+template <class T>
+__device__ __forceinline__ T limited_slope(T dm, T dp, int lim) {
+  if (lim == kLimFlat || !(dm * dp > T(0))) return T(0);
+  const T am = tabs(dm), ap = tabs(dp);
+  T mag = tmin(am, ap);
+  if (lim == kLimMC) mag = tmin(T(2) * mag, T(0.5) * tabs(dm + dp));
+  return dm > T(0) ? mag : -mag;
+}
+
+// PLM face states around one interface from four consecutive cells q0..q3
+// (the interface lies between q1 and q2).  c[j] points at variable 0 of cell
+// j; variables are vstride apart.  Writes the left state (from q1) and the
+// right state (from q2).
+template <class T>
+__device__ __forceinline__ void plm_face_pair(const T* c0, const T* c1, const T* c2,
+                                              const T* c3, int vstride, int lim, T vl[kNV],
+                                              T vr[kNV]) {
+  T s1[kNV], s2[kNV];
+#pragma unroll
+  for (int k = 0; k < kNV; ++k) {
+    const T q0 = c0[k * vstride], q1 = c1[k * vstride], q2 = c2[k * vstride],
+            q3 = c3[k * vstride];
+    s1[k] = limited_slope(q1 - q0, q2 - q1, lim);
+    s2[k] = limited_slope(q2 - q1, q3 - q2, lim);
+    vl[k] = q1;
+    vr[k] = q2;
+  }
+  // zero-slope fallback per cell if a face density or pressure is <= 0
+  const bool ok1 = (vl[kRHO] - T(0.5) * tabs(s1[kRHO]) > T(0)) &&
+                   (vl[kPRS] - T(0.5) * tabs(s1[kPRS]) > T(0));
+  const bool ok2 = (vr[kRHO] - T(0.5) * tabs(s2[kRHO]) > T(0)) &&
+                   (vr[kPRS] - T(0.5) * tabs(s2[kPRS]) > T(0));
+#pragma unroll
+  for (int k = 0; k < kNV; ++k) {
+    if (ok1) vl[k] = vl[k] + T(0.5) * s1[k];
+    if (ok2) vr[k] = vr[k] - T(0.5) * s2[k];
+  }
+}
+
+// Picks component (dir + j) % 3 of a 3-vector given as scalars.
+template <class T>
+__device__ __forceinline__ T rot3(int dir, int j, T a, T b, T c) {
+  const int m = (dir + j) % 3;
+  return m == 0 ? a : (m == 1 ? b : c);
+}
+
+// GLM interface step + HLLD along direction dir (0, 1, 2) for primitive face
+// states vl, vr.  ch: cleaning speed; half_chi = 0.5 / ch.  F in conservative
+// ordering.
+template <class T>
+__device__ __forceinline__ void glm_hlld_flux(const T vl[kNV], const T vr[kNV], int dir, T ch,
+                                              T half_chi, const Phys<T>& ph, T F[kNV]) {
+  const T half = T(0.5);
+  // rotate: u normal, (v, w) tangential in cyclic order; by, bz likewise
+  const T uL = rot3(dir, 0, vl[kVX], vl[kVY], vl[kVZ]);
+  const T vL = rot3(dir, 1, vl[kVX], vl[kVY], vl[kVZ]);
+  const T wL = rot3(dir, 2, vl[kVX], vl[kVY], vl[kVZ]);
+  const T bnL = rot3(dir, 0, vl[kBX], vl[kBY], vl[kBZ]);
+  const T byL = rot3(dir, 1, vl[kBX], vl[kBY], vl[kBZ]);
+  const T bzL = rot3(dir, 2, vl[kBX], vl[kBY], vl[kBZ]);
+  const T uR = rot3(dir, 0, vr[kVX], vr[kVY], vr[kVZ]);
+  const T vR = rot3(dir, 1, vr[kVX], vr[kVY], vr[kVZ]);
+  const T wR = rot3(dir, 2, vr[kVX], vr[kVY], vr[kVZ]);
+  const T bnR = rot3(dir, 0, vr[kBX], vr[kBY], vr[kBZ]);
+  const T byR = rot3(dir, 1, vr[kBX], vr[kBY], vr[kBZ]);
+  const T bzR = rot3(dir, 2, vr[kBX], vr[kBY], vr[kBZ]);
+  const T rL = vl[kRHO], pL = vl[kPRS], rR = vr[kRHO], pR = vr[kPRS];
+
+  // GLM: exact solution of the linear (B_n, psi) interface problem
+  const T bx = half * (bnL + bnR) - half_chi * (vr[kPSI] - vl[kPSI]);
+  const T psis = half * (vl[kPSI] + vr[kPSI]) - half * ch * (bnR - bnL);
+  const T bx2 = bx * bx;
+
+  // outer states
+  const T b2L = bx2 + byL * byL + bzL * bzL;
+  const T b2R = bx2 + byR * byR + bzR * bzR;
+  const T ptL = pL + half * b2L, ptR = pR + half * b2R;
+  const T eL = pL * ph.gm1i + half * rL * (uL * uL + vL * vL + wL * wL) + half * b2L;
+  const T eR = pR * ph.gm1i + half * rR * (uR * uR + vR * vR + wR * wR) + half * b2R;
+  const T cfL = fast_speed(rcp(rL), ph.gamma * pL, b2L, bx2);
+  const T cfR = fast_speed(rcp(rR), ph.gamma * pR, b2R, bx2);
+
+  // wave-speed estimates (MK05 Eq. 67), contact speed and total pressure
+  const T cmax = tmax(cfL, cfR);
+  const T SL = tmin(uL, uR) - cmax;
+  const T SR = tmax(uL, uR) + cmax;
+  const T dL = (SL - uL) * rL, dR = (SR - uR) * rR;
+  const T Di = rcp(dR - dL);
+  const T SM = (dR * uR - dL * uL - ptR + ptL) * Di;
+  const T pts = (dR * ptL - dL * ptR + dL * dR * (uR - uL)) * Di;
+
+  // single-star states (MK05 Eqs. 43-48), degenerate when
+  // |rho (S-u)(S-S_M) - Bx^2| < 1e-8 p_t*
+  T rsL, vsL, wsL, bysL, bzsL, esL, vbsL;
+  T rsR, vsR, wsR, bysR, bzsR, esR, vbsR;
+  {
+    const T sm = SL - SM, smi = rcp(sm);
+    rsL = dL * smi;
+    const T den = dL * sm - bx2;
+    const bool deg = tabs(den) < T(1e-8) * pts;
+    const T deni = rcp(deg ? T(1) : den);
+    const T fv = bx * (SM - uL) * deni;
+    const T fb = (dL * (SL - uL) - bx2) * deni;
+    vsL = deg ? vL : vL - byL * fv;
+    wsL = deg ? wL : wL - bzL * fv;
+    bysL = deg ? byL : byL * fb;
+    bzsL = deg ? bzL : bzL * fb;
+    const T vb = uL * bx + vL * byL + wL * bzL;
+    vbsL = SM * bx + vsL * bysL + wsL * bzsL;
+    esL = ((SL - uL) * eL - ptL * uL + pts * SM + bx * (vb - vbsL)) * smi;
+  }
+  {
+    const T sm = SR - SM, smi = rcp(sm);
+    rsR = dR * smi;
+    const T den = dR * sm - bx2;
+    const bool deg = tabs(den) < T(1e-8) * pts;
+    const T deni = rcp(deg ? T(1) : den);
+    const T fv = bx * (SM - uR) * deni;
+    const T fb = (dR * (SR - uR) - bx2) * deni;
+    vsR = deg ? vR : vR - byR * fv;
+    wsR = deg ? wR : wR - bzR * fv;
+    bysR = deg ? byR : byR * fb;
+    bzsR = deg ? bzR : bzR * fb;
+    const T vb = uR * bx + vR * byR + wR * bzR;
+    vbsR = SM * bx + vsR * bysR + wsR * bzsR;
+    esR = ((SR - uR) * eR - ptR * uR + pts * SM + bx * (vb - vbsR)) * smi;
+  }
+
+  // Alfven waves (MK05 Eq. 51) and double-star states (Eqs. 59-63)
+  const T sqL = tsqrt(rsL), sqR = tsqrt(rsR);
+  const T abx = tabs(bx);
+  const T SLs = SM - abx * rcp(sqL);
+  const T SRs = SM + abx * rcp(sqR);
+  const T sg = bx >= T(0) ? T(1) : T(-1);
+  const T isum = rcp(sqL + sqR);
+  const T vss = (sqL * vsL + sqR * vsR + (bysR - bysL) * sg) * isum;
+  const T wss = (sqL * wsL + sqR * wsR + (bzsR - bzsL) * sg) * isum;
+  const T byss = (sqL * bysR + sqR * bysL + sqL * sqR * (vsR - vsL) * sg) * isum;
+  const T bzss = (sqL * bzsR + sqR * bzsL + sqL * sqR * (wsR - wsL) * sg) * isum;
+  const T vbss = SM * bx + vss * byss + wss * bzss;
+
+  // Fan region: side a = L if (S_L > 0) or (S_R >= 0 and S_M >= 0), else R.
+  // F = F_a + c1 (U*_a - U_a) + c2 (U**_a - U*_a) with c1 = S_a unless the
+  // interface is supersonic, c2 = S*_a inside the Alfven fan.
+  const bool sup = (SL > T(0)) || (SR < T(0));
+  const bool useL = (SL > T(0)) || (!(SR < T(0)) && SM >= T(0));
+  const bool inner = !sup && (useL ? !(SLs > T(0)) : !(SRs < T(0)));
+  const T r = useL ? rL : rR, u = useL ? uL : uR, v = useL ? vL : vR, w = useL ? wL : wR;
+  const T by = useL ? byL : byR, bz = useL ? bzL : bzR, e = useL ? eL : eR;
+  const T pt = useL ? ptL : ptR;
+  const T rs = useL ? rsL : rsR, vs = useL ? vsL : vsR, ws = useL ? wsL : wsR;
+  const T bys = useL ? bysL : bysR, bzs = useL ? bzsL : bzsR, es = useL ? esL : esR;
+  const T sq = useL ? -sqL : sqR;
+  const T vbs = useL ? vbsL : vbsR;
+  const T ess = es + sq * (vbs - vbss) * sg;
+  const T c1 = sup ? T(0) : (useL ? SL : SR);
+  const T c2 = inner ? (useL ? SLs : SRs) : T(0);
+
+  const T vb = u * bx + v * by + w * bz;
+  T f[7];
+  f[0] = r * u + c1 * (rs - r);
+  f[1] = r * u * u + pt - bx2 + c1 * (rs * SM - r * u);
+  f[2] = r * v * u - bx * by + c1 * (rs * vs - r * v) + c2 * rs * (vss - vs);
+  f[3] = r * w * u - bx * bz + c1 * (rs * ws - r * w) + c2 * rs * (wss - ws);
+  f[4] = by * u - bx * v + c1 * (bys - by) + c2 * (byss - bys);
+  f[5] = bz * u - bx * w + c1 * (bzs - bz) + c2 * (bzss - bzs);
+  f[6] = (e + pt) * u - bx * vb + c1 * (es - e) + c2 * (ess - es);
+
+  F[kRHO] = f[0];
+  F[kPRS] = f[6];
+  F[kPSI] = ch * ch * bx;
+  // un-rotate: component m of a vector gets rotated slot j = (m - dir) mod 3
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const int j = (m - dir + 3) % 3;
+    F[kVX + m] = j == 0 ? f[1] : (j == 1 ? f[2] : f[3]);
+    F[kBX + m] = j == 0 ? psis : (j == 1 ? f[4] : f[5]);
+  }
+}
+
+}  // namespace mhd

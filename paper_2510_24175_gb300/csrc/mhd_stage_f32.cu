@@ -1,0 +1,9 @@
+// FP32 instantiation of the fused stage kernel.
+#include "mhd_stage_impl.cuh"
+
+namespace mhd {
+template cudaError_t launch_stage<float>(const Grid&, int, const float*, const float*, float*,
+                                         const StepScalars*, unsigned long long*,
+                                         unsigned long long*, cudaStream_t);
+template void stage_shape<float>(const Grid&, size_t*, int*, int*);
+}  // namespace mhd

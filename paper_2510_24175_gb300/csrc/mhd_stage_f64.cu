@@ -1,0 +1,9 @@
+// FP64 instantiation of the fused stage kernel.
+#include "mhd_stage_impl.cuh"
+
+namespace mhd {
+template cudaError_t launch_stage<double>(const Grid&, int, const double*, const double*, double*,
+                                          const StepScalars*, unsigned long long*,
+                                          unsigned long long*, cudaStream_t);
+template void stage_shape<double>(const Grid&, size_t*, int*, int*);
+}  // namespace mhd

@@ -1,0 +1,88 @@
+// Launch-shape selection and instantiation of the fused stage kernel for one
+// arithmetic type.  Included once per type by mhd_stage_f64.cu / _f32.cu.
+#pragma once
+
+#include "mhd_internal.h"
+
+namespace mhd {
+
+// Tile shapes: 3-D grids use 32 x 8 column tiles marching in z; FP64 runs 13
+// warps per CTA (one CTA per SM: 201 KB of shared memory), which makes the
+// 26 warp-sized flux work items and the 416 loaded halo cells of a plane
+// divide evenly; FP32 runs 8 warps and two CTAs per SM.  2-D grids use the
+// same tile with a single plane; 1-D grids a 32-cell row.
+template <class T>
+struct StageShape3D {
+  static constexpr int TY = 8;
+  static constexpr int NW = sizeof(T) == 8 ? 13 : 8;
+};
+
+template <class T, int TY, int NW, int STAGE, bool ZACT>
+static cudaError_t launch_one(const StageParams<T>& p, dim3 grid, cudaStream_t s) {
+  using G = TileGeom<TY, ZACT>;
+  const size_t smem = (size_t)G::WORDS * sizeof(T);
+  auto kern = rk_stage_kernel<T, TY, NW, STAGE, ZACT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, NW * 32, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <class T>
+void stage_shape(const Grid& g, size_t* smem, int* threads, int* ty) {
+  if (g.ndim == 3) {
+    using S = StageShape3D<T>;
+    *smem = (size_t)TileGeom<S::TY, true>::WORDS * sizeof(T);
+    *threads = S::NW * 32;
+    *ty = S::TY;
+  } else if (g.ndim == 2) {
+    *smem = (size_t)TileGeom<8, false>::WORDS * sizeof(T);
+    *threads = 8 * 32;
+    *ty = 8;
+  } else {
+    *smem = (size_t)TileGeom<1, false>::WORDS * sizeof(T);
+    *threads = 32;
+    *ty = 1;
+  }
+}
+
+template <class T>
+cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T* uout,
+                         const StepScalars* sc, unsigned long long* lam_bits,
+                         unsigned long long* floor_cnt, cudaStream_t stream) {
+  StageParams<T> p;
+  p.win = win;
+  p.un = un;
+  p.uout = uout;
+  for (int d = 0; d < 3; ++d) {
+    p.n[d] = g.n[d];
+    p.bc_lo[d] = g.bc_lo[d];
+    p.bc_hi[d] = g.bc_hi[d];
+  }
+  p.sy = g.n[0];
+  p.sz = (long long)g.n[0] * g.n[1];
+  p.sv = g.ncell;
+  p.limiter = g.limiter;
+  p.tz = g.ndim == 3 ? g.tz : 1;
+  p.ph = make_phys<T>(g);
+  p.sc = sc;
+  p.lam_bits = lam_bits;
+  p.floor_cnt = floor_cnt;
+  if (g.ndim == 3) {
+    using S = StageShape3D<T>;
+    dim3 grid((g.n[0] + 31) / 32, (g.n[1] + S::TY - 1) / S::TY, (g.n[2] + p.tz - 1) / p.tz);
+    return stage == 1 ? launch_one<T, S::TY, S::NW, 1, true>(p, grid, stream)
+                      : launch_one<T, S::TY, S::NW, 2, true>(p, grid, stream);
+  }
+  if (g.ndim == 2) {
+    dim3 grid((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, 1);
+    return stage == 1 ? launch_one<T, 8, 8, 1, false>(p, grid, stream)
+                      : launch_one<T, 8, 8, 2, false>(p, grid, stream);
+  }
+  dim3 grid((g.n[0] + 31) / 32, 1, 1);
+  return stage == 1 ? launch_one<T, 1, 1, 1, false>(p, grid, stream)
+                    : launch_one<T, 1, 1, 2, false>(p, grid, stream);
+}
+
+}  // namespace mhd

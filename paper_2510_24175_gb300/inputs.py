@@ -105,11 +105,12 @@ def _orszag_tang(pb: Problem) -> np.ndarray:
     return V
 
 
-def _gaussian_field(n, rng, kmin, kmax, slope, ncomp):
-    """Real periodic fields (ncomp, nz, ny, nx) with shell spectrum E(k) ~ k^slope
-    for integer |k| in [kmin, kmax], complex Gaussian mode amplitudes."""
+def _half_spectrum(n, rng, kmin, kmax, slope, ncomp):
+    """Seeded complex Gaussian modes on the half (real-FFT) spectrum grid,
+    shape (ncomp, nz, ny, nx//2+1), with shell spectrum E(k) ~ k^slope for
+    integer |k| in [kmin, kmax].  Returns (modes, (kz, ky, kx))."""
     nx, ny, nz = n
-    kx = np.fft.fftfreq(nx, 1.0 / nx) if nx > 1 else np.zeros(1)
+    kx = np.fft.rfftfreq(nx, 1.0 / nx)
     ky = np.fft.fftfreq(ny, 1.0 / ny) if ny > 1 else np.zeros(1)
     kz = np.fft.fftfreq(nz, 1.0 / nz) if nz > 1 else np.zeros(1)
     K = np.sqrt(kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2)
@@ -118,17 +119,30 @@ def _gaussian_field(n, rng, kmin, kmax, slope, ncomp):
     amp = np.zeros_like(K)
     mask = (K >= kmin) & (K <= kmax)
     amp[mask] = K[mask] ** ((slope - (dim - 1)) / 2.0)
-    out = np.empty((ncomp, nz, ny, nx))
+    modes = np.empty((ncomp,) + K.shape, dtype=np.complex128)
     for c in range(ncomp):
-        modes = (rng.standard_normal(K.shape) + 1j * rng.standard_normal(K.shape)) * amp
-        out[c] = np.fft.ifftn(modes).real
-    return out, (kz, ky, kx)
+        modes[c].real = rng.standard_normal(K.shape)
+        modes[c].imag = rng.standard_normal(K.shape)
+        modes[c] *= amp
+    return modes, (kz, ky, kx)
+
+
+def _to_real(modes, n):
+    nx, ny, nz = n
+    return np.fft.irfftn(modes, s=(nz, ny, nx), axes=(-3, -2, -1))
+
+
+def _gaussian_field(n, rng, kmin, kmax, slope, ncomp):
+    """Real periodic fields (ncomp, nz, ny, nx) with a k^slope shell spectrum."""
+    modes, ks = _half_spectrum(n, rng, kmin, kmax, slope, ncomp)
+    return np.stack([_to_real(modes[c], n) for c in range(ncomp)]), ks
 
 
 def _turbulent_box(pb: Problem) -> np.ndarray:
     """rho = 1, p = 0.6; v a seeded Gaussian random field with a k^-2 shell
     spectrum (|k| in [1, 16]) scaled to rms |v| = 0.5; B = (0.2, 0, 0) plus the
-    curl of a seeded vector potential of the same spectral shape, rms 0.05."""
+    curl of a seeded vector potential of the same spectral shape, rms 0.05
+    (divergence-free to round-off: the curl is taken in spectral space)."""
     rng = np.random.default_rng(pb.seed)
     V = _empty(pb)
     V[RHO] = 1.0
@@ -136,17 +150,17 @@ def _turbulent_box(pb: Problem) -> np.ndarray:
     v, _ = _gaussian_field(pb.n, rng, 1, 16, -2.0, 3)
     v *= pb.params.get("v_rms", 0.5) / math.sqrt(np.mean(np.sum(v * v, axis=0)))
     V[VX:VZ + 1] = v
-    # vector potential -> spectral curl (divergence-free to round-off)
-    A, (kz, ky, kx) = _gaussian_field(pb.n, rng, 1, 16, -2.0, 3)
-    Ah = [np.fft.fftn(A[c]) for c in range(3)]
+    del v
+    Ah, (kz, ky, kx) = _half_spectrum(pb.n, rng, 1, 16, -2.0, 3)
     L = [pb.xmax[d] - pb.xmin[d] for d in range(3)]
     ikx = 2j * math.pi * kx[None, None, :] / L[0]
     iky = 2j * math.pi * ky[None, :, None] / L[1]
     ikz = 2j * math.pi * kz[:, None, None] / L[2]
     b = np.empty((3,) + V[0].shape)
-    b[0] = np.fft.ifftn(iky * Ah[2] - ikz * Ah[1]).real
-    b[1] = np.fft.ifftn(ikz * Ah[0] - ikx * Ah[2]).real
-    b[2] = np.fft.ifftn(ikx * Ah[1] - iky * Ah[0]).real
+    b[0] = _to_real(iky * Ah[2] - ikz * Ah[1], pb.n)
+    b[1] = _to_real(ikz * Ah[0] - ikx * Ah[2], pb.n)
+    b[2] = _to_real(ikx * Ah[1] - iky * Ah[0], pb.n)
+    del Ah
     brms = math.sqrt(np.mean(np.sum(b * b, axis=0)))
     if brms > 0:
         b *= pb.params.get("b_rms", 0.05) / brms

@@ -1,0 +1,76 @@
+"""Shared helpers of the parity tests: problem -> oracle grid, GPU runs through
+the C ABI, the relative-L1 norm, and the oracle's one-step value at sampled
+cells of a large periodic grid (a local sub-box computation)."""
+import numpy as np
+
+import oracle as orc
+from paper_2510_24175_gb300.inputs import Problem
+
+RHO, VX, VY, VZ, BX, BY, BZ, PRS, PSI = range(9)
+
+
+def grid_of(pb: Problem) -> orc.Grid:
+    return orc.Grid(n=pb.n, dx=pb.dx, gamma=pb.gamma, glm_alpha=pb.glm_alpha,
+                    rho_floor=pb.rho_floor, p_floor=pb.p_floor, limiter=pb.limiter,
+                    bc=pb.bc, cfl=pb.cfl)
+
+
+def rel_l1(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Per variable ||a-b||_1 / max(||b||_1, 1e-3 ||rho_b||_1): the floor keeps
+    near-zero planes (psi, a vanishing component) from dividing by ~0."""
+    num = np.abs(a - b).reshape(9, -1).sum(axis=1)
+    den = np.abs(b).reshape(9, -1).sum(axis=1)
+    den = np.maximum(den, 1e-3 * den[RHO])
+    return num / den
+
+
+def oracle_run(pb: Problem, nsteps: int, t_end: float = 0.0):
+    g = grid_of(pb)
+    U0 = orc.prim_to_cons(pb.prim(), pb.gamma)
+    return orc.run(U0, g, nsteps, t_end=t_end)
+
+
+def gpu_run(pb: Problem, nsteps: int, precision=None, record=False):
+    """Runs nsteps CFL steps through the C ABI (device computes dt); returns
+    (U as numpy float64, list of (t, dt, ch) per step when record)."""
+    import torch
+    import paper_2510_24175_gb300 as m
+    cfg = m.Config.from_problem(pb, precision=precision)
+    s = m.MHD(cfg)
+    s.set_state(torch.from_numpy(pb.prim()).cuda(), kind=m.MHD_PRIM)
+    hist = []
+    for _ in range(nsteps):
+        s.step()
+        if record or pb.t_end > 0:
+            info = s.step_info()
+            hist.append((info["t"], info["dt"], info["ch"]))
+            if pb.t_end > 0 and info["t"] >= pb.t_end:
+                break
+    U = s.get_state().cpu().numpy()
+    counters = s.counters()
+    return U, hist, counters
+
+
+def sampled_one_step(U0: np.ndarray, pb: Problem, dt: float, ch: float, cells, radius=4):
+    """Oracle value after one RK2 step at the given (k, j, i) cells of a fully
+    periodic grid.  A cell's new value depends only on cells within `radius`
+    (= 2 stages x 2 ghost cells) along each axis, so the oracle advances a
+    (2 radius + 1)^3 box cut out around the cell (periodic wrap) with the
+    global dt and c_h and reads its centre; the box's own boundary treatment
+    cannot reach the centre."""
+    out = np.empty((9, len(cells)))
+    w = 2 * radius + 1
+    sub = Problem(pb.name, (w, w, w), xmin=(0, 0, 0),
+                  xmax=(w * pb.dx[0], w * pb.dx[1], w * pb.dx[2]), gamma=pb.gamma,
+                  limiter=pb.limiter, glm_alpha=pb.glm_alpha, rho_floor=pb.rho_floor,
+                  p_floor=pb.p_floor, bc=(1,) * 6)
+    g = grid_of(sub)
+    nz, ny, nx = U0.shape[1:]
+    for m, (k, j, i) in enumerate(cells):
+        kk = np.arange(k - radius, k + radius + 1) % nz
+        jj = np.arange(j - radius, j + radius + 1) % ny
+        ii = np.arange(i - radius, i + radius + 1) % nx
+        box = U0[:, kk][:, :, jj][:, :, :, ii]
+        r = orc.run(np.ascontiguousarray(box), g, 1, dts=[dt], chs=[ch])
+        out[:, m] = r.U[:, radius, radius, radius]
+    return out

@@ -1,0 +1,193 @@
+"""GPU (through the C ABI) vs the CPU FP64 oracle, element by element.
+
+Tolerances: FP64 state 1e-12 relative L1 per variable (the stated target);
+dt and c_h 1e-13 relative; per-face fluxes 1e-12 relative L1 per component.
+FP32 bulk: relative L1 per variable <= 2e-5 for a few steps of smooth flow
+(FP32 rounding ~6e-8 amplified by the steps; stated and measured bound).
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2510_24175_gb300 import inputs
+from paper_2510_24175_gb300.inputs import Problem
+from parity_util import (RHO, PRS, PSI, grid_of, gpu_run, oracle_run, rel_l1,
+                         sampled_one_step)
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-12
+TOL32 = 2e-5
+
+
+def _torch():
+    import torch
+    return torch
+
+
+# ------------------------------------------------------------- face fluxes --
+@pytest.mark.parametrize("family", [None, "bn0", "bt0", "b0", "vacuum", "equal"])
+@pytest.mark.parametrize("direction", [0, 1, 2])
+def test_flux_batch_fp64(family, direction):
+    torch = _torch()
+    import paper_2510_24175_gb300 as m
+    VL, VR = inputs.random_face_states(100_000, seed=31 + direction, degenerate=family)
+    ch = 1.9
+    ref = orc.interface_flux(VL, VR, direction, ch, 5.0 / 3.0)
+    tl, tr = torch.from_numpy(VL).cuda(), torch.from_numpy(VR).cuda()
+    F = torch.empty_like(tl)
+    m.mhd_flux_batch(tl, tr, F, direction, ch, 5.0 / 3.0)
+    got = F.cpu().numpy()
+    err = np.abs(got - ref).sum(axis=1) / np.maximum(np.abs(ref).sum(axis=1), 1e-300)
+    assert np.all(err <= TOL64), err
+    # worst single face, relative to that face's flux magnitude
+    scale = np.abs(ref).max(axis=0) + np.abs(VL).max(axis=0) + np.abs(VR).max(axis=0)
+    assert np.max(np.abs(got - ref) / scale) < 1e-10
+
+
+def test_flux_batch_fp32():
+    torch = _torch()
+    import paper_2510_24175_gb300 as m
+    VL, VR = inputs.random_face_states(100_000, seed=41)
+    ref = orc.interface_flux(VL, VR, 1, 1.3, 5.0 / 3.0)
+    tl, tr = torch.from_numpy(VL).float().cuda(), torch.from_numpy(VR).float().cuda()
+    F = torch.empty_like(tl)
+    m.mhd_flux_batch(tl, tr, F, 1, 1.3, 5.0 / 3.0)
+    got = F.double().cpu().numpy()
+    err = np.abs(got - ref).sum(axis=1) / np.abs(ref).sum(axis=1)
+    assert np.all(err <= 1e-5), err
+
+
+# --------------------------------------------------------------- full steps --
+def _compare_run(pb, nsteps, tol=TOL64, precision=None):
+    ref = oracle_run(pb, nsteps, t_end=pb.t_end)
+    U, hist, cnt = gpu_run(pb, nsteps, precision=precision, record=True)
+    assert len(hist) == len(ref.dts[ref.dts > 0])
+    for s, (t, dt, ch) in enumerate(hist):
+        assert dt == pytest.approx(ref.dts[s], rel=1e-13 if tol == TOL64 else 1e-5)
+        assert ch == pytest.approx(ref.chs[s], rel=1e-13 if tol == TOL64 else 1e-5)
+    err = rel_l1(U, ref.U)
+    assert np.all(err <= tol), err
+    assert ref.floors == (0, 0)
+    assert cnt["rho_floor"] == 0 and cnt["p_floor"] == 0 and cnt["status"] == 0
+    return err
+
+
+@pytest.mark.parametrize("n", [(40, 20, 12), (32, 16, 8), (37, 9, 5)])
+def test_orszag_tang_3d_ragged(n):
+    pb = inputs.orszag_tang_3d(8).with_n(n)
+    _compare_run(pb, 3)
+
+
+@pytest.mark.parametrize("limiter", [orc.LIM_MINMOD, orc.LIM_MC, orc.LIM_FLAT])
+def test_random_smooth_outflow(limiter):
+    pb = Problem("random_smooth", (35, 18, 10), seed=4, limiter=limiter, bc=(1,) * 6)
+    _compare_run(pb, 3)
+
+
+def test_random_smooth_mixed_bc_psi():
+    pb = Problem("random_smooth", (33, 17, 9), seed=6, bc=(0, 0, 1, 1, 0, 0),
+                 params={"psi_amp": 3.0})
+    _compare_run(pb, 4)
+
+
+def test_orszag_tang_2d():
+    pb = inputs.orszag_tang_2d(72, steps=10)
+    _compare_run(pb, 10)
+
+
+def test_brio_wu_to_t_end():
+    pb = inputs.brio_wu(1024)
+    ref = oracle_run(pb, 100000, t_end=pb.t_end)
+    U, hist, cnt = gpu_run(pb, 100000)
+    assert hist[-1][0] == pytest.approx(0.1, abs=1e-15)
+    assert len(hist) == int(np.count_nonzero(ref.dts))
+    err = rel_l1(U, ref.U)
+    assert np.all(err <= TOL64), err
+
+
+def test_tiny_grids():
+    for n in [(2, 1, 1), (3, 2, 1), (4, 4, 2), (5, 3, 3)]:
+        pb = Problem("random_smooth", n, seed=9)
+        _compare_run(pb, 2)
+
+
+def test_conserved_sums_and_dt_match_oracle():
+    import paper_2510_24175_gb300 as m
+    torch = _torch()
+    pb = Problem("random_smooth", (48, 20, 14), seed=12)
+    g = grid_of(pb)
+    U0 = orc.prim_to_cons(pb.prim(), pb.gamma)
+    s = m.MHD(m.Config.from_problem(pb))
+    s.set_state(torch.from_numpy(U0).cuda())
+    dt, ch = s.dt()
+    odt, och = orc.cfl_dt(U0, g)
+    assert dt == pytest.approx(odt, rel=1e-14) and ch == pytest.approx(och, rel=1e-14)
+    np.testing.assert_allclose(s.conserved_sums(), orc.conserved_sums(U0, g), rtol=1e-13,
+                               atol=1e-13)
+    # host-side set/get round trip is bitwise in FP64
+    s.set_state(U0)
+    back = np.empty_like(U0)
+    s.get_state(back)
+    np.testing.assert_array_equal(back, U0)
+
+
+# ------------------------------------------------------------------- FP32 --
+def test_fp32_orszag_tang_3d():
+    pb = inputs.orszag_tang_3d(8).with_n((40, 24, 16))
+    _compare_run(pb, 3, tol=TOL32, precision=1)
+
+
+def test_fp32_turbulent_small():
+    pb = inputs.turbulent_box(32, steps=3)
+    _compare_run(pb, 3, tol=TOL32, precision=1)
+
+
+# --------------------------------------------------- full-size workload --
+def test_orszag_tang_256_one_step_sampled():
+    """The benchmark workload (3-D OT, 256^3, FP64) in the benchmark's launch
+    configuration: one step on the GPU, the oracle's value at 48 sampled cells
+    (including faces, edges and corners of the periodic box)."""
+    torch = _torch()
+    import paper_2510_24175_gb300 as m
+    pb = inputs.orszag_tang_3d(256)
+    U0 = orc.prim_to_cons(pb.prim(), pb.gamma)
+    dt, ch = orc.cfl_dt(U0, grid_of(pb))
+    s = m.MHD(m.Config.from_problem(pb))
+    s.set_state(torch.from_numpy(U0).cuda())
+    s.step()
+    info = s.step_info()
+    assert info["dt"] == pytest.approx(dt, rel=1e-13)
+    U1 = s.get_state().cpu().numpy()
+    rng = np.random.default_rng(5)
+    cells = [tuple(rng.integers(0, 256, 3)) for _ in range(40)]
+    cells += [(0, 0, 0), (255, 255, 255), (0, 255, 0), (255, 0, 31), (128, 7, 255),
+              (31, 32, 33), (8, 255, 200), (100, 0, 0)]
+    ref = sampled_one_step(U0, pb, dt, ch, cells)
+    got = np.stack([U1[:, k, j, i] for (k, j, i) in cells], axis=1)
+    scale = np.abs(U0).reshape(9, -1).max(axis=1)[:, None]
+    scale[PSI] = scale[RHO]
+    assert np.max(np.abs(got - ref) / scale) < 1e-13
+
+
+def test_orszag_tang_256_twenty_steps_properties():
+    """20 steps of the benchmark workload: point symmetry of the OT vortex
+    and conservation hold at full size."""
+    import paper_2510_24175_gb300 as m
+    torch = _torch()
+    pb = inputs.orszag_tang_3d(256)
+    s = m.MHD(m.Config.from_problem(pb))
+    s.set_state(torch.from_numpy(pb.prim()).cuda(), kind=m.MHD_PRIM)
+    s0 = s.conserved_sums()
+    for _ in range(20):
+        s.step()
+    s.step_info()
+    s1 = s.conserved_sums()
+    # rho, m, E, B: conserved to round-off (B_x etc. sum to ~0 by symmetry)
+    assert np.all(np.abs(s1 - s0) <= 1e-12 * (np.abs(s0).max() + 1.0))
+    U = s.get_state()
+    inv = torch.flip(U, dims=(1, 2, 3))
+    sym = torch.tensor([1, -1, -1, -1, -1, -1, -1, 1, 1.0], device=U.device,
+                       dtype=U.dtype).view(9, 1, 1, 1)
+    scale = U.abs().amax(dim=(1, 2, 3), keepdim=True)
+    assert float(((U - sym * inv).abs() / scale).max()) < 1e-11
+    assert s.counters() == {"rho_floor": 0, "p_floor": 0, "status": 0}
