@@ -2,8 +2,9 @@
 
 Tolerances: FP64 state 1e-12 relative L1 per variable (the stated target);
 dt and c_h 1e-13 relative; per-face fluxes 1e-12 relative L1 per component.
-FP32 bulk: relative L1 per variable <= 2e-5 for a few steps of smooth flow
-(FP32 rounding ~6e-8 amplified by the steps; stated and measured bound).
+FP32 bulk: relative L1 per variable <= 2e-5 for a few steps of smooth flow,
+with the norm's floor at 0.1 ||rho||_1 (FP32 rounding ~6e-8 amplified by the
+steps; stated and measured bound).
 """
 import numpy as np
 import pytest
@@ -65,7 +66,7 @@ def _compare_run(pb, nsteps, tol=TOL64, precision=None):
     for s, (t, dt, ch) in enumerate(hist):
         assert dt == pytest.approx(ref.dts[s], rel=1e-13 if tol == TOL64 else 1e-5)
         assert ch == pytest.approx(ref.chs[s], rel=1e-13 if tol == TOL64 else 1e-5)
-    err = rel_l1(U, ref.U)
+    err = rel_l1(U, ref.U, floor=1e-3 if tol == TOL64 else 0.1)
     assert np.all(err <= tol), err
     assert ref.floors == (0, 0)
     assert cnt["rho_floor"] == 0 and cnt["p_floor"] == 0 and cnt["status"] == 0
@@ -95,14 +96,47 @@ def test_orszag_tang_2d():
     _compare_run(pb, 10)
 
 
-def test_brio_wu_to_t_end():
+@pytest.mark.parametrize("t_end", [0.005, 0.01])
+def test_brio_wu_short_times(t_end):
+    """Brio-Wu (1024 cells, outflow, minmod) at 1e-12 relative L1 while the
+    problem's own round-off amplification is small (oracle vs oracle with
+    1e-16 relative input noise: 2e-14 at t = 0.005, 1e-13 at t = 0.01)."""
     pb = inputs.brio_wu(1024)
-    ref = oracle_run(pb, 100000, t_end=pb.t_end)
+    pb.t_end = t_end
+    ref = oracle_run(pb, 100000, t_end=t_end)
+    U, hist, cnt = gpu_run(pb, 100000)
+    assert hist[-1][0] == pytest.approx(t_end, abs=1e-15)
+    assert len(hist) == int(np.count_nonzero(ref.dts))
+    err = rel_l1(U, ref.U)
+    assert np.all(err <= TOL64), err
+    assert cnt == {"rho_floor": 0, "p_floor": 0, "status": 0}
+
+
+def test_brio_wu_to_t_end_within_conditioning():
+    """Brio-Wu to t = 0.1 amplifies round-off by ~1e9 (the compound wave):
+    the oracle itself moves by ~6e-7 relative L1 when its input is perturbed
+    by 1e-16.  The GPU must agree with the oracle within 10x that measured
+    conditioning, and must satisfy the closed-form boundary-flux balance
+    (mass, energy, By conserved; x-momentum +0.09, y-momentum -0.15)."""
+    pb = inputs.brio_wu(1024)
+    g = grid_of(pb)
+    U0 = orc.prim_to_cons(pb.prim(), pb.gamma)
+    ref = orc.run(U0, g, 100000, t_end=pb.t_end)
+    rng = np.random.default_rng(0)
+    noisy = orc.run(U0 * (1 + 1e-16 * rng.standard_normal(U0.shape)), g, 100000,
+                    t_end=pb.t_end)
+    cond = rel_l1(noisy.U, ref.U).max()
     U, hist, cnt = gpu_run(pb, 100000)
     assert hist[-1][0] == pytest.approx(0.1, abs=1e-15)
     assert len(hist) == int(np.count_nonzero(ref.dts))
     err = rel_l1(U, ref.U)
-    assert np.all(err <= TOL64), err
+    assert err.max() <= 10 * cond, (err, cond)
+    s0, s1 = orc.conserved_sums(U0, g), orc.conserved_sums(U, g)
+    for q in (0, 3, 4, 5, 6, 7):
+        assert abs(s1[q] - s0[q]) < 1e-12, q
+    assert s1[1] - s0[1] == pytest.approx(0.9 * 0.1, rel=1e-10)
+    assert s1[2] - s0[2] == pytest.approx(-1.5 * 0.1, rel=1e-10)
+    assert cnt == {"rho_floor": 0, "p_floor": 0, "status": 0}
 
 
 def test_tiny_grids():
@@ -165,7 +199,7 @@ def test_orszag_tang_256_one_step_sampled():
     ref = sampled_one_step(U0, pb, dt, ch, cells)
     got = np.stack([U1[:, k, j, i] for (k, j, i) in cells], axis=1)
     scale = np.abs(U0).reshape(9, -1).max(axis=1)[:, None]
-    scale[PSI] = scale[RHO]
+    scale = np.maximum(scale, scale[RHO])  # B_z and psi start at zero
     assert np.max(np.abs(got - ref) / scale) < 1e-13
 
 
@@ -189,5 +223,6 @@ def test_orszag_tang_256_twenty_steps_properties():
     sym = torch.tensor([1, -1, -1, -1, -1, -1, -1, 1, 1.0], device=U.device,
                        dtype=U.dtype).view(9, 1, 1, 1)
     scale = U.abs().amax(dim=(1, 2, 3), keepdim=True)
+    scale = torch.maximum(scale, 1e-3 * scale[RHO])  # B_z and psi are near zero
     assert float(((U - sym * inv).abs() / scale).max()) < 1e-11
     assert s.counters() == {"rho_floor": 0, "p_floor": 0, "status": 0}
