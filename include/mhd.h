@@ -157,6 +157,25 @@ int mhd_adjoint_step(mhd_ctx* ctx, const double* U_n, const double* lam_np1, dou
 int mhd_profile_enable(mhd_ctx* ctx, int enable);
 int mhd_profile_read(mhd_ctx* ctx, long long counts[4], double ms[4]);
 
+/* Conservation sums for callers that can't allocate device memory: a host
+ * application whose GPU memory is owned by another allocator, a code that
+ * forbids allocations once its time loop runs, or a hook running while the
+ * caller captures a stream (cudaMalloc is not allowed there in the default
+ * capture mode).  The paper has no counterpart; this is a library service.
+ * Same result as mhd_conserved_sums() (up to the summation order) for a state
+ * U held by the caller in device memory: float64 (cfg->precision = MHD_FP64)
+ * or float32 (MHD_FP32), conservative, [9][nz][ny][nx]; out: 8 host doubles.
+ * Needs no context and no workspace and allocates nothing: the scratch is a
+ * fixed 1 MiB device array inside the library (16384 partial sums), which
+ * every GPU that loads the library holds until the process exits.  Grids of
+ * more than 16384 * 32768 cells are rejected with MHD_ERR_NOMEM.  The first
+ * call on each device looks up that array's device address; make that first
+ * call before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (other streams, other host threads) race.  Enqueues on
+ * stream and synchronises it. */
+int mhd_conserved_sums_noalloc(const mhd_config* cfg, const void* U, double out[8],
+                               void* stream);
+
 /* Message of the last failing call on ctx (never NULL). */
 const char* mhd_last_error(const mhd_ctx* ctx);
 

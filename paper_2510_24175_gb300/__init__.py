@@ -35,7 +35,8 @@ MHD_FLAG_ADJOINT = 1
 EXPORTED = ["mhd_config_default", "mhd_workspace_bytes", "mhd_create", "mhd_set_stream",
             "mhd_set_state", "mhd_get_state", "mhd_dt", "mhd_step", "mhd_step_info",
             "mhd_counters", "mhd_conserved_sums", "mhd_flux_batch", "mhd_adjoint_step",
-            "mhd_profile_enable", "mhd_profile_read", "mhd_last_error", "mhd_destroy"]
+            "mhd_profile_enable", "mhd_profile_read", "mhd_conserved_sums_noalloc",
+            "mhd_last_error", "mhd_destroy"]
 
 
 class MHDError(RuntimeError):
@@ -83,6 +84,7 @@ def lib():
         L.mhd_adjoint_step.argtypes = [vp, vp, vp, vp, d, d]
         L.mhd_profile_enable.argtypes = [vp, i]
         L.mhd_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), dp]
+        L.mhd_conserved_sums_noalloc.argtypes = [cfgp, vp, dp, vp]
         L.mhd_last_error.argtypes = [vp]
         L.mhd_last_error.restype = ctypes.c_char_p
         L.mhd_destroy.argtypes = [vp]
@@ -162,6 +164,16 @@ def mhd_adjoint_step(ctx, U_n, lam_np1, lam_n, dt: float, ch: float):
 
 def mhd_destroy(ctx):
     _check(lib().mhd_destroy(ctx), what="mhd_destroy")
+
+
+def mhd_conserved_sums_noalloc(cfg: mhd_config, U) -> np.ndarray:
+    """Conservation sums of a caller-held CUDA state tensor (float64 or
+    float32 to match cfg.precision) without a context or workspace; the
+    library's fixed internal scratch is used and nothing is allocated."""
+    out = (ctypes.c_double * 8)()
+    _check(lib().mhd_conserved_sums_noalloc(ctypes.byref(cfg), _ptr(U), out, _stream_ptr()),
+           what="mhd_conserved_sums_noalloc")
+    return np.array(out[:])
 
 
 def mhd_flux_batch(VL, VR, F, direction: int, ch: float, gamma: float):
