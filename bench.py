@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -314,6 +315,49 @@ def main():
         del s32
         torch.cuda.empty_cache()
 
+    # ---- adjoint / forward step-time ratio: 2-D Orszag-Tang 512^2 FP64 ------
+    adjoint = None
+    if not args.no_adjoint:
+        from paper_2510_24175_gb300.adjoint import rollout_solver
+        pba = inputs.orszag_tang_2d(512)
+        sa = rollout_solver(pba)
+        sa.set_state(torch.from_numpy(pba.prim()).cuda(), kind=m.MHD_PRIM)
+        for _ in range(W):
+            sa.step()
+        info_a = sa.step_info()
+        dt_a, ch_a = info_a["dt"], info_a["ch"]
+        Ka = max(K, 10)
+        stream = torch.cuda.current_stream()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(Ka):
+            sa.step(dt_a, ch_a)
+        ev[1].record(stream)
+        Ua = sa.get_state()
+        lam = torch.randn_like(Ua)
+        out = torch.empty_like(Ua)
+        for _ in range(W):
+            sa.adjoint_step(Ua, lam, out, dt_a, ch_a)
+        torch.cuda.synchronize()
+        ev[2].record(stream)
+        for i in range(Ka):
+            if i % 2 == 0:
+                sa.adjoint_step(Ua, lam, out, dt_a, ch_a)
+            else:
+                sa.adjoint_step(Ua, out, lam, dt_a, ch_a)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        ms_f = ev[0].elapsed_time(ev[1]) / Ka
+        ms_a = ev[2].elapsed_time(ev[3]) / Ka
+        adjoint = {"workload": "orszag_tang_2d_512^2_fp64", "forward_ms_per_step": ms_f,
+                   "adjoint_ms_per_step": ms_a,
+                   "adjoint_over_forward": (ms_a + ms_f) / ms_f,
+                   "note": "ratio = (adjoint step + its forward recompute) / forward step"}
+        launches += Ka * 3 + Ka * 7
+        del sa
+        torch.cuda.empty_cache()
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -341,6 +385,7 @@ def main():
         "e2e": e2e,
         "fp32": fp32,
         "fp32_over_fp64": (fp32["value"] / value) if fp32 else None,
+        "adjoint": adjoint,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))

@@ -1,0 +1,80 @@
+"""Differentiable RK2 rollouts: a torch.autograd.Function over the C ABI.
+
+forward: advances the state nsteps CFL steps with mhd_step, keeping a copy of
+the state every k steps (checkpoints) and recording each step's dt and c_h.
+backward: for each k-step segment, last first, recomputes the segment's
+states from its checkpoint with the recorded dt and c_h (mhd_step with
+explicit dt, ch: bitwise the same states), then applies mhd_adjoint_step
+(the discrete adjoint of one step with dt and c_h frozen) from the last step
+of the segment to the first.  Every step of the method runs in the CUDA
+library; torch holds the tensors.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import MHD, MHD_FLAG_ADJOINT, Config
+
+
+class MHDRollout(torch.autograd.Function):
+    """U_N = MHDRollout.apply(U0, solver, nsteps, k).
+
+    U0: conservative state, float64 CUDA tensor (9, nz, ny, nx); solver: an
+    ``MHD`` created with ``MHD_FLAG_ADJOINT``; k: checkpoint interval."""
+
+    @staticmethod
+    def forward(ctx, U0, solver: MHD, nsteps: int, k: int):
+        assert solver.config.flags & MHD_FLAG_ADJOINT, "solver needs MHD_FLAG_ADJOINT"
+        solver.set_state(U0.detach().contiguous())
+        ckpts, dts, chs = [], [], []
+        for n in range(nsteps):
+            if n % k == 0:
+                ckpts.append(solver.get_state())
+            solver.step()
+            info = solver.step_info()
+            dts.append(info["dt"])
+            chs.append(info["ch"])
+        UN = solver.get_state()
+        ctx.solver, ctx.nsteps, ctx.k = solver, nsteps, k
+        ctx.ckpts, ctx.dts, ctx.chs = ckpts, dts, chs
+        return UN
+
+    @staticmethod
+    def backward(ctx, gUN):
+        solver, nsteps, k = ctx.solver, ctx.nsteps, ctx.k
+        lam = gUN.contiguous().clone()
+        nseg = len(ctx.ckpts)
+        for s in reversed(range(nseg)):
+            n0 = s * k
+            n1 = min(n0 + k, nsteps)
+            solver.set_state(ctx.ckpts[s])
+            states = [ctx.ckpts[s]]
+            for n in range(n0, n1 - 1):
+                solver.step(ctx.dts[n], ctx.chs[n])
+                states.append(solver.get_state())
+            for i in reversed(range(n1 - n0)):
+                n = n0 + i
+                out = torch.empty_like(lam)
+                solver.adjoint_step(states[i], lam, out, ctx.dts[n], ctx.chs[n])
+                lam = out
+        return lam, None, None, None
+
+
+def rollout_solver(problem) -> MHD:
+    """An adjoint-capable FP64 solver for a Problem."""
+    return MHD(Config.from_problem(problem, precision=0, flags=MHD_FLAG_ADJOINT))
+
+
+def kinetic_energy(U: torch.Tensor, cell_volume: float) -> torch.Tensor:
+    """J = sum over cells of |m|^2 / (2 rho) times the cell volume."""
+    return 0.5 * ((U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0]).sum() * cell_volume
+
+
+def prim_to_cons_torch(V: torch.Tensor, gamma: float) -> torch.Tensor:
+    """Differentiable primitive -> conservative map for parameterising
+    initial conditions in user code (e.g. a velocity perturbation)."""
+    rho = V[0]
+    v2 = V[1] ** 2 + V[2] ** 2 + V[3] ** 2
+    b2 = V[4] ** 2 + V[5] ** 2 + V[6] ** 2
+    E = V[7] / (gamma - 1.0) + 0.5 * rho * v2 + 0.5 * b2
+    return torch.stack([rho, rho * V[1], rho * V[2], rho * V[3], V[4], V[5], V[6], E, V[8]])

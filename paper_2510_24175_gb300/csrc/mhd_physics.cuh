@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#define MHD_HD __host__ __device__ __forceinline__
+
 namespace mhd {
 
 enum { kRHO = 0, kVX = 1, kVY = 2, kVZ = 3, kBX = 4, kBY = 5, kBZ = 6, kPRS = 7, kPSI = 8,
@@ -37,22 +39,36 @@ struct Phys {
   double gamma_d, rho_floor_d, p_floor_d;  // FP64 copies for the floor branch
 };
 
-__device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double tabs(double x) { return fabs(x); }
-__device__ __forceinline__ float tabs(float x) { return fabsf(x); }
-__device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
-__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
-__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
-__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
+// Correctly rounded reciprocal (the host build, used only by host-side unit
+// harnesses, divides).
+MHD_HD double rcp(double x) {
+#ifdef __CUDA_ARCH__
+  return __drcp_rn(x);
+#else
+  return 1.0 / x;
+#endif
+}
+MHD_HD float rcp(float x) {
+#ifdef __CUDA_ARCH__
+  return __frcp_rn(x);
+#else
+  return 1.0f / x;
+#endif
+}
+MHD_HD double tsqrt(double x) { return sqrt(x); }
+MHD_HD float tsqrt(float x) { return sqrtf(x); }
+MHD_HD double tabs(double x) { return fabs(x); }
+MHD_HD float tabs(float x) { return fabsf(x); }
+MHD_HD double tmin(double a, double b) { return fmin(a, b); }
+MHD_HD float tmin(float a, float b) { return fminf(a, b); }
+MHD_HD double tmax(double a, double b) { return fmax(a, b); }
+MHD_HD float tmax(float a, float b) { return fmaxf(a, b); }
 
 // Pressure floor.  FP64: plain comparison.  FP32: when the FP32 pressure is
 // within the cancellation-dominated range (internal energy below 1e-3 of the
 // total, or below the floor) p is recomputed in FP64 from the promoted
 // conservative inputs and the floor decision is taken in FP64.
-__device__ __forceinline__ double pressure_floor(double p, const double u[kNV], double rho,
+MHD_HD double pressure_floor(double p, const double u[kNV], double rho,
                                                  const Phys<double>& ph, unsigned& flags) {
   if (p < ph.p_floor) {
     flags |= kFloorP;
@@ -60,7 +76,7 @@ __device__ __forceinline__ double pressure_floor(double p, const double u[kNV], 
   }
   return p;
 }
-__device__ __forceinline__ float pressure_floor(float p, const float u[kNV], float rho,
+MHD_HD float pressure_floor(float p, const float u[kNV], float rho,
                                                 const Phys<float>& ph, unsigned& flags) {
   if (p < ph.p_floor || p < 1e-3f * ph.gm1 * u[kPRS]) {
     double r = rho;
@@ -79,7 +95,7 @@ __device__ __forceinline__ float pressure_floor(float p, const float u[kNV], flo
 // Conservative -> primitive (step 2 of the stage).  Floors by replacement,
 // density first, then pressure; activations are flagged.
 template <class T>
-__device__ __forceinline__ void cons_to_prim(const T u[kNV], T v[kNV], const Phys<T>& ph,
+MHD_HD void cons_to_prim(const T u[kNV], T v[kNV], const Phys<T>& ph,
                                              unsigned& flags) {
   T rho = u[kRHO];
   if (rho < ph.rho_floor) {
@@ -105,7 +121,7 @@ __device__ __forceinline__ void cons_to_prim(const T u[kNV], T v[kNV], const Phy
 
 // Primitive -> conservative.
 template <class T>
-__device__ __forceinline__ void prim_to_cons(const T v[kNV], T u[kNV], const Phys<T>& ph) {
+MHD_HD void prim_to_cons(const T v[kNV], T u[kNV], const Phys<T>& ph) {
   const T rho = v[kRHO];
   const T v2 = v[kVX] * v[kVX] + v[kVY] * v[kVY] + v[kVZ] * v[kVZ];
   const T b2 = v[kBX] * v[kBX] + v[kBY] * v[kBY] + v[kBZ] * v[kBZ];
@@ -123,7 +139,7 @@ __device__ __forceinline__ void prim_to_cons(const T v[kNV], T u[kNV], const Phy
 // Fast magnetosonic speed from 1/rho, gamma p, |B|^2 and B_n^2:
 // c_f^2 = (a + sqrt(a^2 - 4 gamma p B_n^2 / rho^2)) / 2, a = (gamma p + |B|^2)/rho.
 template <class T>
-__device__ __forceinline__ T fast_speed(T rho_i, T gp, T b2, T bn2) {
+MHD_HD T fast_speed(T rho_i, T gp, T b2, T bn2) {
   const T a = (gp + b2) * rho_i;
   T disc = a * a - T(4) * gp * bn2 * (rho_i * rho_i);
   disc = tmax(disc, T(0));
@@ -132,7 +148,7 @@ __device__ __forceinline__ T fast_speed(T rho_i, T gp, T b2, T bn2) {
 
 // max over active directions of |v_d| + c_f,d for one conservative cell.
 template <class T>
-__device__ __forceinline__ T cell_max_speed(const T u[kNV], const Phys<T>& ph, int ndim,
+MHD_HD T cell_max_speed(const T u[kNV], const Phys<T>& ph, int ndim,
                                             unsigned& flags) {
   T v[kNV];
   cons_to_prim(u, v, ph, flags);
@@ -150,7 +166,7 @@ __device__ __forceinline__ T cell_max_speed(const T u[kNV], const Phys<T>& ph, i
 // Limited slope (van Leer 1977): 0 when the one-sided differences disagree in
 // sign; minmod = smaller magnitude; MC = min(2|dm|, 2|dp|, |dm+dp|/2).
 template <class T>
-__device__ __forceinline__ T limited_slope(T dm, T dp, int lim) {
+MHD_HD T limited_slope(T dm, T dp, int lim) {
   if (lim == kLimFlat || !(dm * dp > T(0))) return T(0);
   const T am = tabs(dm), ap = tabs(dp);
   T mag = tmin(am, ap);
@@ -163,7 +179,7 @@ __device__ __forceinline__ T limited_slope(T dm, T dp, int lim) {
 // j; variables are vstride apart.  Writes the left state (from q1) and the
 // right state (from q2).
 template <class T>
-__device__ __forceinline__ void plm_face_pair(const T* c0, const T* c1, const T* c2,
+MHD_HD void plm_face_pair(const T* c0, const T* c1, const T* c2,
                                               const T* c3, int vstride, int lim, T vl[kNV],
                                               T vr[kNV]) {
   T s1[kNV], s2[kNV];
@@ -190,7 +206,7 @@ __device__ __forceinline__ void plm_face_pair(const T* c0, const T* c1, const T*
 
 // Picks component (dir + j) % 3 of a 3-vector given as scalars.
 template <class T>
-__device__ __forceinline__ T rot3(int dir, int j, T a, T b, T c) {
+MHD_HD T rot3(int dir, int j, T a, T b, T c) {
   const int m = (dir + j) % 3;
   return m == 0 ? a : (m == 1 ? b : c);
 }
@@ -199,7 +215,7 @@ __device__ __forceinline__ T rot3(int dir, int j, T a, T b, T c) {
 // states vl, vr.  ch: cleaning speed; half_chi = 0.5 / ch.  F in conservative
 // ordering.
 template <class T>
-__device__ __forceinline__ void glm_hlld_flux(const T vl[kNV], const T vr[kNV], int dir, T ch,
+MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], int dir, T ch,
                                               T half_chi, const Phys<T>& ph, T F[kNV]) {
   const T half = T(0.5);
   // rotate: u normal, (v, w) tangential in cyclic order; by, bz likewise
