@@ -525,29 +525,28 @@ template <class T>
 MHD_HD T limited_slope_d(T dm, T dp, int lim, T& ddm, T& ddp) {
   ddm = T(0);
   ddp = T(0);
-  if (lim == kLimFlat || !(dm * dp > T(0))) return T(0);
+  // the zero branch is decided exactly as in the forward limiter
+  const T s = limited_slope(dm, dp, lim);
+  if (s == T(0)) return s;
   const T am = tabs(dm), ap = tabs(dp);
   // minmod: the smaller magnitude (dm on ties, as min(a, b) picks a)
   const bool m_is_dm = !(ap < am);
-  T mag = m_is_dm ? am : ap;
-  T gdm = m_is_dm ? T(1) : T(0), gdp = m_is_dm ? T(0) : T(1);  // d|s|/d|.|
+  T gdm = m_is_dm ? T(1) : T(0), gdp = m_is_dm ? T(0) : T(1);
   if (lim == kLimMC) {
-    const T two = T(2) * mag;
-    const T cen = T(0.5) * tabs(dm + dp);
+    const T two = T(2) * (m_is_dm ? am : ap);
+    const T cen = T(0.5) * (am + ap);  // = |dm + dp| / 2 for equal signs
     if (cen < two) {  // central slope selected
-      mag = cen;
       gdm = T(0.5);
       gdp = T(0.5);
     } else {
-      mag = two;
       gdm *= T(2);
       gdp *= T(2);
     }
   }
-  // sign(s) = sign(dm) = sign(dp); d s / d dm = gdm (signs cancel)
+  // sign(s) = sign(dm) = sign(dp), so d s / d dm = gdm (signs cancel)
   ddm = gdm;
   ddp = gdp;
-  return dm > T(0) ? mag : -mag;
+  return s;
 }
 
 // Reverse of cons_to_prim (floors inactive: a floored value has zero

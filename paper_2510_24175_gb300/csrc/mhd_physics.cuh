@@ -18,6 +18,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #define MHD_HD __host__ __device__ __forceinline__
 
@@ -55,6 +56,8 @@ MHD_HD float rcp(float x) {
   return 1.0f / x;
 #endif
 }
+MHD_HD double trsqrt(double x) { return rsqrt(x); }
+MHD_HD float trsqrt(float x) { return rsqrtf(x); }
 MHD_HD double tsqrt(double x) { return sqrt(x); }
 MHD_HD float tsqrt(float x) { return sqrtf(x); }
 MHD_HD double tabs(double x) { return fabs(x); }
@@ -163,6 +166,27 @@ MHD_HD T cell_max_speed(const T u[kNV], const Phys<T>& ph, int ndim,
   return lam;
 }
 
+// Bit-pattern helpers (the host build, used only by host-side harnesses,
+// goes through memcpy).
+MHD_HD long long dbits(double x) {
+#ifdef __CUDA_ARCH__
+  return __double_as_longlong(x);
+#else
+  long long b;
+  memcpy(&b, &x, sizeof(b));
+  return b;
+#endif
+}
+MHD_HD double bits2d(long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double(b);
+#else
+  double x;
+  memcpy(&x, &b, sizeof(x));
+  return x;
+#endif
+}
+
 // Limited slope (van Leer 1977): 0 when the one-sided differences disagree in
 // sign; minmod = smaller magnitude; MC = min(2|dm|, 2|dp|, |dm+dp|/2).
 template <class T>
@@ -172,6 +196,27 @@ MHD_HD T limited_slope(T dm, T dp, int lim) {
   T mag = tmin(am, ap);
   if (lim == kLimMC) mag = tmin(T(2) * mag, T(0.5) * tabs(dm + dp));
   return dm > T(0) ? mag : -mag;
+}
+
+// FP64 specialisation with the same result: the sign and zero tests, |.|,
+// the magnitude comparisons (non-negative doubles order like their bit
+// patterns) and the sign transfer run on the integer pipe; only the additions
+// and the halving use the (scarce) FP64 pipe.  For equal signs
+// |dm + dp| = |dm| + |dp| exactly, so the central slope is (|dm|+|dp|)/2.
+template <>
+MHD_HD double limited_slope<double>(double dm, double dp, int lim) {
+  const long long a = dbits(dm), b = dbits(dp);
+  const long long mask = 0x7fffffffffffffffll;
+  const long long am = a & mask, bm = b & mask;
+  if (lim == kLimFlat || (a ^ b) < 0 || am == 0 || bm == 0) return 0.0;
+  long long mb = am < bm ? am : bm;
+  if (lim == kLimMC) {
+    const double mag = bits2d(mb);
+    const long long two = dbits(mag + mag);
+    const long long cen = dbits(0.5 * (bits2d(am) + bits2d(bm)));
+    mb = cen < two ? cen : two;
+  }
+  return bits2d(mb | (a & ~mask));
 }
 
 // PLM face states around one interface from four consecutive cells q0..q3
@@ -244,8 +289,10 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], int dir, T ch,
   const T ptL = pL + half * b2L, ptR = pR + half * b2R;
   const T eL = pL * ph.gm1i + half * rL * (uL * uL + vL * vL + wL * wL) + half * b2L;
   const T eR = pR * ph.gm1i + half * rR * (uR * uR + vR * vR + wR * wR) + half * b2R;
-  const T cfL = fast_speed(rcp(rL), ph.gamma * pL, b2L, bx2);
-  const T cfR = fast_speed(rcp(rR), ph.gamma * pR, b2R, bx2);
+  // 1/rho of both sides from one reciprocal
+  const T qr = rcp(rL * rR);
+  const T cfL = fast_speed(rR * qr, ph.gamma * pL, b2L, bx2);
+  const T cfR = fast_speed(rL * qr, ph.gamma * pR, b2R, bx2);
 
   // wave-speed estimates (MK05 Eq. 67), contact speed and total pressure
   const T cmax = tmax(cfL, cfR);
@@ -257,47 +304,51 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], int dir, T ch,
   const T pts = (dR * ptL - dL * ptR + dL * dR * (uR - uL)) * Di;
 
   // single-star states (MK05 Eqs. 43-48), degenerate when
-  // |rho (S-u)(S-S_M) - Bx^2| < 1e-8 p_t*
+  // |rho (S-u)(S-S_M) - Bx^2| < 1e-8 p_t*; paired reciprocals of S-S_M and
+  // of the two denominators
+  const T smL = SL - SM, smR = SR - SM;
+  const T qs = rcp(smL * smR);
+  const T smiL = smR * qs, smiR = smL * qs;
+  const T denL = dL * smL - bx2, denR = dR * smR - bx2;
+  const bool degL = tabs(denL) < T(1e-8) * pts;
+  const bool degR = tabs(denR) < T(1e-8) * pts;
+  const T dnL = degL ? T(1) : denL, dnR = degR ? T(1) : denR;
+  const T qd = rcp(dnL * dnR);
+  const T deniL = dnR * qd, deniR = dnL * qd;
   T rsL, vsL, wsL, bysL, bzsL, esL, vbsL;
   T rsR, vsR, wsR, bysR, bzsR, esR, vbsR;
   {
-    const T sm = SL - SM, smi = rcp(sm);
-    rsL = dL * smi;
-    const T den = dL * sm - bx2;
-    const bool deg = tabs(den) < T(1e-8) * pts;
-    const T deni = rcp(deg ? T(1) : den);
-    const T fv = bx * (SM - uL) * deni;
-    const T fb = (dL * (SL - uL) - bx2) * deni;
-    vsL = deg ? vL : vL - byL * fv;
-    wsL = deg ? wL : wL - bzL * fv;
-    bysL = deg ? byL : byL * fb;
-    bzsL = deg ? bzL : bzL * fb;
+    rsL = dL * smiL;
+    const T fv = bx * (SM - uL) * deniL;
+    const T fb = (dL * (SL - uL) - bx2) * deniL;
+    vsL = degL ? vL : vL - byL * fv;
+    wsL = degL ? wL : wL - bzL * fv;
+    bysL = degL ? byL : byL * fb;
+    bzsL = degL ? bzL : bzL * fb;
     const T vb = uL * bx + vL * byL + wL * bzL;
     vbsL = SM * bx + vsL * bysL + wsL * bzsL;
-    esL = ((SL - uL) * eL - ptL * uL + pts * SM + bx * (vb - vbsL)) * smi;
+    esL = ((SL - uL) * eL - ptL * uL + pts * SM + bx * (vb - vbsL)) * smiL;
   }
   {
-    const T sm = SR - SM, smi = rcp(sm);
-    rsR = dR * smi;
-    const T den = dR * sm - bx2;
-    const bool deg = tabs(den) < T(1e-8) * pts;
-    const T deni = rcp(deg ? T(1) : den);
-    const T fv = bx * (SM - uR) * deni;
-    const T fb = (dR * (SR - uR) - bx2) * deni;
-    vsR = deg ? vR : vR - byR * fv;
-    wsR = deg ? wR : wR - bzR * fv;
-    bysR = deg ? byR : byR * fb;
-    bzsR = deg ? bzR : bzR * fb;
+    rsR = dR * smiR;
+    const T fv = bx * (SM - uR) * deniR;
+    const T fb = (dR * (SR - uR) - bx2) * deniR;
+    vsR = degR ? vR : vR - byR * fv;
+    wsR = degR ? wR : wR - bzR * fv;
+    bysR = degR ? byR : byR * fb;
+    bzsR = degR ? bzR : bzR * fb;
     const T vb = uR * bx + vR * byR + wR * bzR;
     vbsR = SM * bx + vsR * bysR + wsR * bzsR;
-    esR = ((SR - uR) * eR - ptR * uR + pts * SM + bx * (vb - vbsR)) * smi;
+    esR = ((SR - uR) * eR - ptR * uR + pts * SM + bx * (vb - vbsR)) * smiR;
   }
 
-  // Alfven waves (MK05 Eq. 51) and double-star states (Eqs. 59-63)
-  const T sqL = tsqrt(rsL), sqR = tsqrt(rsR);
+  // Alfven waves (MK05 Eq. 51) and double-star states (Eqs. 59-63);
+  // 1/sqrt(rho*) by rsqrt, sqrt(rho*) = rho* / sqrt(rho*)
+  const T iqL = trsqrt(rsL), iqR = trsqrt(rsR);
+  const T sqL = rsL * iqL, sqR = rsR * iqR;
   const T abx = tabs(bx);
-  const T SLs = SM - abx * rcp(sqL);
-  const T SRs = SM + abx * rcp(sqR);
+  const T SLs = SM - abx * iqL;
+  const T SRs = SM + abx * iqR;
   const T sg = bx >= T(0) ? T(1) : T(-1);
   const T isum = rcp(sqL + sqR);
   const T vss = (sqL * vsL + sqR * vsR + (bysR - bysL) * sg) * isum;
