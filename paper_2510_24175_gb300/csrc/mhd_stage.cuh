@@ -5,13 +5,21 @@
 // 2010, Eq. 27) and reduces the next step's max wave speed.
 //
 // Decomposition: a CTA owns a 32 x TY column tile in (x, y) and marches in z
-// over p.tz planes.  Primitive variables of the current plane and its
-// (x, y) halo live in a 4-plane shared-memory ring (planes k-1 .. k+2 feed the
-// z faces of plane k).  Ghost zones are never stored: the boundary
-// calculation is an index remap at load time (periodic: wrap; outflow: clamp
-// to the nearest interior cell), so the state arrays are interior-only SoA.
-// Each face flux of the tile is computed once and kept in shared memory;
-// work items are grouped so that every warp handles faces of one direction.
+// over p.tz planes.  Ghost zones are never stored: the boundary calculation
+// is an index remap at load time (periodic: wrap; outflow: clamp to the
+// nearest interior cell), so the state arrays are interior-only SoA.
+//
+// Per plane k, four phases separated by CTA barriers:
+//   A  load + cons->prim: the tile interior of plane k+2 (into a 3-plane
+//      ring) and the (x, y) halo of plane k (into halo buffers);
+//   B  limited slopes, each cell and direction once: x slopes of the 34
+//      cells per row, y slopes of the TY+2 rows, and -- by the thread that
+//      owns the column -- the z slope of cell k+1;
+//   C  face fluxes (PLM face states V -/+ sigma/2, GLM, HLLD), each face of
+//      the tile once, warp-uniform direction; the column owner also computes
+//      the z face k+1/2 and keeps the z data (slope, face state, flux) of its
+//      column in per-owner shared slots across planes;
+//   D  the column owner applies the flux divergence and the RK combination.
 #pragma once
 
 #include "mhd_physics.cuh"
@@ -48,7 +56,7 @@ struct StageParams {
 // Remaps a possibly out-of-range index (>= -2) into [0, n): periodic wraps,
 // outflow clamps.  Indices beyond n+1 only occur in the unused part of a
 // ragged tile and are folded to n+1 first, so every load stays in bounds.
-__device__ __forceinline__ int remap(int i, int n, int lo, int hi) {
+__host__ __device__ __forceinline__ int remap(int i, int n, int lo, int hi) {
   i = min(i, n + 1);
   if (i < 0) return lo == kBcPeriodic ? i + n : 0;
   if (i >= n) return hi == kBcPeriodic ? i - n : n - 1;
@@ -58,46 +66,78 @@ __device__ __forceinline__ int remap(int i, int n, int lo, int hi) {
 template <int TY, bool ZACT>
 struct TileGeom {
   static constexpr int TX = 32;
-  static constexpr int GX = 2;
   static constexpr int GY = TY > 1 ? 2 : 0;
-  static constexpr int SX = TX + 2 * GX;
-  static constexpr int SY = TY + 2 * GY;
-  static constexpr int PLANE = SX * SY;               // ring cells per plane
-  static constexpr int NRING = ZACT ? 4 : 1;
-  static constexpr int NCROSS = TY * SX + 2 * GY * TX;  // cells loaded per plane
-  static constexpr int FX = TY * (TX + 1);            // x faces per plane
-  static constexpr int FY = GY ? (TY + 1) * TX : 0;   // y faces per plane
-  static constexpr int FZ = ZACT ? TY * TX : 0;       // z faces per plane
+  static constexpr int NINT = TY * TX;             // interior cells per plane
+  static constexpr int NXH = 4 * TY;               // x halo: columns -2, -1, 32, 33
+  static constexpr int NYH = GY ? 4 * TX : 0;      // y halo: rows -2, -1, TY, TY+1
+  static constexpr int NRING = ZACT ? 3 : 1;
   // shared-memory words
-  static constexpr int RING_W = NRING * kNV * PLANE;
-  static constexpr int FX_W = kNV * FX;
-  static constexpr int FY_W = kNV * FY;
-  static constexpr int FZ_W = 2 * kNV * FZ;
-  static constexpr int WORDS = RING_W + FX_W + FY_W + FZ_W;
-  // flux work items: warp-aligned segments [x main][y][z][x right edge]
+  static constexpr int RING_W = NRING * kNV * NINT;
+  static constexpr int XH_W = kNV * NXH;
+  static constexpr int YH_W = kNV * NYH;
+  static constexpr int SXN = TY * (TX + 2);         // x slopes, columns -1..32
+  static constexpr int SYN = GY ? (TY + 2) * TX : 0;  // y slopes, rows -1..TY
+  static constexpr int FXN = TY * (TX + 1);
+  static constexpr int FYN = GY ? (TY + 1) * TX : 0;
+  static constexpr int Z_W = ZACT ? 3 * kNV * NINT : 0;  // z slope, z face state, z flux
+  static constexpr int WORDS =
+      RING_W + XH_W + YH_W + kNV * SXN + kNV * SYN + kNV * FXN + kNV * FYN + Z_W;
+  // phase-A items: interior, x halo, y halo
+  static constexpr int NLOAD = NINT + NXH + NYH;
+  // phase-C flux items, warp-aligned segments [x main][y][x right edge]
   static constexpr int IT_X = TY * TX;
-  static constexpr int IT_Y = FY;
-  static constexpr int IT_Z = FZ;
+  static constexpr int IT_Y = FYN;
   static constexpr int IT_XE = TY;
-  static constexpr int ITEMS = IT_X + IT_Y + IT_Z + IT_XE;
+  static constexpr int ITEMS = IT_X + IT_Y + IT_XE;
 };
+
+// Limited slopes of the 9 primitives of one cell from its two neighbours
+// along a direction, with the zero-slope fallback when a face density or
+// pressure would be non-positive.
+template <class T>
+__device__ __forceinline__ void cell_slopes(const T* m, int sm, const T* c, int sc, const T* p,
+                                            int sp, int lim, T sig[kNV]) {
+#pragma unroll
+  for (int k = 0; k < kNV; ++k) {
+    const T q = c[k * sc];
+    sig[k] = limited_slope(q - m[k * sm], p[k * sp] - q, lim);
+  }
+  const bool ok = (c[kRHO * sc] - T(0.5) * tabs(sig[kRHO]) > T(0)) &&
+                  (c[kPRS * sc] - T(0.5) * tabs(sig[kPRS]) > T(0));
+  if (!ok) {
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) sig[k] = T(0);
+  }
+}
 
 template <class T, int TY, int NW, int STAGE, bool ZACT>
 __global__ void __launch_bounds__(NW * 32, 1) rk_stage_kernel(const StageParams<T> p) {
   using G = TileGeom<TY, ZACT>;
   constexpr int NT = NW * 32;
+  constexpr int TX = G::TX;
+  constexpr int ZT0 = NT - G::NINT;  // threads ZT0.. own one tile column each
+  static_assert(ZT0 >= 0, "need one thread per tile column");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = reinterpret_cast<T*>(smem_raw);
-  T* Fx = ring + G::RING_W;
-  T* Fy = Fx + G::FX_W;
-  T* Fz = Fy + G::FY_W;
+  T* xh = ring + G::RING_W;
+  T* yh = xh + G::XH_W;
+  T* sxs = yh + G::YH_W;
+  T* sys = sxs + kNV * G::SXN;
+  T* Fx = sys + kNV * G::SYN;
+  T* Fy = Fx + kNV * G::FXN;
+  T* zS = Fy + kNV * G::FYN;  // per owner: z slope of cell k+1
+  T* zP = zS + kNV * G::NINT;  // per owner: face state V_k + sigma_k / 2
+  T* zF = zP + kNV * G::NINT;  // per owner: z flux at face k-1/2
 
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * G::TX;
+  const int x0 = blockIdx.x * TX;
   const int y0 = blockIdx.y * TY;
   const int z0 = blockIdx.z * p.tz;
   const int z1 = min(z0 + p.tz, p.n[2]);
   const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
+  const bool owner = tid >= ZT0;
+  const int oidx = tid - ZT0;  // owned column = interior cell index r * TX + c
+  const int orow = oidx / TX, ocol = oidx - (oidx / TX) * TX;
 
   const StepScalars sc = *p.sc;
   const T ch = T(sc.ch);
@@ -108,138 +148,239 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_kernel(const StageParams<
   const Phys<T> ph = p.ph;
   unsigned flags = 0;
 
-  // ---- load one plane (cons -> prim) into a ring slot -------------------
-  auto load_plane = [&](int zz, int slot) {
+  auto slot = [](int zz) { return ZACT ? ((zz % 3) + 3) % 3 : 0; };
+  auto ring_plane = [&](int zz) { return ring + slot(zz) * (kNV * G::NINT); };
+
+  // cons -> prim of cell (r, c) of plane zz into dst (variables dst_stride apart)
+  auto load_cell = [&](int zz, int r, int c, T* dst, int dst_stride) {
     const int gz = ZACT ? remap(zz, nz, p.bc_lo[2], p.bc_hi[2]) : 0;
-    T* dst = ring + slot * (kNV * G::PLANE);
-    for (int it = tid; it < G::NCROSS; it += NT) {
-      int r, c;
-      if (it < TY * G::SX) {
-        r = it / G::SX;
-        c = it - r * G::SX - G::GX;
-      } else {
-        const int j = it - TY * G::SX;
-        const int hr = j / G::TX;
-        r = hr < G::GY ? hr - G::GY : TY + hr - G::GY;
-        c = j - hr * G::TX;
-      }
-      const int gx = remap(x0 + c, nx, p.bc_lo[0], p.bc_hi[0]);
-      const int gy = G::GY ? remap(y0 + r, ny, p.bc_lo[1], p.bc_hi[1]) : 0;
-      const long long off = (long long)gz * p.sz + (long long)gy * p.sy + gx;
-      T u[kNV], v[kNV];
+    const int gx = remap(x0 + c, nx, p.bc_lo[0], p.bc_hi[0]);
+    const int gy = G::GY ? remap(y0 + r, ny, p.bc_lo[1], p.bc_hi[1]) : 0;
+    const long long off = (long long)gz * p.sz + (long long)gy * p.sy + gx;
+    T u[kNV], v[kNV];
 #pragma unroll
-      for (int k = 0; k < kNV; ++k) u[k] = p.win[k * p.sv + off];
-      cons_to_prim(u, v, ph, flags);
-      const int s = (r + G::GY) * G::SX + (c + G::GX);
+    for (int k = 0; k < kNV; ++k) u[k] = p.win[k * p.sv + off];
+    cons_to_prim(u, v, ph, flags);
 #pragma unroll
-      for (int k = 0; k < kNV; ++k) dst[k * G::PLANE + s] = v[k];
+    for (int k = 0; k < kNV; ++k) dst[k * dst_stride] = v[k];
+  };
+  // phase-A item: interior cell of plane zi or halo cell of plane zh
+  auto load_item = [&](int it, int zi, int zh) {
+    if (it < G::NINT) {
+      const int r = it / TX, c = it - (it / TX) * TX;
+      load_cell(zi, r, c, ring_plane(zi) + it, G::NINT);
+    } else if (it < G::NINT + G::NXH) {
+      const int j = it - G::NINT;
+      const int r = j >> 2, q = j & 3;
+      const int c = q < 2 ? q - 2 : TX + q - 2;
+      load_cell(zh, r, c, xh + j, G::NXH);
+    } else {
+      const int j = it - G::NINT - G::NXH;
+      const int hr = j / TX, c = j - (j / TX) * TX;
+      const int r = hr < 2 ? hr - 2 : TY + hr - 2;
+      load_cell(zh, r, c, yh + j, G::NYH);
     }
   };
-
-  // ---- face fluxes of plane k (x, y) and of face k+1/2 (z) --------------
-  auto flux_items = [&](int k, bool z_only) {
-    const int lo = z_only ? G::IT_X + G::IT_Y : 0;
-    const int hi = z_only ? G::IT_X + G::IT_Y + G::IT_Z : G::ITEMS;
-    const T* cur = ring + ((k & (G::NRING - 1)) * kNV * G::PLANE);
-    for (int it = lo + tid; it < hi; it += NT) {
-      T vl[kNV], vr[kNV], F[kNV];
-      int dir;
-      T* out;
-      int ostride;
-      if (it < G::IT_X || it >= G::IT_X + G::IT_Y + G::IT_Z) {
-        int r, fi;
-        if (it < G::IT_X) {
-          r = it / G::TX;
-          fi = it - r * G::TX;
-        } else {
-          r = it - (G::IT_X + G::IT_Y + G::IT_Z);
-          fi = G::TX;
-        }
-        // face between tile cells fi-1 and fi: ring cols fi .. fi+3
-        const T* b = cur + (r + G::GY) * G::SX + fi;
-        plm_face_pair(b, b + 1, b + 2, b + 3, G::PLANE, lim, vl, vr);
-        dir = 0;
-        out = Fx + r * (G::TX + 1) + fi;
-        ostride = G::FX;
-      } else if (it < G::IT_X + G::IT_Y) {
-        const int j = it - G::IT_X;
-        const int fj = j / G::TX, c = j - fj * G::TX;
-        const T* b = cur + fj * G::SX + (c + G::GX);
-        plm_face_pair(b, b + G::SX, b + 2 * G::SX, b + 3 * G::SX, G::PLANE, lim, vl, vr);
-        dir = 1;
-        out = Fy + fj * G::TX + c;
-        ostride = G::FY;
-      } else {
-        const int j = it - G::IT_X - G::IT_Y;
-        const int r = j / G::TX, c = j - r * G::TX;
-        const int s = (r + G::GY) * G::SX + (c + G::GX);
-        const T* b0 = ring + (((k - 1) & 3) * kNV * G::PLANE) + s;
-        const T* b1 = ring + (((k) & 3) * kNV * G::PLANE) + s;
-        const T* b2 = ring + (((k + 1) & 3) * kNV * G::PLANE) + s;
-        const T* b3 = ring + (((k + 2) & 3) * kNV * G::PLANE) + s;
-        plm_face_pair(b0, b1, b2, b3, G::PLANE, lim, vl, vr);
-        dir = 2;
-        out = Fz + (k & 1) * (kNV * G::FZ) + j;
-        ostride = G::FZ;
-      }
-      glm_hlld_flux(vl, vr, dir, ch, half_chi, ph, F);
-#pragma unroll
-      for (int q = 0; q < kNV; ++q) out[q * ostride] = F[q];
+  // primitives of cell (r, c) of the current plane (interior in ring slot,
+  // halo in the halo buffers); returns the pointer, stride in *st
+  auto cell_ptr = [&](const T* cur, int r, int c, int* st) -> const T* {
+    if (c < 0 || c >= TX) {
+      *st = G::NXH;
+      return xh + r * 4 + (c < 0 ? c + 2 : c - TX + 2);
     }
+    if (r < 0 || r >= TY) {
+      *st = G::NYH;
+      return yh + (r < 0 ? r + 2 : r - TY + 2) * TX + c;
+    }
+    *st = G::NINT;
+    return cur + r * TX + c;
   };
 
   if constexpr (ZACT) {
-    for (int zz = z0 - 2; zz < z0 + 2; ++zz) load_plane(zz, zz & 3);
+    // prologue: z face state of cell z0-1 and z flux at face z0-1/2
+    for (int it = tid; it < 3 * G::NINT; it += NT) {
+      const int pl = it / G::NINT, j = it - pl * G::NINT;
+      load_item(j, z0 - 2 + pl, 0);
+    }
     __syncthreads();
-    flux_items(z0 - 1, true);  // face z0 - 1/2
+    T Pprev[kNV];
+    if (owner) {
+      T sig[kNV];
+      const T* c = ring_plane(z0 - 1) + oidx;
+      cell_slopes(ring_plane(z0 - 2) + oidx, G::NINT, c, G::NINT, ring_plane(z0) + oidx,
+                  G::NINT, lim, sig);
+#pragma unroll
+      for (int k = 0; k < kNV; ++k) Pprev[k] = c[k * G::NINT] + T(0.5) * sig[k];
+    }
+    __syncthreads();
+    for (int it = tid; it < G::NINT; it += NT) load_item(it, z0 + 1, 0);
+    __syncthreads();
+    if (owner) {
+      T sig[kNV], M[kNV], F[kNV];
+      const T* c = ring_plane(z0) + oidx;
+      cell_slopes(ring_plane(z0 - 1) + oidx, G::NINT, c, G::NINT, ring_plane(z0 + 1) + oidx,
+                  G::NINT, lim, sig);
+#pragma unroll
+      for (int k = 0; k < kNV; ++k) {
+        const T v = c[k * G::NINT];
+        M[k] = v - T(0.5) * sig[k];
+        zP[k * G::NINT + oidx] = v + T(0.5) * sig[k];
+      }
+      glm_hlld_flux(Pprev, M, 2, ch, half_chi, ph, F);
+#pragma unroll
+      for (int k = 0; k < kNV; ++k) zF[k * G::NINT + oidx] = F[k];
+    }
     __syncthreads();
   }
 
   T lam = T(0);
   for (int k = z0; k < z1; ++k) {
-    if constexpr (ZACT) {
-      load_plane(k + 2, (k + 2) & 3);
-    } else {
-      load_plane(0, 0);
+    // ---- A: loads ---------------------------------------------------------
+    for (int it = tid; it < G::NLOAD; it += NT) {
+      if (ZACT && it < G::NINT)
+        load_item(it, k + 2, k);
+      else
+        load_item(it, k, k);
     }
     __syncthreads();
-    flux_items(k, false);
+    const T* cur = ring_plane(k);
+
+    // ---- B: slopes --------------------------------------------------------
+    for (int it = tid; it < G::SXN + G::SYN; it += NT) {
+      T sig[kNV];
+      T* dst;
+      int ds;
+      int s0, s1, s2;
+      const T *m, *c, *pp;
+      if (it < G::SXN) {
+        const int r = it / (TX + 2), cc = it - r * (TX + 2) - 1;
+        m = cell_ptr(cur, r, cc - 1, &s0);
+        c = cell_ptr(cur, r, cc, &s1);
+        pp = cell_ptr(cur, r, cc + 1, &s2);
+        dst = sxs + it;
+        ds = G::SXN;
+      } else {
+        const int j = it - G::SXN;
+        const int rr = j / TX - 1, cc = j - (j / TX) * TX;
+        m = cell_ptr(cur, rr - 1, cc, &s0);
+        c = cell_ptr(cur, rr, cc, &s1);
+        pp = cell_ptr(cur, rr + 1, cc, &s2);
+        dst = sys + j;
+        ds = G::SYN;
+      }
+      cell_slopes(m, s0, c, s1, pp, s2, lim, sig);
+#pragma unroll
+      for (int q = 0; q < kNV; ++q) dst[q * ds] = sig[q];
+    }
+    if (ZACT && owner) {
+      T sig[kNV];
+      cell_slopes(cur + oidx, G::NINT, ring_plane(k + 1) + oidx, G::NINT,
+                  ring_plane(k + 2) + oidx, G::NINT, lim, sig);
+#pragma unroll
+      for (int q = 0; q < kNV; ++q) zS[q * G::NINT + oidx] = sig[q];
+    }
     __syncthreads();
 
-    // ---- right-hand side and RK combination for plane k ------------------
-    for (int it = tid; it < TY * G::TX; it += NT) {
-      const int r = it / G::TX, c = it - r * G::TX;
-      const int gx = x0 + c, gy = y0 + r;
-      if (gx >= nx || gy >= ny) continue;
-      const long long off = (long long)k * p.sz + (long long)gy * p.sy + gx;
-      T unew[kNV];
-#pragma unroll
-      for (int q = 0; q < kNV; ++q) {
-        const T* fx = Fx + q * G::FX + r * (G::TX + 1) + c;
-        T du = (fx[1] - fx[0]) * dtdx;
-        if constexpr (G::GY > 0) {
-          const T* fy = Fy + q * G::FY + r * G::TX + c;
-          du += (fy[G::TX] - fy[0]) * dtdy;
-        }
-        if constexpr (ZACT) {
-          const T fp = Fz[(k & 1) * (kNV * G::FZ) + q * G::FZ + it];
-          const T fm = Fz[((k - 1) & 1) * (kNV * G::FZ) + q * G::FZ + it];
-          du += (fp - fm) * dtdz;
-        }
-        const T s1 = p.win[q * p.sv + off] - du;
-        if constexpr (STAGE == 1) {
-          unew[q] = s1;
+    // ---- C: fluxes --------------------------------------------------------
+    for (int it = tid; it < G::ITEMS; it += NT) {
+      T vl[kNV], vr[kNV], F[kNV];
+      int dir;
+      T* out;
+      int os;
+      if (it < G::IT_X || it >= G::IT_X + G::IT_Y) {
+        int r, fi;
+        if (it < G::IT_X) {
+          r = it / TX;
+          fi = it - r * TX;
         } else {
-          unew[q] = T(0.5) * (p.un[q * p.sv + off] + s1);
+          r = it - (G::IT_X + G::IT_Y);
+          fi = TX;
+        }
+        int sa, sb;
+        const T* a = cell_ptr(cur, r, fi - 1, &sa);
+        const T* b = cell_ptr(cur, r, fi, &sb);
+        const T* ga = sxs + r * (TX + 2) + fi;      // slope of cell fi-1
+        const T* gb = ga + 1;                        // slope of cell fi
+#pragma unroll
+        for (int q = 0; q < kNV; ++q) {
+          vl[q] = a[q * sa] + T(0.5) * ga[q * G::SXN];
+          vr[q] = b[q * sb] - T(0.5) * gb[q * G::SXN];
+        }
+        dir = 0;
+        out = Fx + r * (TX + 1) + fi;
+        os = G::FXN;
+      } else {
+        const int j = it - G::IT_X;
+        const int fj = j / TX, c = j - (j / TX) * TX;
+        int sa, sb;
+        const T* a = cell_ptr(cur, fj - 1, c, &sa);
+        const T* b = cell_ptr(cur, fj, c, &sb);
+        const T* ga = sys + fj * TX + c;             // slope of row fj-1
+        const T* gb = ga + TX;                       // slope of row fj
+#pragma unroll
+        for (int q = 0; q < kNV; ++q) {
+          vl[q] = a[q * sa] + T(0.5) * ga[q * G::SYN];
+          vr[q] = b[q * sb] - T(0.5) * gb[q * G::SYN];
+        }
+        dir = 1;
+        out = Fy + j;
+        os = G::FYN;
+      }
+      glm_hlld_flux(vl, vr, dir, ch, half_chi, ph, F);
+#pragma unroll
+      for (int q = 0; q < kNV; ++q) out[q * os] = F[q];
+    }
+    T dUz[kNV];
+    if constexpr (ZACT) {
+      if (owner) {
+        T vl[kNV], vr[kNV], F[kNV];
+        const T* c = ring_plane(k + 1) + oidx;
+#pragma unroll
+        for (int q = 0; q < kNV; ++q) {
+          vl[q] = zP[q * G::NINT + oidx];
+          vr[q] = c[q * G::NINT] - T(0.5) * zS[q * G::NINT + oidx];
+        }
+        glm_hlld_flux(vl, vr, 2, ch, half_chi, ph, F);
+#pragma unroll
+        for (int q = 0; q < kNV; ++q) {
+          dUz[q] = (F[q] - zF[q * G::NINT + oidx]) * dtdz;
+          zF[q * G::NINT + oidx] = F[q];
+          zP[q * G::NINT + oidx] = c[q * G::NINT] + T(0.5) * zS[q * G::NINT + oidx];
         }
       }
-      if constexpr (STAGE == 2) unew[kPSI] *= damp;
+    }
+    __syncthreads();
+
+    // ---- D: right-hand side and RK combination (column owners) -------------
+    if (owner) {
+      const int gx = x0 + ocol, gy = y0 + orow;
+      if (gx < nx && gy < ny) {
+        const long long off = (long long)k * p.sz + (long long)gy * p.sy + gx;
+        T unew[kNV];
 #pragma unroll
-      for (int q = 0; q < kNV; ++q) p.uout[q * p.sv + off] = unew[q];
-      if constexpr (STAGE == 2) {
-        const int ndim = 1 + (G::GY > 0) + (ZACT ? 1 : 0);
-        const T s = cell_max_speed(unew, ph, ndim, flags);
-        if (!(s <= lam)) lam = s;  // keeps NaN
+        for (int q = 0; q < kNV; ++q) {
+          const T* fx = Fx + q * G::FXN + orow * (TX + 1) + ocol;
+          T du = (fx[1] - fx[0]) * dtdx;
+          if constexpr (G::GY > 0) {
+            const T* fy = Fy + q * G::FYN + orow * TX + ocol;
+            du += (fy[TX] - fy[0]) * dtdy;
+          }
+          if constexpr (ZACT) du += dUz[q];
+          const T s1 = p.win[q * p.sv + off] - du;
+          if constexpr (STAGE == 1) {
+            unew[q] = s1;
+          } else {
+            unew[q] = T(0.5) * (p.un[q * p.sv + off] + s1);
+          }
+        }
+        if constexpr (STAGE == 2) unew[kPSI] *= damp;
+#pragma unroll
+        for (int q = 0; q < kNV; ++q) p.uout[q * p.sv + off] = unew[q];
+        if constexpr (STAGE == 2) {
+          const int ndim = 1 + (G::GY > 0) + (ZACT ? 1 : 0);
+          const T s = cell_max_speed(unew, ph, ndim, flags);
+          if (!(s <= lam)) lam = s;  // keeps NaN
+        }
       }
     }
   }
