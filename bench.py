@@ -36,12 +36,15 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# FP64 operations per cell and RK stage executed by the stage kernel
-# (DADD + DMUL + 2 x DFMA, thread-level, from ncu instruction counters on the
-# 256^3 workload; see profiles/).  Used for the ALU roofline of the FP64 path.
-FP64_OPS_PER_CELL_STAGE = None
-# Nominal FP64 peak of GB300 (CUDA cores): 1.25 TFLOP/s.
-FP64_PEAK_TFLOPS = 1.25
+# FP64-pipe lane-instructions (DADD, DMUL, DFMA, DSETP, DMNMX, conversions)
+# per cell executed by the FP64 stage kernel, stage 1 and stage 2 (which adds
+# the GLM damping and the next step's wave-speed reduction): ncu
+# smsp__inst_executed_pipe_fp64 x 32 / cells on Orszag-Tang 128^3 (per-cell
+# figures; see profiles/).  They change whenever the kernel does.
+FP64_INST_PER_CELL = {1: 1294.0, 2: 1474.0}
+# FP64 pipe peak: 2 lanes/clk/SM (a DFMA probe measured 1.9) x 152 SMs x
+# 2.07 GHz = 629 G lane-instructions/s (1.26 TFLOP/s counting an FMA as 2).
+FP64_PEAK_GINST = 2 * 152 * 2.07
 # Algorithmic HBM bytes per cell: stage 1 reads U^n and writes U1 (18 words),
 # stage 2 reads U1 and U^n and writes U^{n+1} (27 words).
 WORDS_STAGE = {1: 18, 2: 27}
@@ -202,7 +205,7 @@ def timed_steps(s, torch, K, dist, world):
     return ms, prof
 
 
-def roofline_of(prof, ncell, esize, hbm_peak, peak_kind, fp64_ops):
+def roofline_of(prof, ncell, esize, hbm_peak, peak_kind, fp64):
     """Roofline of the stage kernel (both RK stages) from its CUDA-event times."""
     n1, ms1 = prof["stage1"]
     n2, ms2 = prof["stage2"]
@@ -213,13 +216,16 @@ def roofline_of(prof, ncell, esize, hbm_peak, peak_kind, fp64_ops):
            "avg_launch_ms": avg_ms, "bytes_per_launch": bytes_launch,
            "peak_source": peak_kind}
     hbm["frac"] = hbm["achieved"] / hbm_peak
-    if fp64_ops is None:
+    if not fp64:
         return hbm, None
-    flops = ncell * fp64_ops / (avg_ms * 1e-3) / 1e12
-    alu = {"bound": "alu", "achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-           "frac": flops / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "rk_stage_kernel",
-           "avg_launch_ms": avg_ms, "fp64_ops_per_cell_stage": fp64_ops,
-           "peak_source": "nominal GB300 FP64 (CUDA cores), 152 SMs"}
+    inst = ncell * (FP64_INST_PER_CELL[1] * n1 + FP64_INST_PER_CELL[2] * n2) / max(n1 + n2, 1)
+    ach = inst / (avg_ms * 1e-3) / 1e9
+    alu = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GINST,
+           "unit": "G FP64-lane-inst/s", "frac": ach / FP64_PEAK_GINST, "traffic": None,
+           "kernel": "rk_stage_kernel", "avg_launch_ms": avg_ms,
+           "fp64_inst_per_cell": FP64_INST_PER_CELL,
+           "peak_source": "2 FP64 lanes/clk/SM x 152 SMs x 2.07 GHz (GB300 nominal 1.25 "
+                          "TFLOP/s FP64); FP64 pipe is the bound (ncu: 85 % busy)"}
     return hbm, alu
 
 
@@ -260,7 +266,7 @@ def main():
     clk = clocks.stop()
     info = s.step_info()
     value = world * N * K / (ms * 1e-3)
-    hbm, alu = roofline_of(prof, N, 8, hbm_peak, peak_kind, FP64_OPS_PER_CELL_STAGE)
+    hbm, alu = roofline_of(prof, N, 8, hbm_peak, peak_kind, True)
     launches = sum(c for c, _ in prof.values())
     kernels = {k: {"launches": c, "total_ms": t, "avg_ms": (t / c if c else 0.0)}
                for k, (c, t) in prof.items()}
@@ -306,7 +312,7 @@ def main():
         s32.step_info()
         ms32, prof32 = timed_steps(s32, torch, K, dist, world)
         s32.step_info()
-        hbm32, _ = roofline_of(prof32, N32, 4, hbm_peak, peak_kind, None)
+        hbm32, _ = roofline_of(prof32, N32, 4, hbm_peak, peak_kind, False)
         fp32 = {"workload": f"turbulent_box_{args.n32}^3_fp32", "value": world * N32 * K / (ms32 * 1e-3),
                 "unit": "zone-updates/s", "ms_per_step": ms32 / K, "roofline": hbm32,
                 "kernels": {k: {"launches": c, "total_ms": t} for k, (c, t) in prof32.items()},

@@ -285,7 +285,7 @@ __global__ void flux_batch_kernel(const T* __restrict__ VL, const T* __restrict_
       vl[k] = VL[k * nface + f];
       vr[k] = VR[k * nface + f];
     }
-    glm_hlld_flux(vl, vr, dir, ch, half_chi, ph, out);
+    glm_hlld_flux_dir(vl, vr, dir, ch, half_chi, ph, out);
 #pragma unroll
     for (int k = 0; k < kNV; ++k) F[k * nface + f] = out[k];
   }

@@ -49,9 +49,11 @@ MHD_HD double rcp(double x) {
   return 1.0 / x;
 #endif
 }
+// FP32 mode: hardware-approximate reciprocal and square root (a few ulp;
+// the FP32 bulk path's error budget is ~1e-5 relative).
 MHD_HD float rcp(float x) {
 #ifdef __CUDA_ARCH__
-  return __frcp_rn(x);
+  return __fdividef(1.0f, x);
 #else
   return 1.0f / x;
 #endif
@@ -59,7 +61,13 @@ MHD_HD float rcp(float x) {
 MHD_HD double trsqrt(double x) { return rsqrt(x); }
 MHD_HD float trsqrt(float x) { return rsqrtf(x); }
 MHD_HD double tsqrt(double x) { return sqrt(x); }
-MHD_HD float tsqrt(float x) { return sqrtf(x); }
+MHD_HD float tsqrt(float x) {
+#ifdef __CUDA_ARCH__
+  return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+#else
+  return sqrtf(x);
+#endif
+}
 MHD_HD double tabs(double x) { return fabs(x); }
 MHD_HD float tabs(float x) { return fabsf(x); }
 MHD_HD double tmin(double a, double b) { return fmin(a, b); }
@@ -147,6 +155,15 @@ MHD_HD T fast_speed(T rho_i, T gp, T b2, T bn2) {
   T disc = a * a - T(4) * gp * bn2 * (rho_i * rho_i);
   disc = tmax(disc, T(0));
   return tsqrt(T(0.5) * (a + tsqrt(disc)));
+}
+
+// c_f^2 (see fast_speed).
+template <class T>
+MHD_HD T fast_speed2(T rho_i, T gp, T b2, T bn2) {
+  const T a = (gp + b2) * rho_i;
+  T disc = a * a - T(4) * gp * bn2 * (rho_i * rho_i);
+  disc = tmax(disc, T(0));
+  return T(0.5) * (a + tsqrt(disc));
 }
 
 // max over active directions of |v_d| + c_f,d for one conservative cell.
@@ -249,19 +266,20 @@ MHD_HD void plm_face_pair(const T* c0, const T* c1, const T* c2,
   }
 }
 
-// Picks component (dir + j) % 3 of a 3-vector given as scalars.
+// Picks component (dir + j) % 3 of a 3-vector given as scalars (dir is a
+// compile-time constant in the flux kernels, so this folds away).
 template <class T>
 MHD_HD T rot3(int dir, int j, T a, T b, T c) {
   const int m = (dir + j) % 3;
   return m == 0 ? a : (m == 1 ? b : c);
 }
 
-// GLM interface step + HLLD along direction dir (0, 1, 2) for primitive face
-// states vl, vr.  ch: cleaning speed; half_chi = 0.5 / ch.  F in conservative
-// ordering.
-template <class T>
-MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], int dir, T ch,
-                                              T half_chi, const Phys<T>& ph, T F[kNV]) {
+// GLM interface step + HLLD along direction dir (0, 1, 2; template
+// argument) for primitive face states vl, vr.  ch: cleaning speed;
+// half_chi = 0.5 / ch.  F in conservative ordering.
+template <int dir, class T>
+MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
+                          const Phys<T>& ph, T F[kNV]) {
   const T half = T(0.5);
   // rotate: u normal, (v, w) tangential in cyclic order; by, bz likewise
   const T uL = rot3(dir, 0, vl[kVX], vl[kVY], vl[kVZ]);
@@ -289,13 +307,15 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], int dir, T ch,
   const T ptL = pL + half * b2L, ptR = pR + half * b2R;
   const T eL = pL * ph.gm1i + half * rL * (uL * uL + vL * vL + wL * wL) + half * b2L;
   const T eR = pR * ph.gm1i + half * rR * (uR * uR + vR * vR + wR * wR) + half * b2R;
-  // 1/rho of both sides from one reciprocal
+  // 1/rho of both sides from one reciprocal; only max(c_fL, c_fR) is used,
+  // so one square root of max(c_fL^2, c_fR^2) (sqrt is monotone and
+  // correctly rounded: the same value)
   const T qr = rcp(rL * rR);
-  const T cfL = fast_speed(rR * qr, ph.gamma * pL, b2L, bx2);
-  const T cfR = fast_speed(rL * qr, ph.gamma * pR, b2R, bx2);
+  const T cf2L = fast_speed2(rR * qr, ph.gamma * pL, b2L, bx2);
+  const T cf2R = fast_speed2(rL * qr, ph.gamma * pR, b2R, bx2);
 
   // wave-speed estimates (MK05 Eq. 67), contact speed and total pressure
-  const T cmax = tmax(cfL, cfR);
+  const T cmax = tsqrt(tmax(cf2L, cf2R));
   const T SL = tmin(uL, uR) - cmax;
   const T SR = tmax(uL, uR) + cmax;
   const T dL = (SL - uL) * rL, dR = (SR - uR) * rR;
@@ -307,13 +327,14 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], int dir, T ch,
   // |rho (S-u)(S-S_M) - Bx^2| < 1e-8 p_t*; paired reciprocals of S-S_M and
   // of the two denominators
   const T smL = SL - SM, smR = SR - SM;
-  const T qs = rcp(smL * smR);
-  const T smiL = smR * qs, smiR = smL * qs;
   const T denL = dL * smL - bx2, denR = dR * smR - bx2;
   const bool degL = tabs(denL) < T(1e-8) * pts;
   const bool degR = tabs(denR) < T(1e-8) * pts;
   const T dnL = degL ? T(1) : denL, dnR = degR ? T(1) : denR;
-  const T qd = rcp(dnL * dnR);
+  const T ps = smL * smR, pd = dnL * dnR;
+  const T q4 = rcp(ps * pd);  // one reciprocal for the four divisors
+  const T qs = pd * q4, qd = ps * q4;
+  const T smiL = smR * qs, smiR = smL * qs;
   const T deniL = dnR * qd, deniR = dnL * qd;
   T rsL, vsL, wsL, bysL, bzsL, esL, vbsL;
   T rsR, vsR, wsR, bysR, bzsR, esR, vbsR;
@@ -396,4 +417,19 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], int dir, T ch,
   }
 }
 
+}  // namespace mhd
+
+namespace mhd {
+// Runtime-direction entry (batched unit kernel): dispatches to the
+// compile-time direction.
+template <class T>
+MHD_HD void glm_hlld_flux_dir(const T vl[kNV], const T vr[kNV], int dir, T ch, T half_chi,
+                              const Phys<T>& ph, T F[kNV]) {
+  if (dir == 0)
+    glm_hlld_flux<0>(vl, vr, ch, half_chi, ph, F);
+  else if (dir == 1)
+    glm_hlld_flux<1>(vl, vr, ch, half_chi, ph, F);
+  else
+    glm_hlld_flux<2>(vl, vr, ch, half_chi, ph, F);
+}
 }  // namespace mhd

@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_kernel(const StageParams<
         M[k] = v - T(0.5) * sig[k];
         zP[k * G::NINT + oidx] = v + T(0.5) * sig[k];
       }
-      glm_hlld_flux(Pprev, M, 2, ch, half_chi, ph, F);
+      glm_hlld_flux<2>(Pprev, M, ch, half_chi, ph, F);
 #pragma unroll
       for (int k = 0; k < kNV; ++k) zF[k * G::NINT + oidx] = F[k];
     }
@@ -326,7 +326,11 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_kernel(const StageParams<
         out = Fy + j;
         os = G::FYN;
       }
-      glm_hlld_flux(vl, vr, dir, ch, half_chi, ph, F);
+      // warp-uniform branch to the compile-time direction
+      if (dir == 0)
+        glm_hlld_flux<0>(vl, vr, ch, half_chi, ph, F);
+      else
+        glm_hlld_flux<1>(vl, vr, ch, half_chi, ph, F);
 #pragma unroll
       for (int q = 0; q < kNV; ++q) out[q * os] = F[q];
     }
@@ -340,7 +344,7 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_kernel(const StageParams<
           vl[q] = zP[q * G::NINT + oidx];
           vr[q] = c[q * G::NINT] - T(0.5) * zS[q * G::NINT + oidx];
         }
-        glm_hlld_flux(vl, vr, 2, ch, half_chi, ph, F);
+        glm_hlld_flux<2>(vl, vr, ch, half_chi, ph, F);
 #pragma unroll
         for (int q = 0; q < kNV; ++q) {
           dUz[q] = (F[q] - zF[q * G::NINT + oidx]) * dtdz;
