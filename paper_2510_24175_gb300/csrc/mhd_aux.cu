@@ -74,12 +74,12 @@ __global__ void __launch_bounds__(256) max_speed_kernel(const T* __restrict__ U,
 #pragma unroll
     for (int k = 0; k < kNV; ++k) u[k] = U[k * ncell + c];
     const double s = (double)cell_max_speed(u, ph, ndim, flags);
-    if (!(s <= lam)) lam = s;
+    lam = nan_max(lam, s);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const double other = __shfl_xor_sync(0xffffffffu, lam, o);
-    if (!(other <= lam)) lam = other;
+    lam = nan_max(lam, other);
   }
   __shared__ double w[8];
   if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = lam;
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) max_speed_kernel(const T* __restrict__ U,
   if (threadIdx.x == 0) {
     double m = w[0];
     for (int i = 1; i < (int)(blockDim.x >> 5); ++i)
-      if (!(w[i] <= m)) m = w[i];
+      m = nan_max(m, w[i]);
     unsigned long long bits = (unsigned long long)__double_as_longlong(m);
     if (m != m) bits = 0x7ff8000000000000ull;
     atomicMax(lam_bits, bits);

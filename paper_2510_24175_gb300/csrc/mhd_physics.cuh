@@ -75,6 +75,10 @@ MHD_HD float tmin(float a, float b) { return fminf(a, b); }
 MHD_HD double tmax(double a, double b) { return fmax(a, b); }
 MHD_HD float tmax(float a, float b) { return fmaxf(a, b); }
 
+// max that keeps a NaN once either operand has one (fmax drops NaNs).
+MHD_HD double nan_max(double a, double b) { return (a != a || b > a || b != b) ? (a != a ? a : b) : a; }
+MHD_HD float nan_max(float a, float b) { return (a != a || b > a || b != b) ? (a != a ? a : b) : a; }
+
 // Pressure floor.  FP64: plain comparison.  FP32: when the FP32 pressure is
 // within the cancellation-dominated range (internal energy below 1e-3 of the
 // total, or below the floor) p is recomputed in FP64 from the promoted
@@ -176,8 +180,8 @@ MHD_HD T cell_max_speed(const T u[kNV], const Phys<T>& ph, int ndim,
   const T gp = ph.gamma * v[kPRS];
   const T b2 = v[kBX] * v[kBX] + v[kBY] * v[kBY] + v[kBZ] * v[kBZ];
   T lam = tabs(v[kVX]) + fast_speed(ri, gp, b2, v[kBX] * v[kBX]);
-  if (ndim > 1) lam = tmax(lam, tabs(v[kVY]) + fast_speed(ri, gp, b2, v[kBY] * v[kBY]));
-  if (ndim > 2) lam = tmax(lam, tabs(v[kVZ]) + fast_speed(ri, gp, b2, v[kBZ] * v[kBZ]));
+  if (ndim > 1) lam = nan_max(lam, tabs(v[kVY]) + fast_speed(ri, gp, b2, v[kBY] * v[kBY]));
+  if (ndim > 2) lam = nan_max(lam, tabs(v[kVZ]) + fast_speed(ri, gp, b2, v[kBZ] * v[kBZ]));
   // NaN anywhere in the cell (psi included) makes the speed NaN
   if (!(v[kPSI] == v[kPSI]) || !(lam == lam)) lam = T(NAN);
   return lam;

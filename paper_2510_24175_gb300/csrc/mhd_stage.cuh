@@ -144,6 +144,10 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_kernel(const StageParams<
   const T half_chi = T(0.5 / sc.ch);
   const T dtdx = T(sc.dtdx[0]), dtdy = T(sc.dtdx[1]), dtdz = T(sc.dtdx[2]);
   const T damp = T(sc.damp);
+  // dt == 0 (a step at t_end, or one the prepare kernel turned into a no-op
+  // after a non-finite wave speed): the state is copied through unchanged,
+  // even where fluxes are not finite
+  const bool frozen = !(sc.dt != 0.0);
   const int lim = p.limiter;
   const Phys<T> ph = p.ph;
   unsigned flags = 0;
@@ -370,6 +374,7 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_kernel(const StageParams<
             du += (fy[TX] - fy[0]) * dtdy;
           }
           if constexpr (ZACT) du += dUz[q];
+          if (frozen) du = T(0);
           const T s1 = p.win[q * p.sv + off] - du;
           if constexpr (STAGE == 1) {
             unew[q] = s1;
@@ -383,7 +388,7 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_kernel(const StageParams<
         if constexpr (STAGE == 2) {
           const int ndim = 1 + (G::GY > 0) + (ZACT ? 1 : 0);
           const T s = cell_max_speed(unew, ph, ndim, flags);
-          if (!(s <= lam)) lam = s;  // keeps NaN
+          lam = nan_max(lam, s);
         }
       }
     }
@@ -395,7 +400,7 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_kernel(const StageParams<
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const double other = __shfl_xor_sync(0xffffffffu, l, o);
-      if (!(other <= l)) l = other;
+      l = nan_max(l, other);
     }
     __shared__ double wmax[NW];
     __syncthreads();
@@ -404,7 +409,7 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_kernel(const StageParams<
     if (tid == 0) {
       double m = wmax[0];
       for (int w = 1; w < NW; ++w)
-        if (!(wmax[w] <= m)) m = wmax[w];
+        m = nan_max(m, wmax[w]);
       unsigned long long bits = (unsigned long long)__double_as_longlong(m);
       if (m != m) bits = 0x7ff8000000000000ull;
       atomicMax(p.lam_bits, bits);
