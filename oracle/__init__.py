@@ -109,6 +109,8 @@ def lib():
         _lib.orc_run.restype = ctypes.c_double
         _lib.orc_run_jvp.argtypes = [P, D, D, ctypes.c_int, D, D]
         _lib.orc_conserved_sums.argtypes = [P, D, D]
+        _lib.orc_stage_padded.argtypes = [P, D, D, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_int, D]
     return _lib
 
 
@@ -193,6 +195,18 @@ def stage(W: np.ndarray, grid: Grid, dt: float, ch: float, stage_no: int,
     un = _d(_f64(Un)) if Un is not None else None
     lib().orc_stage(ctypes.byref(p), _d(W), un, dt, ch, stage_no, _d(out), cnt)
     return out, (cnt[0], cnt[1])
+
+
+def stage_padded(Wp: np.ndarray, grid: Grid, dt: float, ch: float, stage_no: int,
+                 Un: np.ndarray | None = None, damp: bool = False) -> np.ndarray:
+    """One stage on a padded array whose ghost zones the caller filled."""
+    Wp = _f64(Wp)
+    nx, ny, nz = grid.n
+    out = np.empty((9, nz, ny, nx))
+    p = grid.c()
+    un = _d(_f64(Un)) if Un is not None else None
+    lib().orc_stage_padded(ctypes.byref(p), _d(Wp), un, dt, ch, stage_no, int(damp), _d(out))
+    return out
 
 
 @dataclass

@@ -443,8 +443,8 @@ void fill_ghosts(Field<S>& f, const Params& P) {
 // on interior cells.  W's ghosts are (re)filled here.
 template <class S>
 void rk_stage(const Params& P, Field<S>& W, const Field<S>* Un, double dt, double ch,
-              int stage, Field<S>& out, Counters* cnt) {
-  fill_ghosts(W, P);                                                  // step 1
+              int stage, Field<S>& out, Counters* cnt, bool fill = true) {
+  if (fill) fill_ghosts(W, P);                                        // step 1
 
   Field<S> V(P.n);                                                    // step 2
   {
@@ -564,6 +564,14 @@ double max_speed(const Params& P, const Field<S>& U, Counters* cnt) {
   return lam;
 }
 
+// GLM damping of psi after a full step (Mignone & Tzeferacos 2010, Eq. 27).
+inline double damping_factor(const Params& P, double dt, double ch) {
+  double dh = 1e300;
+  for (int d = 0; d < 3; ++d)
+    if (P.n[d] > 1) dh = std::min(dh, P.dx[d]);
+  return std::exp(-P.glm_alpha * ch * dt / dh);
+}
+
 // One full RK2 step with frozen dt and c_h, followed by the GLM damping
 // psi <- psi exp(-alpha c_h dt / dh_min) (Mignone & Tzeferacos 2010, Eq. 27).
 template <class S>
@@ -571,10 +579,7 @@ void rk2_step(const Params& P, Field<S>& U, double dt, double ch, Counters* cnt)
   Field<S> U1(P.n), Un1(P.n);
   rk_stage(P, U, (const Field<S>*)nullptr, dt, ch, 1, U1, cnt);
   rk_stage(P, U1, &U, dt, ch, 2, Un1, cnt);
-  double dh = 1e300;
-  for (int d = 0; d < 3; ++d)
-    if (P.n[d] > 1) dh = std::min(dh, P.dx[d]);
-  double damp = std::exp(-P.glm_alpha * ch * dt / dh);
+  const double damp = damping_factor(P, dt, ch);
   int c[3];
   for (c[2] = 0; c[2] < P.n[2]; ++c[2])
     for (c[1] = 0; c[1] < P.n[1]; ++c[1])
@@ -736,6 +741,27 @@ void orc_stage(const orc_params* p, const double* W, const double* Un, double dt
     counters[0] = cnt.rho_floor_hits;
     counters[1] = cnt.p_floor_hits;
   }
+}
+
+// One RK2 stage on a caller-filled padded array (ghost zones supplied by the
+// caller, e.g. exchanged between subdomains): Wp is
+// [9][nz+2gz][ny+2gy][nx+2gx]; Un and out are interior-only.  With damp != 0
+// (stage 2 only) psi of the result is multiplied by the step's GLM damping
+// factor, completing the step.
+void orc_stage_padded(const orc_params* p, const double* Wp, const double* Un, double dt,
+                      double ch, int stage, int damp, double* out) {
+  Params P = to_params(p);
+  Field<double> w(P.n), un(P.n), o(P.n);
+  std::memcpy(w.a.data(), Wp, w.a.size() * sizeof(double));
+  if (Un) load_interior(un, Un, nullptr);
+  rk_stage(P, w, Un ? &un : nullptr, dt, ch, stage, o, (Counters*)nullptr, false);
+  if (damp) {
+    const double f = damping_factor(P, dt, ch);
+    for (int k = 0; k < P.n[2]; ++k)
+      for (int j = 0; j < P.n[1]; ++j)
+        for (int i = 0; i < P.n[0]; ++i) o.at(PSI, i, j, k) = f * o.at(PSI, i, j, k);
+  }
+  store_interior(o, out, nullptr);
 }
 
 // nsteps full RK2 steps in place.  If dts/chs are non-null and dts[s] > 0 the
