@@ -321,6 +321,24 @@ def main():
         del s32
         torch.cuda.empty_cache()
 
+    # ---- FP32 on the FP64 grid (same-grid precision ratio) -----------------
+    fp32_same = None
+    if not args.no_fp32:
+        pbs = inputs.orszag_tang_3d(args.n)
+        ss = m.MHD(m.Config.from_problem(pbs, precision=m.MHD_FP32))
+        ss.set_state(torch.from_numpy(pbs.prim()).cuda(), kind=m.MHD_PRIM)
+        for _ in range(W):
+            ss.step()
+        ss.step_info()
+        mss, profs = timed_steps(ss, torch, K, dist, world)
+        ss.step_info()
+        fp32_same = {"workload": f"orszag_tang_3d_{args.n}^3_fp32",
+                     "value": world * pbs.ncell * K / (mss * 1e-3), "unit": "zone-updates/s",
+                     "ms_per_step": mss / K}
+        launches += sum(c for c, _ in profs.values())
+        del ss
+        torch.cuda.empty_cache()
+
     # ---- adjoint / forward step-time ratio: 2-D Orszag-Tang 512^2 FP64 ------
     adjoint = None
     if not args.no_adjoint:
@@ -390,7 +408,8 @@ def main():
         "clocks": clk,
         "e2e": e2e,
         "fp32": fp32,
-        "fp32_over_fp64": (fp32["value"] / value) if fp32 else None,
+        "fp32_same_grid": fp32_same,
+        "fp32_over_fp64_same_grid": (fp32_same["value"] / value) if fp32_same else None,
         "adjoint": adjoint,
         "cpu_baseline": cpu,
     }
