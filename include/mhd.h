@@ -176,6 +176,38 @@ int mhd_profile_read(mhd_ctx* ctx, long long counts[4], double ms[4]);
 int mhd_conserved_sums_noalloc(const mhd_config* cfg, const void* U, double out[8],
                                void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched ensemble: independent 3-D boxes (each with its own grid, domain,
+ * boundary conditions and CFL time step) advanced together by ONE
+ * persistent cooperative kernel launch per mhd_ensemble_step call, captured
+ * in a CUDA graph.  Boxes must be 3-D and MHD_FP32.  Every box evolves
+ * bitwise as it would under its own mhd_step calls (same tile code).  The
+ * caller allocates one device workspace (mhd_ensemble_workspace_bytes,
+ * 256-byte aligned).
+ * ------------------------------------------------------------------------- */
+typedef struct mhd_ensemble mhd_ensemble;
+int mhd_ensemble_workspace_bytes(const mhd_config* cfgs, int nbox, size_t* bytes);
+int mhd_ensemble_create(const mhd_config* cfgs, int nbox, void* d_workspace, size_t bytes,
+                        void* stream, mhd_ensemble** out);
+/* Same conventions as mhd_set_state / mhd_get_state, for box `box`;
+ * set_state restarts that box's time and step count. */
+int mhd_ensemble_set_state(mhd_ensemble* ens, int box, const double* U, int where, int kind);
+int mhd_ensemble_get_state(mhd_ensemble* ens, int box, double* U, int where, int kind);
+/* nsteps CFL steps of every box in one persistent launch (per step: per-box
+ * dt and c_h, stage 1, grid barrier, stage 2, grid barrier).  Asynchronous. */
+int mhd_ensemble_step(mhd_ensemble* ens, int nsteps);
+/* out[0] = t, out[1] = dt, out[2] = c_h, out[3] = steps of box `box`,
+ * out[4] = its z-chunk depth, out[5] = 1 if launches are graph-captured.
+ * Synchronises; MHD_ERR_NONFINITE if the box saw a non-finite dt. */
+int mhd_ensemble_info(mhd_ensemble* ens, int box, double out[6]);
+/* Timing autotuner: for each box-size class, tries z-chunk depths
+ * {4, 8, 16, 32, 64} (coordinate descent, timing trial_steps-step launches)
+ * and keeps the fastest.  ADVANCES every box by the trial steps: save and
+ * restore the states around it.  Synchronises. */
+int mhd_ensemble_autotune(mhd_ensemble* ens, int trial_steps);
+const char* mhd_ensemble_last_error(const mhd_ensemble* ens);
+int mhd_ensemble_destroy(mhd_ensemble* ens);
+
 /* Message of the last failing call on ctx (never NULL). */
 const char* mhd_last_error(const mhd_ctx* ctx);
 

@@ -36,7 +36,10 @@ EXPORTED = ["mhd_config_default", "mhd_workspace_bytes", "mhd_create", "mhd_set_
             "mhd_set_state", "mhd_get_state", "mhd_dt", "mhd_step", "mhd_step_info",
             "mhd_counters", "mhd_conserved_sums", "mhd_flux_batch", "mhd_adjoint_step",
             "mhd_profile_enable", "mhd_profile_read", "mhd_conserved_sums_noalloc",
-            "mhd_last_error", "mhd_destroy"]
+            "mhd_last_error", "mhd_destroy",
+            "mhd_ensemble_workspace_bytes", "mhd_ensemble_create", "mhd_ensemble_set_state",
+            "mhd_ensemble_get_state", "mhd_ensemble_step", "mhd_ensemble_info",
+            "mhd_ensemble_autotune", "mhd_ensemble_last_error", "mhd_ensemble_destroy"]
 
 
 class MHDError(RuntimeError):
@@ -87,9 +90,19 @@ def lib():
         L.mhd_conserved_sums_noalloc.argtypes = [cfgp, vp, dp, vp]
         L.mhd_last_error.argtypes = [vp]
         L.mhd_last_error.restype = ctypes.c_char_p
+        L.mhd_ensemble_workspace_bytes.argtypes = [cfgp, i, ctypes.POINTER(ctypes.c_size_t)]
+        L.mhd_ensemble_create.argtypes = [cfgp, i, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+        L.mhd_ensemble_set_state.argtypes = [vp, i, vp, i, i]
+        L.mhd_ensemble_get_state.argtypes = [vp, i, vp, i, i]
+        L.mhd_ensemble_step.argtypes = [vp, i]
+        L.mhd_ensemble_info.argtypes = [vp, i, dp]
+        L.mhd_ensemble_autotune.argtypes = [vp, i]
+        L.mhd_ensemble_last_error.argtypes = [vp]
+        L.mhd_ensemble_last_error.restype = ctypes.c_char_p
+        L.mhd_ensemble_destroy.argtypes = [vp]
         L.mhd_destroy.argtypes = [vp]
         for name in EXPORTED:
-            if name != "mhd_last_error":
+            if not name.endswith("last_error"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -324,3 +337,69 @@ class MHD:
                 if info["t"] >= t_end:
                     break
         return self.step_info()
+
+
+class Ensemble:
+    """Independent 3-D FP32 boxes advanced together by one persistent,
+    graph-captured launch per ``step`` call (mhd_ensemble_*)."""
+
+    def __init__(self, configs, stream=None):
+        torch = _torch()
+        self.configs = list(configs)
+        n = len(self.configs)
+        self._c = (mhd_config * n)(*[c.c() for c in self.configs])
+        nbytes = ctypes.c_size_t()
+        _check(lib().mhd_ensemble_workspace_bytes(self._c, n, ctypes.byref(nbytes)),
+               what="mhd_ensemble_workspace_bytes")
+        self.workspace = torch.empty(nbytes.value + 256, dtype=torch.uint8, device="cuda")
+        off = (-self.workspace.data_ptr()) % 256
+        ws = self.workspace[off:off + nbytes.value]
+        s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else _stream_ptr()
+        self.ens = ctypes.c_void_p()
+        _check(lib().mhd_ensemble_create(self._c, n, _ptr(ws), nbytes.value, s,
+                                         ctypes.byref(self.ens)), what="mhd_ensemble_create")
+        self.shapes = [(9, c.n[2], c.n[1], c.n[0]) for c in self.configs]
+
+    def _err(self, rc, what):
+        if rc != MHD_OK:
+            raise MHDError(rc, f"{what}: {lib().mhd_ensemble_last_error(self.ens).decode()}")
+
+    def __del__(self):
+        try:
+            if getattr(self, "ens", None) and self.ens.value:
+                lib().mhd_ensemble_destroy(self.ens)
+                self.ens = None
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.configs)
+
+    def set_state(self, box: int, U, kind=MHD_CONS):
+        assert U.is_cuda and U.is_contiguous() and tuple(U.shape) == self.shapes[box]
+        self._err(lib().mhd_ensemble_set_state(self.ens, box, _ptr(U), MHD_DEVICE, kind),
+                  "mhd_ensemble_set_state")
+
+    def get_state(self, box: int, kind=MHD_CONS):
+        torch = _torch()
+        out = torch.empty(self.shapes[box], dtype=torch.float64, device="cuda")
+        self._err(lib().mhd_ensemble_get_state(self.ens, box, _ptr(out), MHD_DEVICE, kind),
+                  "mhd_ensemble_get_state")
+        return out
+
+    def step(self, nsteps: int = 1):
+        self._err(lib().mhd_ensemble_step(self.ens, nsteps), "mhd_ensemble_step")
+
+    def info(self, box: int):
+        out = (ctypes.c_double * 6)()
+        self._err(lib().mhd_ensemble_info(self.ens, box, out), "mhd_ensemble_info")
+        return {"t": out[0], "dt": out[1], "ch": out[2], "steps": int(out[3]),
+                "tz": int(out[4]), "graph": bool(out[5])}
+
+    def autotune(self, trial_steps: int = 1):
+        """Picks z-chunk depths by timing; the boxes' states are saved before
+        and restored after (the trial launches advance them)."""
+        saved = [self.get_state(b) for b in range(len(self))]
+        self._err(lib().mhd_ensemble_autotune(self.ens, trial_steps), "mhd_ensemble_autotune")
+        for b, U in enumerate(saved):
+            self.set_state(b, U)

@@ -10,50 +10,11 @@
 #include <new>
 #include <vector>
 
-#include "../../include/mhd.h"
-#include "mhd_internal.h"
+#include "mhd_ctx.h"
 
-namespace {
-
-constexpr int kSumBlocks = 1024;
-
-struct Scalars {  // device block at the start of the scalar region
-  mhd::StepScalars sc;
-  unsigned long long lam_bits;
-  unsigned long long floor_cnt[2];
-  unsigned int status;
-  unsigned int pad;
-  double sums[8];
-};
-
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-}  // namespace
-
-struct mhd_ctx {
-  mhd_config cfg;
-  mhd::Grid grid;
-  size_t esize;          // bytes per state element (8 or 4)
-  size_t state_bytes;    // 9 * ncell * esize
-  char* ws;
-  size_t ws_bytes;
-  void* Ua;              // U^n (and U^{n+1}, in place)
-  void* Ub;              // U1 / staging
-  Scalars* scal;
-  double* partials;
-  void* adj;             // adjoint scratch (MHD_FLAG_ADJOINT)
-  size_t adj_bytes;
-  cudaStream_t stream;
-  bool have_state;
-  bool lam_valid;
-  double inv_dx_sum, dh_min;
-  // CUDA-event timing (mhd_profile_enable)
-  bool prof_on;
-  struct Rec { cudaEvent_t a, b; int kind; };
-  std::vector<Rec> prof_recs;
-  std::vector<cudaEvent_t> prof_pool;
-  char err[512];
-};
+using mhd::Scalars;
+using mhd::align256;
+using mhd::kSumBlocks;
 
 static cudaEvent_t prof_event(mhd_ctx* c) {
   if (!c->prof_pool.empty()) {

@@ -110,14 +110,17 @@ __device__ __forceinline__ void cell_slopes(const T* m, int sm, const T* c, int 
   }
 }
 
+// One tile (bx, by, bz) of one RK stage; called by every thread of a CTA of
+// NW warps.  smem_raw: TileGeom::WORDS elements of T; wmax: NW doubles.
 template <class T, int TY, int NW, int STAGE, bool ZACT>
-__global__ void __launch_bounds__(NW * 32, 1) rk_stage_kernel(const StageParams<T> p) {
+__device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepScalars& sc,
+                                           int bx, int by, int bz, unsigned char* smem_raw,
+                                           double* wmax) {
   using G = TileGeom<TY, ZACT>;
   constexpr int NT = NW * 32;
   constexpr int TX = G::TX;
   constexpr int ZT0 = NT - G::NINT;  // threads ZT0.. own one tile column each
   static_assert(ZT0 >= 0, "need one thread per tile column");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = reinterpret_cast<T*>(smem_raw);
   T* xh = ring + G::RING_W;
   T* yh = xh + G::XH_W;
@@ -130,16 +133,15 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_kernel(const StageParams<
   T* zF = zP + kNV * G::NINT;  // per owner: z flux at face k-1/2
 
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * TX;
-  const int y0 = blockIdx.y * TY;
-  const int z0 = blockIdx.z * p.tz;
+  const int x0 = bx * TX;
+  const int y0 = by * TY;
+  const int z0 = bz * p.tz;
   const int z1 = min(z0 + p.tz, p.n[2]);
   const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
   const bool owner = tid >= ZT0;
   const int oidx = tid - ZT0;  // owned column = interior cell index r * TX + c
   const int orow = oidx / TX, ocol = oidx - (oidx / TX) * TX;
 
-  const StepScalars sc = *p.sc;
   const T ch = T(sc.ch);
   const T half_chi = T(0.5 / sc.ch);
   const T dtdx = T(sc.dtdx[0]), dtdy = T(sc.dtdx[1]), dtdz = T(sc.dtdx[2]);
@@ -402,7 +404,6 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_kernel(const StageParams<
       const double other = __shfl_xor_sync(0xffffffffu, l, o);
       l = nan_max(l, other);
     }
-    __shared__ double wmax[NW];
     __syncthreads();
     if ((tid & 31) == 0) wmax[tid >> 5] = l;
     __syncthreads();
@@ -419,6 +420,15 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_kernel(const StageParams<
     if (flags & kFloorRho) atomicAdd(&p.floor_cnt[0], 1ull);
     if (flags & kFloorP) atomicAdd(&p.floor_cnt[1], 1ull);
   }
+  __syncthreads();  // the CTA may start another tile on the same shared memory
+}
+
+template <class T, int TY, int NW, int STAGE, bool ZACT>
+__global__ void __launch_bounds__(NW * 32, 1) rk_stage_kernel(const StageParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double wmax[NW];
+  const StepScalars sc = *p.sc;
+  stage_tile<T, TY, NW, STAGE, ZACT>(p, sc, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw, wmax);
 }
 
 }  // namespace mhd
