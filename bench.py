@@ -149,6 +149,16 @@ def cpu_oracle_sample(target_s: float = 12.0):
                       f"single thread, {t:.1f} s", "host_cores": os.cpu_count()}
 
 
+def workload_config(n: int, world: int, t_reached=None) -> dict:
+    cfg = {"workload": f"orszag_tang_3d_{n}^3_fp64", "n": [n, n, n],
+           "limiter": "MC", "riemann": "HLLD+GLM", "time": "RK2", "cfl": 0.8,
+           "l2": "state arrays (1.2 GB each at 256^3) larger than L2; no flush",
+           "parallelism": f"{world} independent replica(s)"}
+    if t_reached is not None:
+        cfg["t_reached"] = t_reached
+    return cfg
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -166,15 +176,16 @@ def run_reference(args):
         U = orc.run(U, g, 1).U
     el = time.perf_counter() - t0
     val = pb.ncell * args.steps / el
-    sample = (f"one RK2 step per bench step of 3-D Orszag-Tang at 48^3 (FP64), the 256^3 "
-              f"workload's problem at a size the single-threaded oracle finishes quickly")
+    sample = ("each bench step: one RK2 step of the same Orszag-Tang problem on a 48^3 "
+              "periodic box (the same per-zone arithmetic as the 256^3 workload), CPU "
+              "oracle, single thread")
     print(json.dumps({
         "impl": "reference", "metric": "zone-updates/s", "value": val,
         "unit": "zone-updates/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": "orszag_tang_3d_48_cpu_oracle",
-                                        "n": [48, 48, 48]},
+        "data": "synthetic (closed-form Orszag-Tang initial condition)",
+        "config": workload_config(args.n, 1),
         "cpu_baseline": {"value": val, "unit": "zone-updates/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": val, "unit": "zone-updates/s", "h2d_bytes_per_step": 0,
@@ -445,11 +456,7 @@ def main():
         "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (closed-form Orszag-Tang initial condition)",
-        "config": {"workload": f"orszag_tang_3d_{args.n}^3_fp64", "n": list(pb.n),
-                   "limiter": "MC", "riemann": "HLLD+GLM", "time": "RK2", "cfl": pb.cfl,
-                   "l2": "state arrays (1.2 GB each) larger than L2; no flush",
-                   "parallelism": f"{world} independent replica(s)",
-                   "t_reached": info["t"]},
+        "config": workload_config(args.n, world, info["t"]),
         "roofline": alu if alu is not None else hbm,
         "roofline_hbm": hbm,
         "kernels": kernels,
