@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mhd_oracle.cpp")
 _LIB = os.path.join(_HERE, "_build", "libmhd_oracle.so")
 
-LIM_FLAT, LIM_MINMOD, LIM_MC = 0, 1, 2
+LIM_FLAT, LIM_MINMOD, LIM_MC, LIM_WENOZ = 0, 1, 2, 3
 BC_PERIODIC, BC_OUTFLOW = 0, 1
 
 
@@ -44,7 +44,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("dx", ctypes.c_double * 3),
                 ("gamma", ctypes.c_double), ("glm_alpha", ctypes.c_double),
                 ("rho_floor", ctypes.c_double), ("p_floor", ctypes.c_double),
-                ("limiter", ctypes.c_int), ("bc", ctypes.c_int * 6)]
+                ("limiter", ctypes.c_int), ("bc", ctypes.c_int * 6), ("rk_order", ctypes.c_int)]
 
 
 @dataclass
@@ -59,6 +59,11 @@ class Grid:
     limiter: int = LIM_MC
     bc: tuple = (BC_PERIODIC,) * 6
     cfl: float = 0.8
+    rk_order: int = 2
+
+    @property
+    def ghost(self) -> int:
+        return 3 if self.limiter == LIM_WENOZ else 2
 
     def c(self) -> _Params:
         p = _Params()
@@ -70,6 +75,7 @@ class Grid:
         p.limiter = int(self.limiter)
         for s in range(6):
             p.bc[s] = int(self.bc[s])
+        p.rk_order = int(self.rk_order)
         return p
 
     @property
@@ -99,6 +105,7 @@ def lib():
         _lib.orc_interface_flux.argtypes = [D, D, D, L, ctypes.c_int, ctypes.c_double,
                                             ctypes.c_double]
         _lib.orc_limited_slope.argtypes = [D, D, D, L, ctypes.c_int]
+        _lib.orc_wenoz_face.argtypes = [D, D, L]
         _lib.orc_fill_ghosts.argtypes = [P, D, D]
         _lib.orc_max_speed.argtypes = [P, D, LL]
         _lib.orc_max_speed.restype = ctypes.c_double
@@ -163,9 +170,18 @@ def limited_slope(dm, dp, lim: int) -> np.ndarray:
     return out
 
 
+def wenoz_face(f: np.ndarray) -> np.ndarray:
+    """WENO-Z value at x_{i+1/2} biased towards cell i from f of shape
+    (5, n) = values at cells i-2 .. i+2."""
+    f = _f64(f)
+    out = np.empty(f.shape[1])
+    lib().orc_wenoz_face(_d(f), _d(out), f.shape[1])
+    return out
+
+
 def fill_ghosts(U: np.ndarray, grid: Grid) -> np.ndarray:
     U = _f64(U)
-    g = [2 if n > 1 else 0 for n in grid.n]
+    g = [grid.ghost if n > 1 else 0 for n in grid.n]
     nx, ny, nz = grid.n
     out = np.empty((9, nz + 2 * g[2], ny + 2 * g[1], nx + 2 * g[0]))
     p = grid.c()

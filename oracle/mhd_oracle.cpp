@@ -17,8 +17,13 @@
 //     psi <- psi exp(-alpha c_h dt / dh) of Mignone & Tzeferacos (2010),
 //     J. Comput. Phys. 229, 2117, Eq. 27.
 //   * PLM on primitive variables with the minmod or monotonised-central (MC)
-//     limiter of van Leer (1977).
-//   * RK2: two-stage, second-order (Heun / SSP) Runge-Kutta.
+//     limiter of van Leer (1977); or WENO-Z (Borges, Carmona, Costa & Don
+//     2008, J. Comput. Phys. 227, 3191: their weights with exponent 1 and the
+//     Jiang & Shu 1996 smoothness indicators), the reconstruction of the
+//     paper's own runs (Section 4.2).
+//   * RK2: two-stage, second-order (Heun / SSP) Runge-Kutta; or the
+//     three-stage third-order SSP Runge-Kutta of Shu & Osher (1988), the
+//     paper's RK3 (Section 4.2).
 //   * CFL time step from the global maximum of |v_d| + c_f,d.
 // Readings where the paper is silent are the ones stated next to each
 // function.  Everything is templated on the scalar S so that S = Dual gives
@@ -72,7 +77,7 @@ template <class S> inline S smax(S a, S b) { return val(b) > val(a) ? b : a; }
 // Primitive V = (rho, vx, vy, vz, Bx, By, Bz, p, psi)
 // Conservative U = (rho, mx, my, mz, Bx, By, Bz, E, psi)
 enum { RHO = 0, VX = 1, VY = 2, VZ = 3, BX = 4, BY = 5, BZ = 6, PRS = 7, PSI = 8, NV = 9 };
-enum { LIM_FLAT = 0, LIM_MINMOD = 1, LIM_MC = 2 };
+enum { LIM_FLAT = 0, LIM_MINMOD = 1, LIM_MC = 2, LIM_WENOZ = 3 };
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1 };
 
 struct Params {
@@ -83,7 +88,10 @@ struct Params {
   double rho_floor, p_floor;
   int limiter;
   int bc[6];
+  int rk_order;  // 2 or 3
 };
+
+inline int ghost_width(const Params& P) { return P.limiter == LIM_WENOZ ? 3 : 2; }
 
 struct Counters {
   long long rho_floor_hits;
@@ -161,6 +169,28 @@ S limited_slope(S dm, S dp, int lim) {
     mag = smin(smin(2.0 * am, 2.0 * ap), 0.5 * sabs(dm + dp));
   }
   return val(dm) > 0.0 ? mag : -mag;
+}
+
+// WENO-Z value at the face x_{i+1/2}, biased towards cell i, from the five
+// values f[0..4] at cells i-2 .. i+2 (Borges et al. 2008, exponent 1,
+// epsilon 1e-40; candidate stencils and smoothness indicators of Jiang & Shu
+// 1996).  The value at x_{i-1/2} biased towards cell i is the same function
+// of the reversed stencil.
+template <class S>
+S wenoz_face(const S f[5]) {
+  auto sq = [](S a) { return a * a; };
+  S q0 = (2.0 * f[0] - 7.0 * f[1] + 11.0 * f[2]) / 6.0;
+  S q1 = (-f[1] + 5.0 * f[2] + 2.0 * f[3]) / 6.0;
+  S q2 = (2.0 * f[2] + 5.0 * f[3] - f[4]) / 6.0;
+  S b0 = 13.0 / 12.0 * sq(f[0] - 2.0 * f[1] + f[2]) + 0.25 * sq(f[0] - 4.0 * f[1] + 3.0 * f[2]);
+  S b1 = 13.0 / 12.0 * sq(f[1] - 2.0 * f[2] + f[3]) + 0.25 * sq(f[1] - f[3]);
+  S b2 = 13.0 / 12.0 * sq(f[2] - 2.0 * f[3] + f[4]) + 0.25 * sq(3.0 * f[2] - 4.0 * f[3] + f[4]);
+  S tau = sabs(b0 - b2);
+  const double eps = 1e-40;
+  S a0 = 0.1 * (1.0 + tau / (b0 + eps));
+  S a1 = 0.6 * (1.0 + tau / (b1 + eps));
+  S a2 = 0.3 * (1.0 + tau / (b2 + eps));
+  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
 }
 
 // Physical MHD flux along the rotated normal (index n = velocity component,
@@ -383,10 +413,10 @@ template <class S>
 struct Field {
   int n[3], g[3], p[3];
   std::vector<S> a;
-  explicit Field(const int nn[3]) {
+  explicit Field(const int nn[3], int gw = 2) {
     for (int d = 0; d < 3; ++d) {
       n[d] = nn[d];
-      g[d] = nn[d] > 1 ? 2 : 0;
+      g[d] = nn[d] > 1 ? gw : 0;
       p[d] = n[d] + 2 * g[d];
     }
     a.assign((size_t)NV * p[0] * p[1] * p[2], S(0.0));
@@ -441,12 +471,29 @@ void fill_ghosts(Field<S>& f, const Params& P) {
 //   stage 1:  out = W + dt L(W)
 //   stage 2:  out = (Un + (W + dt L(W))) / 2
 // on interior cells.  W's ghosts are (re)filled here.
+// Runge-Kutta stage coefficients: out = a_n U^n + a_w (W + dt L(W)).
+inline void rk_coeffs(int order, int stage, double* a_n, double* a_w) {
+  if (stage == 1) {
+    *a_n = 0.0;
+    *a_w = 1.0;
+  } else if (order == 2) {
+    *a_n = 0.5;
+    *a_w = 0.5;
+  } else if (stage == 2) {
+    *a_n = 0.75;
+    *a_w = 0.25;
+  } else {
+    *a_n = 1.0 / 3.0;
+    *a_w = 2.0 / 3.0;
+  }
+}
+
 template <class S>
 void rk_stage(const Params& P, Field<S>& W, const Field<S>* Un, double dt, double ch,
               int stage, Field<S>& out, Counters* cnt, bool fill = true) {
   if (fill) fill_ghosts(W, P);                                        // step 1
 
-  Field<S> V(P.n);                                                    // step 2
+  Field<S> V(P.n, ghost_width(P));                                    // step 2
   {
     int c[3];
     for (c[2] = -W.g[2]; c[2] < W.n[2] + W.g[2]; ++c[2])
@@ -479,34 +526,40 @@ void rk_stage(const Params& P, Field<S>& W, const Field<S>* Un, double dt, doubl
     for (c[2] = 0; c[2] < fn[2]; ++c[2])
       for (c[1] = 0; c[1] < fn[1]; ++c[1])
         for (c[0] = 0; c[0] < fn[0]; ++c[0]) {
-          // Step 3: PLM.  Slopes of cells f-1 and f (cell index along d).
+          // Step 3: reconstruction.  Face f's left state comes from cell
+          // f-1 and its right state from cell f.
           S face[2][NV];
           for (int side = 0; side < 2; ++side) {
-            int cell = c[d] - 1 + side;          // f-1 (left), f (right)
-            S Vm[NV], V0[NV], Vp[NV], sig[NV];
-            for (int k = 0; k < NV; ++k) {
+            const int cell = c[d] - 1 + side;  // f-1 (left), f (right)
+            auto at = [&](int k, int off) {
               int a[3] = {c[0], c[1], c[2]};
-              a[d] = cell - 1;
-              Vm[k] = V.at(k, a[0], a[1], a[2]);
-              a[d] = cell;
-              V0[k] = V.at(k, a[0], a[1], a[2]);
-              a[d] = cell + 1;
-              Vp[k] = V.at(k, a[0], a[1], a[2]);
-              sig[k] = limited_slope(V0[k] - Vm[k], Vp[k] - V0[k], P.limiter);
+              a[d] = cell + off;
+              return V.at(k, a[0], a[1], a[2]);
+            };
+            S plus[NV], minus[NV];  // values at the cell's faces +1/2 and -1/2
+            if (P.limiter == LIM_WENOZ) {
+              for (int k = 0; k < NV; ++k) {
+                S st[5], rv[5];
+                for (int o = -2; o <= 2; ++o) st[o + 2] = at(k, o);
+                for (int o = 0; o < 5; ++o) rv[o] = st[4 - o];
+                plus[k] = wenoz_face(st);
+                minus[k] = wenoz_face(rv);
+              }
+            } else {
+              for (int k = 0; k < NV; ++k) {
+                S sig = limited_slope(at(k, 0) - at(k, -1), at(k, 1) - at(k, 0), P.limiter);
+                plus[k] = at(k, 0) + 0.5 * sig;
+                minus[k] = at(k, 0) - 0.5 * sig;
+              }
             }
             // Reading: if either face value of this cell has rho <= 0 or
-            // p <= 0, the cell falls back to a zero slope (all variables).
-            bool bad = false;
-            for (int sgn = -1; sgn <= 1; sgn += 2) {
-              S r = V0[RHO] + 0.5 * sgn * sig[RHO];
-              S p = V0[PRS] + 0.5 * sgn * sig[PRS];
-              if (val(r) <= 0.0 || val(p) <= 0.0) bad = true;
+            // p <= 0, the cell falls back to its own (flat) value.
+            bool bad = val(plus[RHO]) <= 0.0 || val(minus[RHO]) <= 0.0 ||
+                       val(plus[PRS]) <= 0.0 || val(minus[PRS]) <= 0.0;
+            for (int k = 0; k < NV; ++k) {
+              const S v0 = at(k, 0);
+              face[side][k] = bad ? v0 : (side == 0 ? plus[k] : minus[k]);
             }
-            if (bad)
-              for (int k = 0; k < NV; ++k) sig[k] = S(0.0);
-            for (int k = 0; k < NV; ++k)
-              face[side][k] = side == 0 ? V0[k] + 0.5 * sig[k]   // V^L_{f} from cell f-1
-                                        : V0[k] - 0.5 * sig[k];  // V^R_{f} from cell f
           }
           // Step 4: GLM + HLLD.
           S F[NV];
@@ -527,7 +580,9 @@ void rk_stage(const Params& P, Field<S>& W, const Field<S>* Un, double dt, doubl
         }
   }
 
-  // RK2 combination.
+  // Runge-Kutta combination.
+  double a_n, a_w;
+  rk_coeffs(P.rk_order, stage, &a_n, &a_w);
   int c[3];
   for (c[2] = 0; c[2] < P.n[2]; ++c[2])
     for (c[1] = 0; c[1] < P.n[1]; ++c[1])
@@ -538,7 +593,7 @@ void rk_stage(const Params& P, Field<S>& W, const Field<S>* Un, double dt, doubl
           if (stage == 1)
             out.at(k, c[0], c[1], c[2]) = s1;
           else
-            out.at(k, c[0], c[1], c[2]) = 0.5 * (Un->at(k, c[0], c[1], c[2]) + s1);
+            out.at(k, c[0], c[1], c[2]) = a_n * Un->at(k, c[0], c[1], c[2]) + a_w * s1;
         }
 }
 
@@ -572,13 +627,21 @@ inline double damping_factor(const Params& P, double dt, double ch) {
   return std::exp(-P.glm_alpha * ch * dt / dh);
 }
 
-// One full RK2 step with frozen dt and c_h, followed by the GLM damping
+// One full Runge-Kutta step (RK2, or SSP-RK3 when rk_order == 3) with frozen
+// dt and c_h, followed by the GLM damping
 // psi <- psi exp(-alpha c_h dt / dh_min) (Mignone & Tzeferacos 2010, Eq. 27).
 template <class S>
 void rk2_step(const Params& P, Field<S>& U, double dt, double ch, Counters* cnt) {
-  Field<S> U1(P.n), Un1(P.n);
+  const int gw = ghost_width(P);
+  Field<S> U1(P.n, gw), Un1(P.n, gw);
   rk_stage(P, U, (const Field<S>*)nullptr, dt, ch, 1, U1, cnt);
-  rk_stage(P, U1, &U, dt, ch, 2, Un1, cnt);
+  if (P.rk_order == 3) {
+    Field<S> U2(P.n, gw);
+    rk_stage(P, U1, &U, dt, ch, 2, U2, cnt);
+    rk_stage(P, U2, &U, dt, ch, 3, Un1, cnt);
+  } else {
+    rk_stage(P, U1, &U, dt, ch, 2, Un1, cnt);
+  }
   const double damp = damping_factor(P, dt, ch);
   int c[3];
   for (c[2] = 0; c[2] < P.n[2]; ++c[2])
@@ -632,6 +695,7 @@ struct orc_params {
   double gamma, glm_alpha, rho_floor, p_floor;
   int limiter;
   int bc[6];
+  int rk_order;
 };
 
 static Params to_params(const orc_params* p) {
@@ -646,6 +710,7 @@ static Params to_params(const orc_params* p) {
   P.p_floor = p->p_floor;
   P.limiter = p->limiter;
   for (int s = 0; s < 6; ++s) P.bc[s] = p->bc[s];
+  P.rk_order = p->rk_order == 3 ? 3 : 2;
   return P;
 }
 
@@ -703,11 +768,21 @@ void orc_limited_slope(const double* dm, const double* dp, double* out, long n, 
   for (long i = 0; i < n; ++i) out[i] = limited_slope(dm[i], dp[i], lim);
 }
 
+// WENO-Z face values: f is [5][n] (cells i-2..i+2), out[n] = value at
+// x_{i+1/2} biased towards cell i.
+void orc_wenoz_face(const double* f, double* out, long n) {
+  for (long i = 0; i < n; ++i) {
+    double st[5];
+    for (int o = 0; o < 5; ++o) st[o] = f[o * n + i];
+    out[i] = wenoz_face(st);
+  }
+}
+
 // Ghost fill on an interior-only array, returning the padded array
 // ([9][nz+2gz][ny+2gy][nx+2gx]).
 void orc_fill_ghosts(const orc_params* p, const double* U, double* padded) {
   Params P = to_params(p);
-  Field<double> f(P.n);
+  Field<double> f(P.n, ghost_width(P));
   load_interior(f, U, nullptr);
   fill_ghosts(f, P);
   std::memcpy(padded, f.a.data(), f.a.size() * sizeof(double));
@@ -716,7 +791,7 @@ void orc_fill_ghosts(const orc_params* p, const double* U, double* padded) {
 // lambda = max |v_d| + c_f,d (see max_speed).
 double orc_max_speed(const orc_params* p, const double* U, long long counters[2]) {
   Params P = to_params(p);
-  Field<double> f(P.n);
+  Field<double> f(P.n, ghost_width(P));
   load_interior(f, U, nullptr);
   Counters cnt = {0, 0};
   double lam = max_speed(P, f, &cnt);
@@ -731,7 +806,7 @@ double orc_max_speed(const orc_params* p, const double* U, long long counters[2]
 void orc_stage(const orc_params* p, const double* W, const double* Un, double dt, double ch,
                int stage, double* out, long long counters[2]) {
   Params P = to_params(p);
-  Field<double> w(P.n), un(P.n), o(P.n);
+  Field<double> w(P.n, ghost_width(P)), un(P.n, ghost_width(P)), o(P.n, ghost_width(P));
   load_interior(w, W, nullptr);
   if (Un) load_interior(un, Un, nullptr);
   Counters cnt = {0, 0};
@@ -751,7 +826,7 @@ void orc_stage(const orc_params* p, const double* W, const double* Un, double dt
 void orc_stage_padded(const orc_params* p, const double* Wp, const double* Un, double dt,
                       double ch, int stage, int damp, double* out) {
   Params P = to_params(p);
-  Field<double> w(P.n), un(P.n), o(P.n);
+  Field<double> w(P.n, ghost_width(P)), un(P.n, ghost_width(P)), o(P.n, ghost_width(P));
   std::memcpy(w.a.data(), Wp, w.a.size() * sizeof(double));
   if (Un) load_interior(un, Un, nullptr);
   rk_stage(P, w, Un ? &un : nullptr, dt, ch, stage, o, (Counters*)nullptr, false);
@@ -772,7 +847,7 @@ void orc_stage_padded(const orc_params* p, const double* Wp, const double* Un, d
 double orc_run(const orc_params* p, double* U, int nsteps, double cfl, double t0, double t_end,
                double* dts, double* chs, long long counters[2]) {
   Params P = to_params(p);
-  Field<double> f(P.n);
+  Field<double> f(P.n, ghost_width(P));
   load_interior(f, U, nullptr);
   Counters cnt = {0, 0};
   double t = t0;
@@ -810,7 +885,7 @@ double orc_run(const orc_params* p, double* U, int nsteps, double cfl, double t0
 void orc_run_jvp(const orc_params* p, double* U, double* dU, int nsteps, const double* dts,
                  const double* chs) {
   Params P = to_params(p);
-  Field<Dual> f(P.n);
+  Field<Dual> f(P.n, ghost_width(P));
   load_interior(f, U, dU);
   for (int s = 0; s < nsteps; ++s) rk2_step(P, f, dts[s], chs[s], (Counters*)nullptr);
   store_interior(f, U, dU);

@@ -20,7 +20,7 @@ from dataclasses import dataclass, field, replace
 import numpy as np
 
 RHO, VX, VY, VZ, BX, BY, BZ, PRS, PSI = range(9)
-LIM_FLAT, LIM_MINMOD, LIM_MC = 0, 1, 2
+LIM_FLAT, LIM_MINMOD, LIM_MC, LIM_WENOZ = 0, 1, 2, 3
 BC_PERIODIC, BC_OUTFLOW = 0, 1
 FP64, FP32 = 0, 1
 
@@ -42,6 +42,7 @@ class Problem:
     steps: int = 20
     t_end: float = 0.0            # > 0: clamp the last step to reach t_end
     precision: int = FP64
+    rk_order: int = 2             # 2: RK2; 3: SSP-RK3
     seed: int = 0
     params: dict = field(default_factory=dict)
 

@@ -21,7 +21,7 @@ RHO, VX, VY, VZ, BX, BY, BZ, PRS, PSI = range(9)
 def grid_of(pb: Problem) -> orc.Grid:
     return orc.Grid(n=pb.n, dx=pb.dx, gamma=pb.gamma, glm_alpha=pb.glm_alpha,
                     rho_floor=pb.rho_floor, p_floor=pb.p_floor, limiter=pb.limiter,
-                    bc=pb.bc, cfl=pb.cfl)
+                    bc=pb.bc, cfl=pb.cfl, rk_order=pb.rk_order)
 
 
 def cons_of(pb: Problem) -> np.ndarray:
