@@ -73,12 +73,14 @@ typedef struct mhd_config {
                             be set on both sides of a dimension)              */
   int precision;         /* MHD_FP64 or MHD_FP32                              */
   int flags;             /* MHD_FLAG_* (ADJOINT reserves adjoint buffers)     */
+  int rk_order;          /* 2: RK2 (default); 3: SSP-RK3 of Shu & Osher,
+                            the time integrator of the paper's runs          */
 } mhd_config;
 
 typedef struct mhd_ctx mhd_ctx;
 
 /* Fills *cfg with defaults: gamma 5/3, cfl 0.8, glm_alpha 0.1, floors 1e-12,
- * MC limiter, periodic BCs, FP64, unit domain, n = (1,1,1). */
+ * MC limiter, periodic BCs, FP64, RK2, unit domain, n = (1,1,1). */
 int mhd_config_default(mhd_config* cfg);
 
 /* Device workspace the context needs for cfg (bytes, before alignment). */
@@ -110,8 +112,9 @@ int mhd_get_state(mhd_ctx* ctx, double* U, int where, int kind);
  * dt = cfl / (c_h sum_d 1/dx_d)).  Synchronises.  Either pointer may be NULL. */
 int mhd_dt(mhd_ctx* ctx, double* dt, double* ch);
 
-/* One RK2 step:  U1 = U + dt L(U);  U' = (U + U1 + dt L(U1)) / 2;  then
- * psi' *= exp(-glm_alpha c_h dt / dh_min).  dt > 0 and ch > 0 are used as
+/* One Runge-Kutta step.  RK2:  U1 = U + dt L(U);  U' = (U + U1 + dt L(U1))/2.
+ * SSP-RK3 (rk_order 3):  U1 = U + dt L(U);  U2 = 3/4 U + 1/4 (U1 + dt L(U1));
+ * U' = 1/3 U + 2/3 (U2 + dt L(U2)).  Then psi' *= exp(-glm_alpha c_h dt / dh_min).  dt > 0 and ch > 0 are used as
  * given; dt <= 0 uses the CFL rule on the device (clamped to t_end when
  * t_end > 0); ch <= 0 uses c_h = lambda of the current state.  Does not
  * synchronise: dt and c_h stay on the device (see mhd_step_info). */
@@ -140,7 +143,8 @@ int mhd_flux_batch(const void* VL, const void* VR, void* F, long long nface, int
                    double ch, double gamma, int precision, void* stream);
 
 /* Discrete adjoint of one RK2 step (reverse-mode derivative of mhd_step with
- * dt and c_h frozen):  lam_n = (dU^{n+1}/dU^n)^T lam_np1.
+ * dt and c_h frozen):  lam_n = (dU^{n+1}/dU^n)^T lam_np1.  Needs RK2 and a
+ * PLM limiter (MHD_LIM_FLAT / MINMOD / MC).
  * U_n: the step's input state; lam_np1, lam_n: adjoints; all device float64
  * arrays [9][nz][ny][nx].  lam_n may not alias lam_np1.  Needs a context
  * created with MHD_FLAG_ADJOINT and MHD_FP64.  Does not change the context's
@@ -150,12 +154,12 @@ int mhd_adjoint_step(mhd_ctx* ctx, const double* U_n, const double* lam_np1, dou
 
 /* Per-kernel timing of the context's launches with CUDA events recorded on
  * the context's stream (off by default; the events are created on the host
- * when enabled).  Kernel classes: 0 = step prepare, 1 = RK stage 1,
- * 2 = RK stage 2, 3 = max-wave-speed reduction.  mhd_profile_read()
- * synchronises, returns the launch count and total milliseconds per class
- * since the last read, and clears the record. */
+ * when enabled).  Kernel classes: 0 = step prepare, 1 = first RK stage,
+ * 2 = last RK stage, 3 = max-wave-speed reduction, 4 = middle stage of
+ * SSP-RK3.  mhd_profile_read() synchronises, returns the launch count and
+ * total milliseconds per class since the last read, and clears the record. */
 int mhd_profile_enable(mhd_ctx* ctx, int enable);
-int mhd_profile_read(mhd_ctx* ctx, long long counts[4], double ms[4]);
+int mhd_profile_read(mhd_ctx* ctx, long long counts[5], double ms[5]);
 
 /* Conservation sums for callers that can't allocate device memory: a host
  * application whose GPU memory is owned by another allocator, a code that

@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmhd_gb300.so")
 
 MHD_OK, MHD_ERR_INVALID, MHD_ERR_NOMEM, MHD_ERR_CUDA = 0, -1, -2, -3
 MHD_ERR_NONFINITE, MHD_ERR_TIMEOUT, MHD_ERR_STATE = -4, -5, -6
-MHD_LIM_FLAT, MHD_LIM_MINMOD, MHD_LIM_MC = 0, 1, 2
+MHD_LIM_FLAT, MHD_LIM_MINMOD, MHD_LIM_MC, MHD_LIM_WENOZ = 0, 1, 2, 3
 MHD_BC_PERIODIC, MHD_BC_OUTFLOW = 0, 1
 MHD_FP64, MHD_FP32 = 0, 1
 MHD_HOST, MHD_DEVICE = 0, 1
@@ -54,7 +54,8 @@ class mhd_config(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("glm_alpha", ctypes.c_double),
                 ("rho_floor", ctypes.c_double), ("p_floor", ctypes.c_double),
                 ("t_end", ctypes.c_double), ("limiter", ctypes.c_int),
-                ("bc", ctypes.c_int * 6), ("precision", ctypes.c_int), ("flags", ctypes.c_int)]
+                ("bc", ctypes.c_int * 6), ("precision", ctypes.c_int), ("flags", ctypes.c_int),
+                ("rk_order", ctypes.c_int)]
 
 
 _lib = None
@@ -216,13 +217,15 @@ class Config:
     bc: tuple = (MHD_BC_PERIODIC,) * 6
     precision: int = MHD_FP64
     flags: int = 0
+    rk_order: int = 2
 
     @classmethod
     def from_problem(cls, pb, precision=None, flags: int = 0) -> "Config":
         return cls(n=tuple(pb.n), xmin=tuple(pb.xmin), xmax=tuple(pb.xmax), gamma=pb.gamma,
                    cfl=pb.cfl, glm_alpha=pb.glm_alpha, rho_floor=pb.rho_floor,
                    p_floor=pb.p_floor, t_end=pb.t_end, limiter=pb.limiter, bc=tuple(pb.bc),
-                   precision=pb.precision if precision is None else precision, flags=flags)
+                   precision=pb.precision if precision is None else precision, flags=flags,
+                   rk_order=getattr(pb, "rk_order", 2))
 
     def c(self) -> mhd_config:
         c = mhd_config()
@@ -233,6 +236,7 @@ class Config:
         c.gamma, c.cfl, c.glm_alpha = self.gamma, self.cfl, self.glm_alpha
         c.rho_floor, c.p_floor, c.t_end = self.rho_floor, self.p_floor, self.t_end
         c.limiter, c.precision, c.flags = int(self.limiter), int(self.precision), int(self.flags)
+        c.rk_order = int(self.rk_order)
         for s in range(6):
             c.bc[s] = int(self.bc[s])
         return c
@@ -318,11 +322,11 @@ class MHD:
 
     def profile_read(self):
         """{kernel class: (launches, total ms)} since the last read."""
-        cnt = (ctypes.c_longlong * 4)()
-        ms = (ctypes.c_double * 4)()
+        cnt = (ctypes.c_longlong * 5)()
+        ms = (ctypes.c_double * 5)()
         _check(lib().mhd_profile_read(self.ctx, cnt, ms), self.ctx, "mhd_profile_read")
-        names = ("prep", "stage1", "stage2", "max_speed")
-        return {names[k]: (int(cnt[k]), float(ms[k])) for k in range(4)}
+        names = ("prep", "stage1", "stage2", "max_speed", "stage_mid")
+        return {names[k]: (int(cnt[k]), float(ms[k])) for k in range(5)}
 
     def adjoint_step(self, U_n, lam_np1, lam_n, dt: float, ch: float):
         mhd_adjoint_step(self.ctx, U_n, lam_np1, lam_n, dt, ch)

@@ -111,8 +111,12 @@ static int validate(const mhd_config* c, char* msg, size_t len) {
     snprintf(msg, len, "bad precision %d", c->precision);
     return MHD_ERR_INVALID;
   }
-  if ((c->flags & MHD_FLAG_ADJOINT) && c->precision != MHD_FP64) {
-    snprintf(msg, len, "the adjoint needs MHD_FP64");
+  if (c->rk_order != 2 && c->rk_order != 3) {
+    snprintf(msg, len, "rk_order must be 2 or 3");
+    return MHD_ERR_INVALID;
+  }
+  if ((c->flags & MHD_FLAG_ADJOINT) && (c->precision != MHD_FP64 || c->rk_order != 2)) {
+    snprintf(msg, len, "the adjoint needs MHD_FP64 and RK2");
     return MHD_ERR_INVALID;
   }
   return MHD_OK;
@@ -185,6 +189,7 @@ int mhd_config_default(mhd_config* cfg) {
   for (int s = 0; s < 6; ++s) cfg->bc[s] = MHD_BC_PERIODIC;
   cfg->precision = MHD_FP64;
   cfg->flags = 0;
+  cfg->rk_order = 2;
   return MHD_OK;
 }
 
@@ -196,7 +201,9 @@ int mhd_workspace_bytes(const mhd_config* cfg, size_t* bytes) {
   fill_grid(cfg, &g);
   const size_t es = cfg->precision == MHD_FP64 ? 8 : 4;
   const size_t state = align256((size_t)9 * g.ncell * es);
-  size_t total = 2 * state + align256(sizeof(Scalars)) + align256(kSumBlocks * 8 * sizeof(double));
+  const int nstate = cfg->rk_order == 3 ? 3 : 2;
+  size_t total = nstate * state + align256(sizeof(Scalars)) +
+                 align256(kSumBlocks * 8 * sizeof(double));
   if (cfg->flags & MHD_FLAG_ADJOINT) total += align256(mhd::adjoint_scratch_bytes(g));
   *bytes = total;
   return MHD_OK;
@@ -241,6 +248,11 @@ int mhd_create(const mhd_config* cfg, void* d_workspace, size_t bytes, void* str
   off += align256(c->state_bytes);
   c->Ub = c->ws + off;
   off += align256(c->state_bytes);
+  c->Uc = nullptr;
+  if (cfg->rk_order == 3) {
+    c->Uc = c->ws + off;
+    off += align256(c->state_bytes);
+  }
   c->scal = reinterpret_cast<Scalars*>(c->ws + off);
   off += align256(sizeof(Scalars));
   c->partials = reinterpret_cast<double*>(c->ws + off);
@@ -422,23 +434,34 @@ int mhd_step(mhd_ctx* c, double dt, double ch) {
     ProfScope ps(c, 0);
     CK(c, mhd::launch_prep(a, &c->scal->sc, &c->scal->lam_bits, &c->scal->status, c->stream));
   }
-  for (int stage = 1; stage <= 2; ++stage) {
-    ProfScope ps(c, stage);
-    if (c->esize == 8) {
-      double* A = static_cast<double*>(c->Ua);
-      double* B = static_cast<double*>(c->Ub);
-      CK(c, mhd::launch_stage<double>(c->grid, stage, stage == 1 ? A : B,
-                                      stage == 1 ? nullptr : A, stage == 1 ? B : A,
-                                      &c->scal->sc, &c->scal->lam_bits, c->scal->floor_cnt,
-                                      c->stream));
-    } else {
-      float* A = static_cast<float*>(c->Ua);
-      float* B = static_cast<float*>(c->Ub);
-      CK(c, mhd::launch_stage<float>(c->grid, stage, stage == 1 ? A : B,
-                                     stage == 1 ? nullptr : A, stage == 1 ? B : A,
+  // stage sequence: (kernel stage, profile class, input, U^n, output, a_n, a_w)
+  struct St { int kind, cls; void *win, *un, *out; double an, aw; };
+  St seq[3];
+  int nst;
+  if (c->cfg.rk_order == 3) {
+    seq[0] = {1, 1, c->Ua, nullptr, c->Ub, 0.0, 1.0};
+    seq[1] = {3, 4, c->Ub, c->Ua, c->Uc, 0.75, 0.25};
+    seq[2] = {2, 2, c->Uc, c->Ua, c->Ua, 1.0 / 3.0, 2.0 / 3.0};
+    nst = 3;
+  } else {
+    seq[0] = {1, 1, c->Ua, nullptr, c->Ub, 0.0, 1.0};
+    seq[1] = {2, 2, c->Ub, c->Ua, c->Ua, 0.5, 0.5};
+    nst = 2;
+  }
+  for (int i = 0; i < nst; ++i) {
+    const St& q = seq[i];
+    ProfScope ps(c, q.cls);
+    if (c->esize == 8)
+      CK(c, mhd::launch_stage<double>(c->grid, q.kind, static_cast<const double*>(q.win),
+                                      static_cast<const double*>(q.un),
+                                      static_cast<double*>(q.out), &c->scal->sc,
+                                      &c->scal->lam_bits, c->scal->floor_cnt, c->stream, q.an,
+                                      q.aw));
+    else
+      CK(c, mhd::launch_stage<float>(c->grid, q.kind, static_cast<const float*>(q.win),
+                                     static_cast<const float*>(q.un), static_cast<float*>(q.out),
                                      &c->scal->sc, &c->scal->lam_bits, c->scal->floor_cnt,
-                                     c->stream));
-    }
+                                     c->stream, q.an, q.aw));
   }
   c->lam_valid = true;
   return MHD_OK;
@@ -523,9 +546,9 @@ int mhd_profile_enable(mhd_ctx* c, int enable) {
   return MHD_OK;
 }
 
-int mhd_profile_read(mhd_ctx* c, long long counts[4], double ms[4]) {
+int mhd_profile_read(mhd_ctx* c, long long counts[5], double ms[5]) {
   if (!c || !counts || !ms) return MHD_ERR_INVALID;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 5; ++k) {
     counts[k] = 0;
     ms[k] = 0.0;
   }

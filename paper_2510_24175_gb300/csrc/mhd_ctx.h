@@ -35,6 +35,7 @@ struct mhd_ctx {
   size_t ws_bytes;
   void* Ua;              // U^n (and U^{n+1}, in place)
   void* Ub;              // U1 / staging
+  void* Uc;              // U2 of SSP-RK3 (rk_order 3), else null
   mhd::Scalars* scal;
   double* partials;
   void* adj;             // adjoint scratch (MHD_FLAG_ADJOINT)

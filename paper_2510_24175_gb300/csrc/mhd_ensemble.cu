@@ -100,6 +100,8 @@ __device__ __forceinline__ void ens_stage(const EnsArgs& a, unsigned char* smem,
     p.uout = STAGE == 1 ? B.Ub : B.Ua;
     p.lam_bits = &B.lam_bits[B.cur];
     p.floor_cnt = B.floor_cnt;
+    p.a_n = 0.5f;
+    p.a_w = 0.5f;
     const StepScalars sc = B.sc;
     const long long j = it - B.item0;
     const int bx = (int)(j % B.ntx);
@@ -171,7 +173,7 @@ static int ens_validate(const mhd_config* cfgs, int nbox) {
     size_t bytes;
     if (mhd_workspace_bytes(&cfgs[b], &bytes) != MHD_OK) return MHD_ERR_INVALID;
     if (cfgs[b].precision != MHD_FP32 || cfgs[b].n[1] < 2 || cfgs[b].n[2] < 2 ||
-        (cfgs[b].flags & MHD_FLAG_ADJOINT))
+        (cfgs[b].flags & MHD_FLAG_ADJOINT) || cfgs[b].rk_order != 2)
       return MHD_ERR_INVALID;
   }
   return MHD_OK;

@@ -27,11 +27,14 @@ struct Grid {
 template <class T>
 Phys<T> make_phys(const Grid& g);
 
-// Stage kernel (mhd_stage_f64.cu / mhd_stage_f32.cu).
+// Stage kernel (mhd_stage_f64.cu / mhd_stage_f32.cu).  stage 1: first stage;
+// 2: last stage (combination with a_n, a_w + damping + wave-speed
+// reduction); 3: SSP-RK3 middle stage (combination only).
 template <class T>
 cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T* uout,
                          const StepScalars* sc, unsigned long long* lam_bits,
-                         unsigned long long* floor_cnt, cudaStream_t stream);
+                         unsigned long long* floor_cnt, cudaStream_t stream,
+                         double a_n = 0.5, double a_w = 0.5);
 
 // Shared-memory bytes and threads of the stage kernel for this grid.
 template <class T>

@@ -1,8 +1,10 @@
-// Fused RK2 stage kernel: one launch performs, for its tile of cells, the five
-// per-stage steps of Section 3.2 (boundary calculation, cons->prim,
-// reconstruction, Riemann solver, right-hand side) and the Runge-Kutta
-// combination; stage 2 also applies the GLM damping (Mignone & Tzeferacos
-// 2010, Eq. 27) and reduces the next step's max wave speed.
+// Fused Runge-Kutta stage kernel: one launch performs, for its tile of cells,
+// the five per-stage steps of Section 3.2 (boundary calculation,
+// cons->prim, reconstruction, Riemann solver, right-hand side) and the
+// Runge-Kutta combination.  STAGE 1: out = W + dt L(W); STAGE 2 (last stage):
+// out = a_n U^n + a_w (W + dt L(W)), then the GLM damping (Mignone &
+// Tzeferacos 2010, Eq. 27) and the next step's max-wave-speed reduction;
+// STAGE 3 (SSP-RK3 middle stage): the combination without the epilogue.
 //
 // Decomposition: a CTA owns a 32 x TY column tile in (x, y) and marches in z
 // over p.tz planes.  Ghost zones are never stored: the boundary calculation
@@ -47,6 +49,7 @@ struct StageParams {
   int bc_lo[3], bc_hi[3];
   int limiter;
   int tz;         // planes per CTA
+  T a_n, a_w;     // combining stages: out = a_n U^n + a_w (W + dt L(W))
   Phys<T> ph;
   const StepScalars* sc;
   unsigned long long* lam_bits;   // stage 2: max wave speed as FP64 bits
@@ -381,7 +384,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
           if constexpr (STAGE == 1) {
             unew[q] = s1;
           } else {
-            unew[q] = T(0.5) * (p.un[q * p.sv + off] + s1);
+            unew[q] = p.a_n * p.un[q * p.sv + off] + p.a_w * s1;
           }
         }
         if constexpr (STAGE == 2) unew[kPSI] *= damp;

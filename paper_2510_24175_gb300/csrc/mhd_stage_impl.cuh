@@ -50,8 +50,11 @@ void stage_shape(const Grid& g, size_t* smem, int* threads, int* ty) {
 template <class T>
 cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T* uout,
                          const StepScalars* sc, unsigned long long* lam_bits,
-                         unsigned long long* floor_cnt, cudaStream_t stream) {
+                         unsigned long long* floor_cnt, cudaStream_t stream, double a_n,
+                         double a_w) {
   StageParams<T> p;
+  p.a_n = T(a_n);
+  p.a_w = T(a_w);
   p.win = win;
   p.un = un;
   p.uout = uout;
@@ -72,17 +75,20 @@ cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T*
   if (g.ndim == 3) {
     using S = StageShape3D<T>;
     dim3 grid((g.n[0] + 31) / 32, (g.n[1] + S::TY - 1) / S::TY, (g.n[2] + p.tz - 1) / p.tz);
-    return stage == 1 ? launch_one<T, S::TY, S::NW, 1, true>(p, grid, stream)
-                      : launch_one<T, S::TY, S::NW, 2, true>(p, grid, stream);
+    if (stage == 1) return launch_one<T, S::TY, S::NW, 1, true>(p, grid, stream);
+    if (stage == 2) return launch_one<T, S::TY, S::NW, 2, true>(p, grid, stream);
+    return launch_one<T, S::TY, S::NW, 3, true>(p, grid, stream);
   }
   if (g.ndim == 2) {
     dim3 grid((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, 1);
-    return stage == 1 ? launch_one<T, 8, 8, 1, false>(p, grid, stream)
-                      : launch_one<T, 8, 8, 2, false>(p, grid, stream);
+    if (stage == 1) return launch_one<T, 8, 8, 1, false>(p, grid, stream);
+    if (stage == 2) return launch_one<T, 8, 8, 2, false>(p, grid, stream);
+    return launch_one<T, 8, 8, 3, false>(p, grid, stream);
   }
   dim3 grid((g.n[0] + 31) / 32, 1, 1);
-  return stage == 1 ? launch_one<T, 1, 1, 1, false>(p, grid, stream)
-                    : launch_one<T, 1, 1, 2, false>(p, grid, stream);
+  if (stage == 1) return launch_one<T, 1, 1, 1, false>(p, grid, stream);
+  if (stage == 2) return launch_one<T, 1, 1, 2, false>(p, grid, stream);
+  return launch_one<T, 1, 1, 3, false>(p, grid, stream);
 }
 
 }  // namespace mhd

@@ -243,3 +243,32 @@ def test_fp32_turbulent_box_50_steps_error_vs_oracle():
     print("fp32 turbulent 64^3 x 50 steps rel L1:", err)
     assert np.all(err <= 2e-6), err
     assert cnt == {"rho_floor": 0, "p_floor": 0, "status": 0}
+
+
+# ------------------------------------------------------------------ SSP-RK3 --
+@pytest.mark.parametrize("n,bc,lim", [((40, 20, 12), 0, orc.LIM_MC),
+                                      ((35, 18, 10), 1, orc.LIM_MINMOD),
+                                      ((48, 40, 1), 0, orc.LIM_MC)])
+def test_ssp_rk3_matches_oracle(n, bc, lim):
+    pb = Problem("random_smooth", n, seed=8, bc=(bc,) * 6, limiter=lim, rk_order=3)
+    _compare_run(pb, 3)
+
+
+def test_ssp_rk3_brio_wu_short_time_and_fp32():
+    pb = inputs.brio_wu(1024)
+    pb.t_end, pb.rk_order = 0.005, 3
+    ref = oracle_run(pb, 100000, t_end=pb.t_end)
+    U, hist, cnt = gpu_run(pb, 100000)
+    assert len(hist) == int(np.count_nonzero(ref.dts))
+    assert np.all(rel_l1(U, ref.U) <= TOL64)
+    pb3 = inputs.orszag_tang_3d(8).with_n((40, 24, 16))
+    pb3.rk_order = 3
+    _compare_run(pb3, 3, tol=TOL32, precision=1)
+
+
+def test_ssp_rk3_rejected_for_adjoint_and_ensemble():
+    import paper_2510_24175_gb300 as m
+    with pytest.raises(m.MHDError):
+        m.MHD(m.Config(n=(16, 8, 4), rk_order=3, flags=m.MHD_FLAG_ADJOINT))
+    with pytest.raises(m.MHDError):
+        m.Ensemble([m.Config(n=(16, 16, 16), precision=m.MHD_FP32, rk_order=3)])
