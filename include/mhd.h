@@ -48,7 +48,10 @@ enum {
   MHD_ERR_STATE = -6      /* call out of order (e.g. step before set_state) */
 };
 
-enum { MHD_LIM_FLAT = 0, MHD_LIM_MINMOD = 1, MHD_LIM_MC = 2 };
+/* Reconstruction: flat (first order), PLM with minmod or MC limiter, or
+ * WENO-Z (Borges et al. 2008; the reconstruction of the paper's runs,
+ * Section 4.2; needs active dimensions of at least 3 cells). */
+enum { MHD_LIM_FLAT = 0, MHD_LIM_MINMOD = 1, MHD_LIM_MC = 2, MHD_LIM_WENOZ = 3 };
 enum { MHD_BC_PERIODIC = 0, MHD_BC_OUTFLOW = 1 };
 /* MHD_FP64: all arithmetic in FP64.  MHD_FP32: FP32 state and stage
  * arithmetic; FP64 for the time-step reduction result and dt, the
@@ -68,7 +71,7 @@ typedef struct mhd_config {
   double rho_floor;      /* absolute floors of cons->prim (counted)           */
   double p_floor;
   double t_end;          /* > 0: CFL steps are clamped to end exactly at t_end */
-  int limiter;           /* MHD_LIM_*                                         */
+  int limiter;           /* MHD_LIM_* (reconstruction)                        */
   int bc[6];             /* MHD_BC_* for x-, x+, y-, y+, z-, z+ (periodic must
                             be set on both sides of a dimension)              */
   int precision;         /* MHD_FP64 or MHD_FP32                              */

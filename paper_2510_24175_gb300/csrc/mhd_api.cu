@@ -94,10 +94,16 @@ static int validate(const mhd_config* c, char* msg, size_t len) {
     snprintf(msg, len, "bad physics constant (gamma > 1, 0 < cfl <= 1, alpha/floors >= 0)");
     return MHD_ERR_INVALID;
   }
-  if (c->limiter < MHD_LIM_FLAT || c->limiter > MHD_LIM_MC) {
+  if (c->limiter < MHD_LIM_FLAT || c->limiter > MHD_LIM_WENOZ) {
     snprintf(msg, len, "bad limiter %d", c->limiter);
     return MHD_ERR_INVALID;
   }
+  if (c->limiter == MHD_LIM_WENOZ)
+    for (int d = 0; d < 3; ++d)
+      if (c->n[d] == 2) {
+        snprintf(msg, len, "WENO-Z needs active dimensions of at least 3 cells");
+        return MHD_ERR_INVALID;
+      }
   for (int d = 0; d < 3; ++d) {
     const int lo = c->bc[2 * d], hi = c->bc[2 * d + 1];
     if ((lo != MHD_BC_PERIODIC && lo != MHD_BC_OUTFLOW) ||
@@ -115,8 +121,9 @@ static int validate(const mhd_config* c, char* msg, size_t len) {
     snprintf(msg, len, "rk_order must be 2 or 3");
     return MHD_ERR_INVALID;
   }
-  if ((c->flags & MHD_FLAG_ADJOINT) && (c->precision != MHD_FP64 || c->rk_order != 2)) {
-    snprintf(msg, len, "the adjoint needs MHD_FP64 and RK2");
+  if ((c->flags & MHD_FLAG_ADJOINT) &&
+      (c->precision != MHD_FP64 || c->rk_order != 2 || c->limiter == MHD_LIM_WENOZ)) {
+    snprintf(msg, len, "the adjoint needs MHD_FP64, RK2 and a PLM limiter");
     return MHD_ERR_INVALID;
   }
   return MHD_OK;

@@ -26,7 +26,7 @@ namespace mhd {
 
 enum { kRHO = 0, kVX = 1, kVY = 2, kVZ = 3, kBX = 4, kBY = 5, kBZ = 6, kPRS = 7, kPSI = 8,
        kNV = 9 };
-enum { kLimFlat = 0, kLimMinmod = 1, kLimMC = 2 };
+enum { kLimFlat = 0, kLimMinmod = 1, kLimMC = 2, kLimWenoz = 3 };
 enum { kBcPeriodic = 0, kBcOutflow = 1 };
 enum { kFloorRho = 1u, kFloorP = 2u };
 

@@ -66,6 +66,14 @@ __host__ __device__ __forceinline__ int remap(int i, int n, int lo, int hi) {
   return i;
 }
 
+// Same for a three-cell-deep halo (WENO-Z; active dimensions need n >= 3).
+__host__ __device__ __forceinline__ int remap3(int i, int n, int lo, int hi) {
+  i = min(i, n + 2);
+  if (i < 0) return lo == kBcPeriodic ? i + n : 0;
+  if (i >= n) return hi == kBcPeriodic ? i - n : n - 1;
+  return i;
+}
+
 template <int TY, bool ZACT>
 struct TileGeom {
   static constexpr int TX = 32;

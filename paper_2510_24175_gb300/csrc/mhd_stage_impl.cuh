@@ -3,6 +3,7 @@
 #pragma once
 
 #include "mhd_internal.h"
+#include "mhd_stage_weno.cuh"
 
 namespace mhd {
 
@@ -29,8 +30,38 @@ static cudaError_t launch_one(const StageParams<T>& p, dim3 grid, cudaStream_t s
   return cudaGetLastError();
 }
 
+template <class T, int TY, int NW, int STAGE, bool ZACT>
+static cudaError_t launch_weno(const StageParams<T>& p, dim3 grid, cudaStream_t s) {
+  using G = WenoGeom<TY, ZACT>;
+  const size_t smem = (size_t)G::WORDS * sizeof(T);
+  auto kern = rk_stage_weno_kernel<T, TY, NW, STAGE, ZACT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, NW * 32, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+// WENO-Z tiles: 32 x 4 columns, 8 warps (the face-value phase gives every
+// warp two cells' worth of work); one CTA per SM in FP64, two in FP32.
 template <class T>
 void stage_shape(const Grid& g, size_t* smem, int* threads, int* ty) {
+  if (g.limiter == kLimWenoz) {
+    if (g.ndim == 3) {
+      *smem = (size_t)WenoGeom<4, true>::WORDS * sizeof(T);
+      *threads = 256;
+      *ty = 4;
+    } else if (g.ndim == 2) {
+      *smem = (size_t)WenoGeom<4, false>::WORDS * sizeof(T);
+      *threads = 256;
+      *ty = 4;
+    } else {
+      *smem = (size_t)WenoGeom<1, false>::WORDS * sizeof(T);
+      *threads = 32;
+      *ty = 1;
+    }
+    return;
+  }
   if (g.ndim == 3) {
     using S = StageShape3D<T>;
     *smem = (size_t)TileGeom<S::TY, true>::WORDS * sizeof(T);
@@ -72,6 +103,24 @@ cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T*
   p.sc = sc;
   p.lam_bits = lam_bits;
   p.floor_cnt = floor_cnt;
+  if (g.limiter == kLimWenoz) {
+    if (g.ndim == 3) {
+      dim3 grid((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, (g.n[2] + p.tz - 1) / p.tz);
+      if (stage == 1) return launch_weno<T, 4, 8, 1, true>(p, grid, stream);
+      if (stage == 2) return launch_weno<T, 4, 8, 2, true>(p, grid, stream);
+      return launch_weno<T, 4, 8, 3, true>(p, grid, stream);
+    }
+    if (g.ndim == 2) {
+      dim3 grid((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, 1);
+      if (stage == 1) return launch_weno<T, 4, 8, 1, false>(p, grid, stream);
+      if (stage == 2) return launch_weno<T, 4, 8, 2, false>(p, grid, stream);
+      return launch_weno<T, 4, 8, 3, false>(p, grid, stream);
+    }
+    dim3 grid((g.n[0] + 31) / 32, 1, 1);
+    if (stage == 1) return launch_weno<T, 1, 1, 1, false>(p, grid, stream);
+    if (stage == 2) return launch_weno<T, 1, 1, 2, false>(p, grid, stream);
+    return launch_weno<T, 1, 1, 3, false>(p, grid, stream);
+  }
   if (g.ndim == 3) {
     using S = StageShape3D<T>;
     dim3 grid((g.n[0] + 31) / 32, (g.n[1] + S::TY - 1) / S::TY, (g.n[2] + p.tz - 1) / p.tz);

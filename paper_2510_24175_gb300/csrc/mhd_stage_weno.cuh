@@ -1,0 +1,399 @@
+// Fused Runge-Kutta stage kernel with WENO-Z reconstruction (the
+// reconstruction of the paper's own runs, Section 4.2): WENO-Z weights of
+// Borges, Carmona, Costa & Don (2008) with exponent 1 and the candidate
+// stencils and smoothness indicators of Jiang & Shu (1996), applied to the
+// primitive variables.  Same phases as the PLM kernel (mhd_stage.cuh):
+//   A  load + cons->prim: interior of plane k+3 (5-plane ring) and the
+//      (x, y) halo of plane k (three cells deep);
+//   B  the two face values of each cell and direction, once: x for the 34
+//      cells of each row, y for the TY+2 rows, z (column owners) for cell k+1;
+//      a cell whose face density or pressure would be <= 0 keeps its flat
+//      value;
+//   C  face fluxes (GLM + HLLD), each face of the tile once; column owners also
+//      the z face k+1/2;
+//   D  flux divergence + Runge-Kutta combination (+ damping and the wave-speed
+//      reduction in the last stage).
+#pragma once
+
+#include "mhd_stage.cuh"
+
+namespace mhd {
+
+// epsilon of the WENO-Z weights (FP32 uses a larger one so the products of
+// two smoothness indicators below stay normal)
+template <class T> struct WenoEps;
+template <> struct WenoEps<double> { static constexpr double v = 1e-40; };
+template <> struct WenoEps<float> { static constexpr float v = 1e-18f; };
+
+// WENO-Z values of one variable at the cell's faces i-1/2 (minus) and i+1/2
+// (plus) from f[0..4] = cells i-2 .. i+2.  The smoothness indicators are
+// shared by both faces (those of the reversed stencil are the same three in
+// reverse order); the normalised weights
+//   w_k = d_k (1 + tau / e_k) / sum_j d_j (1 + tau / e_j),  e_k = beta_k + eps,
+// are evaluated as d_k (e_k + tau) E_k / sum_j d_j (e_j + tau) E_j with
+// E_k = prod_{j != k} e_j, so each face value needs one reciprocal.
+template <class T>
+__device__ __forceinline__ void wenoz_pair(const T f[5], T& minus, T& plus) {
+  const T c1312 = T(13.0 / 12.0), q4 = T(0.25), sixth = T(1.0 / 6.0);
+  const T d0 = f[0] - T(2) * f[1] + f[2], g0 = f[0] - T(4) * f[1] + T(3) * f[2];
+  const T d1 = f[1] - T(2) * f[2] + f[3], g1 = f[1] - f[3];
+  const T d2 = f[2] - T(2) * f[3] + f[4], g2 = T(3) * f[2] - T(4) * f[3] + f[4];
+  const T b0 = c1312 * d0 * d0 + q4 * g0 * g0;
+  const T b1 = c1312 * d1 * d1 + q4 * g1 * g1;
+  const T b2 = c1312 * d2 * d2 + q4 * g2 * g2;
+  const T tau = tabs(b0 - b2);
+  const T e0 = b0 + WenoEps<T>::v, e1 = b1 + WenoEps<T>::v, e2 = b2 + WenoEps<T>::v;
+  const T E0 = e1 * e2, E1 = e0 * e2, E2 = e0 * e1;
+  // ideal weights 1/10, 6/10, 3/10 (plus face); reversed for the minus face
+  const T ap0 = T(0.1) * (e0 + tau) * E0, ap1 = T(0.6) * (e1 + tau) * E1,
+          ap2 = T(0.3) * (e2 + tau) * E2;
+  const T am0 = T(0.1) * (e2 + tau) * E2, am1 = T(0.6) * (e1 + tau) * E1,
+          am2 = T(0.3) * (e0 + tau) * E0;
+  const T qp0 = (T(2) * f[0] - T(7) * f[1] + T(11) * f[2]) * sixth;
+  const T qp1 = (-f[1] + T(5) * f[2] + T(2) * f[3]) * sixth;
+  const T qp2 = (T(2) * f[2] + T(5) * f[3] - f[4]) * sixth;
+  const T qm0 = (T(2) * f[4] - T(7) * f[3] + T(11) * f[2]) * sixth;
+  const T qm1 = (-f[3] + T(5) * f[2] + T(2) * f[1]) * sixth;
+  const T qm2 = (T(2) * f[2] + T(5) * f[1] - f[0]) * sixth;
+  plus = (ap0 * qp0 + ap1 * qp1 + ap2 * qp2) * rcp(ap0 + ap1 + ap2);
+  minus = (am0 * qm0 + am1 * qm1 + am2 * qm2) * rcp(am0 + am1 + am2);
+}
+
+// Face values of all 9 primitives of one cell from five cells c[0..4]
+// (variables stride[j] apart); flat fallback on non-positive face density
+// or pressure.
+template <class T>
+__device__ __forceinline__ void cell_weno(const T* const c[5], const int st[5], T M[kNV],
+                                          T P[kNV]) {
+#pragma unroll
+  for (int k = 0; k < kNV; ++k) {
+    T f[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) f[j] = c[j][k * st[j]];
+    wenoz_pair(f, M[k], P[k]);
+  }
+  const bool ok = M[kRHO] > T(0) && P[kRHO] > T(0) && M[kPRS] > T(0) && P[kPRS] > T(0);
+  if (!ok) {
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) M[k] = P[k] = c[2][k * st[2]];
+  }
+}
+
+template <int TY, bool ZACT>
+struct WenoGeom {
+  static constexpr int TX = 32;
+  static constexpr int GY = TY > 1 ? 3 : 0;
+  static constexpr int NINT = TY * TX;
+  static constexpr int NXH = 6 * TY;               // x halo: columns -3..-1, 32..34
+  static constexpr int NYH = GY ? 6 * TX : 0;      // y halo: rows -3..-1, TY..TY+2
+  static constexpr int NRING = ZACT ? 5 : 1;
+  static constexpr int RING_W = NRING * kNV * NINT;
+  static constexpr int XH_W = kNV * NXH;
+  static constexpr int YH_W = kNV * NYH;
+  static constexpr int SXN = TY * (TX + 2);           // x face values, columns -1..32
+  static constexpr int SYN = GY ? (TY + 2) * TX : 0;  // y face values, rows -1..TY
+  static constexpr int FXN = TY * (TX + 1);
+  static constexpr int FYN = GY ? (TY + 1) * TX : 0;
+  static constexpr int Z_W = ZACT ? 4 * kNV * NINT : 0;  // zM, zPn, zP, zF per owner
+  static constexpr int WORDS = RING_W + XH_W + YH_W + 2 * kNV * SXN + 2 * kNV * SYN +
+                               kNV * FXN + kNV * FYN + Z_W;
+  static constexpr int NLOAD = NINT + NXH + NYH;
+  static constexpr int IT_X = TY * TX;
+  static constexpr int IT_Y = FYN;
+  static constexpr int IT_XE = TY;
+  static constexpr int ITEMS = IT_X + IT_Y + IT_XE;
+};
+
+template <class T, int TY, int NW, int STAGE, bool ZACT>
+__global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StageParams<T> p) {
+  using G = WenoGeom<TY, ZACT>;
+  constexpr int NT = NW * 32;
+  constexpr int TX = G::TX;
+  constexpr int ZT0 = NT - G::NINT;
+  static_assert(ZT0 >= 0, "need one thread per tile column");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double wmax[NW];
+  T* ring = reinterpret_cast<T*>(smem_raw);
+  T* xh = ring + G::RING_W;
+  T* yh = xh + G::XH_W;
+  T* xM = yh + G::YH_W;
+  T* xP = xM + kNV * G::SXN;
+  T* yM = xP + kNV * G::SXN;
+  T* yP = yM + kNV * G::SYN;
+  T* Fx = yP + kNV * G::SYN;
+  T* Fy = Fx + kNV * G::FXN;
+  T* zM = Fy + kNV * G::FYN;   // per owner: minus-face value of cell k+1
+  T* zPn = zM + kNV * G::NINT;  // per owner: plus-face value of cell k+1
+  T* zP = zPn + kNV * G::NINT;  // per owner: plus-face value of cell k
+  T* zF = zP + kNV * G::NINT;   // per owner: z flux at face k-1/2
+
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * TX;
+  const int y0 = blockIdx.y * TY;
+  const int z0 = blockIdx.z * p.tz;
+  const int z1 = min(z0 + p.tz, p.n[2]);
+  const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
+  const bool owner = tid >= ZT0;
+  const int oidx = tid - ZT0;
+  const int orow = oidx / TX, ocol = oidx - (oidx / TX) * TX;
+
+  const StepScalars sc = *p.sc;
+  const T ch = T(sc.ch);
+  const T half_chi = T(0.5 / sc.ch);
+  const T dtdx = T(sc.dtdx[0]), dtdy = T(sc.dtdx[1]), dtdz = T(sc.dtdx[2]);
+  const T damp = T(sc.damp);
+  const bool frozen = !(sc.dt != 0.0);
+  const Phys<T> ph = p.ph;
+  unsigned flags = 0;
+
+  auto slot = [](int zz) { return ZACT ? ((zz % 5) + 5) % 5 : 0; };
+  auto ring_plane = [&](int zz) { return ring + slot(zz) * (kNV * G::NINT); };
+
+  auto load_cell = [&](int zz, int r, int c, T* dst, int dst_stride) {
+    const int gz = ZACT ? remap3(zz, nz, p.bc_lo[2], p.bc_hi[2]) : 0;
+    const int gx = remap3(x0 + c, nx, p.bc_lo[0], p.bc_hi[0]);
+    const int gy = G::GY ? remap3(y0 + r, ny, p.bc_lo[1], p.bc_hi[1]) : 0;
+    const long long off = (long long)gz * p.sz + (long long)gy * p.sy + gx;
+    T u[kNV], v[kNV];
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) u[k] = p.win[k * p.sv + off];
+    cons_to_prim(u, v, ph, flags);
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) dst[k * dst_stride] = v[k];
+  };
+  auto load_item = [&](int it, int zi, int zh) {
+    if (it < G::NINT) {
+      const int r = it / TX, c = it - (it / TX) * TX;
+      load_cell(zi, r, c, ring_plane(zi) + it, G::NINT);
+    } else if (it < G::NINT + G::NXH) {
+      const int j = it - G::NINT;
+      const int r = j / 6, q = j - (j / 6) * 6;
+      const int c = q < 3 ? q - 3 : TX + q - 3;
+      load_cell(zh, r, c, xh + j, G::NXH);
+    } else {
+      const int j = it - G::NINT - G::NXH;
+      const int hr = j / TX, c = j - (j / TX) * TX;
+      const int r = hr < 3 ? hr - 3 : TY + hr - 3;
+      load_cell(zh, r, c, yh + j, G::NYH);
+    }
+  };
+  auto cell_ptr = [&](const T* cur, int r, int c, int* st) -> const T* {
+    if (c < 0 || c >= TX) {
+      *st = G::NXH;
+      return xh + r * 6 + (c < 0 ? c + 3 : c - TX + 3);
+    }
+    if (r < 0 || r >= TY) {
+      *st = G::NYH;
+      return yh + (r < 0 ? r + 3 : r - TY + 3) * TX + c;
+    }
+    *st = G::NINT;
+    return cur + r * TX + c;
+  };
+  // face values of the owned column's cell in plane zc (planes zc-2..zc+2)
+  auto z_cell = [&](int zc, T M[kNV], T P[kNV]) {
+    const T* c[5];
+    int st[5];
+    for (int j = 0; j < 5; ++j) {
+      c[j] = ring_plane(zc - 2 + j) + oidx;
+      st[j] = G::NINT;
+    }
+    cell_weno(c, st, M, P);
+  };
+
+  if constexpr (ZACT) {
+    // prologue: z face value P of cell z0-1 and the z flux at face z0-1/2
+    for (int it = tid; it < 5 * G::NINT; it += NT) {
+      const int pl = it / G::NINT, j = it - pl * G::NINT;
+      load_item(j, z0 - 3 + pl, 0);
+    }
+    __syncthreads();
+    T Pprev[kNV];
+    if (owner) {
+      T M[kNV];
+      z_cell(z0 - 1, M, Pprev);
+    }
+    __syncthreads();
+    for (int it = tid; it < G::NINT; it += NT) load_item(it, z0 + 2, 0);
+    __syncthreads();
+    if (owner) {
+      T M[kNV], P[kNV], F[kNV];
+      z_cell(z0, M, P);
+      glm_hlld_flux<2>(Pprev, M, ch, half_chi, ph, F);
+#pragma unroll
+      for (int k = 0; k < kNV; ++k) {
+        zP[k * G::NINT + oidx] = P[k];
+        zF[k * G::NINT + oidx] = F[k];
+      }
+    }
+    __syncthreads();
+  }
+
+  T lam = T(0);
+  for (int k = z0; k < z1; ++k) {
+    // ---- A: loads ---------------------------------------------------------
+    for (int it = tid; it < G::NLOAD; it += NT) {
+      if (ZACT && it < G::NINT)
+        load_item(it, k + 3, k);
+      else
+        load_item(it, k, k);
+    }
+    __syncthreads();
+    const T* cur = ring_plane(k);
+
+    // ---- B: face values ---------------------------------------------------
+    for (int it = tid; it < G::SXN + G::SYN; it += NT) {
+      const T* c[5];
+      int st[5];
+      T M[kNV], P[kNV];
+      T *dM, *dP;
+      int ds;
+      if (it < G::SXN) {
+        const int r = it / (TX + 2), cc = it - r * (TX + 2) - 1;
+        for (int j = 0; j < 5; ++j) c[j] = cell_ptr(cur, r, cc - 2 + j, &st[j]);
+        dM = xM + it;
+        dP = xP + it;
+        ds = G::SXN;
+      } else {
+        const int j0 = it - G::SXN;
+        const int rr = j0 / TX - 1, cc = j0 - (j0 / TX) * TX;
+        for (int j = 0; j < 5; ++j) c[j] = cell_ptr(cur, rr - 2 + j, cc, &st[j]);
+        dM = yM + j0;
+        dP = yP + j0;
+        ds = G::SYN;
+      }
+      cell_weno(c, st, M, P);
+#pragma unroll
+      for (int q = 0; q < kNV; ++q) {
+        dM[q * ds] = M[q];
+        dP[q * ds] = P[q];
+      }
+    }
+    if (ZACT && owner) {
+      T M[kNV], P[kNV];
+      z_cell(k + 1, M, P);
+#pragma unroll
+      for (int q = 0; q < kNV; ++q) {
+        zM[q * G::NINT + oidx] = M[q];
+        zPn[q * G::NINT + oidx] = P[q];
+      }
+    }
+    __syncthreads();
+
+    // ---- C: fluxes --------------------------------------------------------
+    for (int it = tid; it < G::ITEMS; it += NT) {
+      T vl[kNV], vr[kNV], F[kNV];
+      T* out;
+      int os;
+      const bool xdir = it < G::IT_X || it >= G::IT_X + G::IT_Y;
+      if (xdir) {
+        int r, fi;
+        if (it < G::IT_X) {
+          r = it / TX;
+          fi = it - r * TX;
+        } else {
+          r = it - (G::IT_X + G::IT_Y);
+          fi = TX;
+        }
+        const int ia = r * (TX + 2) + fi;  // cell fi-1; cell fi is ia + 1
+#pragma unroll
+        for (int q = 0; q < kNV; ++q) {
+          vl[q] = xP[q * G::SXN + ia];
+          vr[q] = xM[q * G::SXN + ia + 1];
+        }
+        out = Fx + r * (TX + 1) + fi;
+        os = G::FXN;
+      } else {
+        const int j = it - G::IT_X;
+        const int fj = j / TX, c = j - (j / TX) * TX;
+        const int ia = fj * TX + c;  // row fj-1; row fj is ia + TX
+#pragma unroll
+        for (int q = 0; q < kNV; ++q) {
+          vl[q] = yP[q * G::SYN + ia];
+          vr[q] = yM[q * G::SYN + ia + TX];
+        }
+        out = Fy + j;
+        os = G::FYN;
+      }
+      if (xdir)
+        glm_hlld_flux<0>(vl, vr, ch, half_chi, ph, F);
+      else
+        glm_hlld_flux<1>(vl, vr, ch, half_chi, ph, F);
+#pragma unroll
+      for (int q = 0; q < kNV; ++q) out[q * os] = F[q];
+    }
+    T dUz[kNV];
+    if constexpr (ZACT) {
+      if (owner) {
+        T vl[kNV], vr[kNV], F[kNV];
+#pragma unroll
+        for (int q = 0; q < kNV; ++q) {
+          vl[q] = zP[q * G::NINT + oidx];
+          vr[q] = zM[q * G::NINT + oidx];
+        }
+        glm_hlld_flux<2>(vl, vr, ch, half_chi, ph, F);
+#pragma unroll
+        for (int q = 0; q < kNV; ++q) {
+          dUz[q] = (F[q] - zF[q * G::NINT + oidx]) * dtdz;
+          zF[q * G::NINT + oidx] = F[q];
+          zP[q * G::NINT + oidx] = zPn[q * G::NINT + oidx];
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- D: right-hand side and Runge-Kutta combination --------------------
+    if (owner) {
+      const int gx = x0 + ocol, gy = y0 + orow;
+      if (gx < nx && gy < ny) {
+        const long long off = (long long)k * p.sz + (long long)gy * p.sy + gx;
+        T unew[kNV];
+#pragma unroll
+        for (int q = 0; q < kNV; ++q) {
+          const T* fx = Fx + q * G::FXN + orow * (TX + 1) + ocol;
+          T du = (fx[1] - fx[0]) * dtdx;
+          if constexpr (G::GY > 0) {
+            const T* fy = Fy + q * G::FYN + orow * TX + ocol;
+            du += (fy[TX] - fy[0]) * dtdy;
+          }
+          if constexpr (ZACT) du += dUz[q];
+          if (frozen) du = T(0);
+          const T s1 = p.win[q * p.sv + off] - du;
+          if constexpr (STAGE == 1) {
+            unew[q] = s1;
+          } else {
+            unew[q] = p.a_n * p.un[q * p.sv + off] + p.a_w * s1;
+          }
+        }
+        if constexpr (STAGE == 2) unew[kPSI] *= damp;
+#pragma unroll
+        for (int q = 0; q < kNV; ++q) p.uout[q * p.sv + off] = unew[q];
+        if constexpr (STAGE == 2) {
+          const int ndim = 1 + (G::GY > 0) + (ZACT ? 1 : 0);
+          lam = nan_max(lam, cell_max_speed(unew, ph, ndim, flags));
+        }
+      }
+    }
+  }
+
+  if constexpr (STAGE == 2) {
+    double l = (double)lam;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l = nan_max(l, __shfl_xor_sync(0xffffffffu, l, o));
+    __syncthreads();
+    if ((tid & 31) == 0) wmax[tid >> 5] = l;
+    __syncthreads();
+    if (tid == 0) {
+      double m = wmax[0];
+      for (int w = 1; w < NW; ++w) m = nan_max(m, wmax[w]);
+      unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+      if (m != m) bits = 0x7ff8000000000000ull;
+      atomicMax(p.lam_bits, bits);
+    }
+  }
+  if (flags) {
+    if (flags & kFloorRho) atomicAdd(&p.floor_cnt[0], 1ull);
+    if (flags & kFloorP) atomicAdd(&p.floor_cnt[1], 1ull);
+  }
+}
+
+}  // namespace mhd

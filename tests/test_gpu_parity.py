@@ -272,3 +272,32 @@ def test_ssp_rk3_rejected_for_adjoint_and_ensemble():
         m.MHD(m.Config(n=(16, 8, 4), rk_order=3, flags=m.MHD_FLAG_ADJOINT))
     with pytest.raises(m.MHDError):
         m.Ensemble([m.Config(n=(16, 16, 16), precision=m.MHD_FP32, rk_order=3)])
+
+
+# ------------------------------------------------------------------ WENO-Z --
+@pytest.mark.parametrize("n,bc,rk", [((40, 20, 12), 0, 3), ((35, 18, 10), 1, 3),
+                                     ((37, 9, 7), 0, 2), ((48, 40, 1), 0, 3),
+                                     ((3, 3, 3), 0, 3), ((5, 4, 3), 1, 2)])
+def test_wenoz_matches_oracle(n, bc, rk):
+    pb = Problem("random_smooth", n, seed=9, bc=(bc,) * 6, limiter=orc.LIM_WENOZ, rk_order=rk)
+    _compare_run(pb, 3)
+
+
+def test_wenoz_brio_wu_short_time_and_fp32_orszag_tang():
+    pb = inputs.brio_wu(1024)
+    pb.t_end, pb.rk_order, pb.limiter = 0.005, 3, orc.LIM_WENOZ
+    ref = oracle_run(pb, 100000, t_end=pb.t_end)
+    U, hist, cnt = gpu_run(pb, 100000)
+    assert len(hist) == int(np.count_nonzero(ref.dts))
+    assert np.all(rel_l1(U, ref.U) <= TOL64), rel_l1(U, ref.U)
+    ot = inputs.orszag_tang_3d(8).with_n((40, 24, 16))
+    ot.rk_order, ot.limiter = 3, orc.LIM_WENOZ
+    _compare_run(ot, 3, tol=TOL32, precision=1)
+
+
+def test_wenoz_rejected_where_unsupported():
+    import paper_2510_24175_gb300 as m
+    with pytest.raises(m.MHDError):
+        m.MHD(m.Config(n=(16, 2, 1), limiter=m.MHD_LIM_WENOZ))
+    with pytest.raises(m.MHDError):
+        m.MHD(m.Config(n=(16, 8, 4), limiter=m.MHD_LIM_WENOZ, flags=m.MHD_FLAG_ADJOINT))
