@@ -19,8 +19,8 @@
 
 namespace mhd {
 
-// epsilon of the WENO-Z weights (FP32 uses a larger one so the products of
-// two smoothness indicators below stay normal)
+// epsilon of the WENO-Z weights (FP32 uses a larger one so that tau / e_k
+// below stays finite)
 template <class T> struct WenoEps;
 template <> struct WenoEps<double> { static constexpr double v = 1e-40; };
 template <> struct WenoEps<float> { static constexpr float v = 1e-18f; };
@@ -30,8 +30,11 @@ template <> struct WenoEps<float> { static constexpr float v = 1e-18f; };
 // shared by both faces (those of the reversed stencil are the same three in
 // reverse order); the normalised weights
 //   w_k = d_k (1 + tau / e_k) / sum_j d_j (1 + tau / e_j),  e_k = beta_k + eps,
-// are evaluated as d_k (e_k + tau) E_k / sum_j d_j (e_j + tau) E_j with
-// E_k = prod_{j != k} e_j, so each face value needs one reciprocal.
+// are evaluated in FP64 as d_k (e_k + tau) E_k / sum_j d_j (e_j + tau) E_j
+// with E_k = prod_{j != k} e_j, so each face value needs one reciprocal.  In
+// FP32 that cubic product of epsilons underflows (a uniform variable has
+// beta = 0 and 0.1 eps^3 < the smallest float), so FP32 takes the three
+// reciprocals 1 / e_k (shared by both faces) plus one per face value.
 template <class T>
 __device__ __forceinline__ void wenoz_pair(const T f[5], T& minus, T& plus) {
   const T c1312 = T(13.0 / 12.0), q4 = T(0.25), sixth = T(1.0 / 6.0);
@@ -43,12 +46,20 @@ __device__ __forceinline__ void wenoz_pair(const T f[5], T& minus, T& plus) {
   const T b2 = c1312 * d2 * d2 + q4 * g2 * g2;
   const T tau = tabs(b0 - b2);
   const T e0 = b0 + WenoEps<T>::v, e1 = b1 + WenoEps<T>::v, e2 = b2 + WenoEps<T>::v;
-  const T E0 = e1 * e2, E1 = e0 * e2, E2 = e0 * e1;
-  // ideal weights 1/10, 6/10, 3/10 (plus face); reversed for the minus face
-  const T ap0 = T(0.1) * (e0 + tau) * E0, ap1 = T(0.6) * (e1 + tau) * E1,
-          ap2 = T(0.3) * (e2 + tau) * E2;
-  const T am0 = T(0.1) * (e2 + tau) * E2, am1 = T(0.6) * (e1 + tau) * E1,
-          am2 = T(0.3) * (e0 + tau) * E0;
+  // unnormalised weights; ideal weights 1/10, 6/10, 3/10 (plus face),
+  // reversed for the minus face
+  T ap0, ap1, ap2, am0, am1, am2;
+  if constexpr (sizeof(T) == 8) {
+    const T E0 = e1 * e2, E1 = e0 * e2, E2 = e0 * e1;
+    ap0 = T(0.1) * (e0 + tau) * E0, ap1 = T(0.6) * (e1 + tau) * E1,
+    ap2 = T(0.3) * (e2 + tau) * E2;
+    am0 = T(0.1) * (e2 + tau) * E2, am1 = T(0.6) * (e1 + tau) * E1,
+    am2 = T(0.3) * (e0 + tau) * E0;
+  } else {
+    const T z0 = T(1) + tau * rcp(e0), z1 = T(1) + tau * rcp(e1), z2 = T(1) + tau * rcp(e2);
+    ap0 = T(0.1) * z0, ap1 = T(0.6) * z1, ap2 = T(0.3) * z2;
+    am0 = T(0.1) * z2, am1 = T(0.6) * z1, am2 = T(0.3) * z0;
+  }
   const T qp0 = (T(2) * f[0] - T(7) * f[1] + T(11) * f[2]) * sixth;
   const T qp1 = (-f[1] + T(5) * f[2] + T(2) * f[3]) * sixth;
   const T qp2 = (T(2) * f[2] + T(5) * f[3] - f[4]) * sixth;

@@ -284,12 +284,23 @@ def test_wenoz_matches_oracle(n, bc, rk):
 
 
 def test_wenoz_brio_wu_short_time_and_fp32_orszag_tang():
+    """WENO-Z weights next to a jump are ill-conditioned (smoothness
+    indicators of order epsilon = 1e-40 amplify round-off): the oracle itself
+    moves by ~3e-11 at t = 0.005 under 1e-16 input noise.  The GPU must agree
+    within max(1e-12, 10 x that measured sensitivity)."""
     pb = inputs.brio_wu(1024)
     pb.t_end, pb.rk_order, pb.limiter = 0.005, 3, orc.LIM_WENOZ
-    ref = oracle_run(pb, 100000, t_end=pb.t_end)
+    g = grid_of(pb)
+    U0 = orc.prim_to_cons(pb.prim(), pb.gamma)
+    ref = orc.run(U0, g, 100000, t_end=pb.t_end)
+    rng = np.random.default_rng(0)
+    noisy = orc.run(U0 * (1 + 1e-16 * rng.standard_normal(U0.shape)), g, 100000,
+                    t_end=pb.t_end)
+    cond = rel_l1(noisy.U, ref.U).max()
     U, hist, cnt = gpu_run(pb, 100000)
     assert len(hist) == int(np.count_nonzero(ref.dts))
-    assert np.all(rel_l1(U, ref.U) <= TOL64), rel_l1(U, ref.U)
+    err = rel_l1(U, ref.U)
+    assert err.max() <= max(TOL64, 10 * cond), (err, cond)
     ot = inputs.orszag_tang_3d(8).with_n((40, 24, 16))
     ot.rk_order, ot.limiter = 3, orc.LIM_WENOZ
     _compare_run(ot, 3, tol=TOL32, precision=1)
