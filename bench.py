@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-paper-scheme", action="store_true",
+                    help="skip the WENO-Z + SSP-RK3 throughput lines")
     return ap.parse_args()
 
 
@@ -351,6 +353,30 @@ def main():
         del ss
         torch.cuda.empty_cache()
 
+    # ---- the paper's own scheme: WENO-Z + SSP-RK3 (+ GLM), OT 256^3 ----------
+    paper_scheme = None
+    if not args.no_paper_scheme:
+        paper_scheme = {}
+        Kp = max(3, min(K, 5))
+        for prec, tag in ((m.MHD_FP64, "fp64"), (m.MHD_FP32, "fp32")):
+            pw = inputs.orszag_tang_3d(args.n)
+            pw.limiter, pw.rk_order = m.MHD_LIM_WENOZ, 3
+            sw = m.MHD(m.Config.from_problem(pw, precision=prec))
+            sw.set_state(torch.from_numpy(pw.prim()).cuda(), kind=m.MHD_PRIM)
+            for _ in range(W):
+                sw.step()
+            sw.step_info()
+            msw, profw = timed_steps(sw, torch, Kp, dist, world)
+            sw.step_info()
+            paper_scheme[tag] = {
+                "workload": f"orszag_tang_3d_{args.n}^3_wenoz_rk3_{tag}",
+                "value": world * pw.ncell * Kp / (msw * 1e-3), "unit": "zone-updates/s",
+                "steps": Kp, "ms_per_step": msw / Kp,
+                "kernels": {k: {"launches": c, "total_ms": t} for k, (c, t) in profw.items()}}
+            launches += sum(c for c, _ in profw.values())
+            del sw
+            torch.cuda.empty_cache()
+
     # ---- adjoint / forward step-time ratio: 2-D Orszag-Tang 512^2 FP64 ------
     adjoint = None
     if not args.no_adjoint:
@@ -466,6 +492,7 @@ def main():
         "fp32": fp32,
         "fp32_same_grid": fp32_same,
         "fp32_over_fp64_same_grid": (fp32_same["value"] / value) if fp32_same else None,
+        "paper_scheme_wenoz_rk3": paper_scheme,
         "adjoint": adjoint,
         "ensemble": ensemble,
         "cpu_baseline": cpu,
