@@ -20,54 +20,67 @@
 namespace mhd {
 
 // epsilon of the WENO-Z weights (FP32 uses a larger one so that tau / e_k
-// below stays finite)
+// below stays finite).  FP64's form below holds while |primitive| < ~1e25
+// (the product of both faces' denominators, ~beta^6, stays finite).
 template <class T> struct WenoEps;
 template <> struct WenoEps<double> { static constexpr double v = 1e-40; };
 template <> struct WenoEps<float> { static constexpr float v = 1e-18f; };
 
 // WENO-Z values of one variable at the cell's faces i-1/2 (minus) and i+1/2
-// (plus) from f[0..4] = cells i-2 .. i+2.  The smoothness indicators are
-// shared by both faces (those of the reversed stencil are the same three in
-// reverse order); the normalised weights
-//   w_k = d_k (1 + tau / e_k) / sum_j d_j (1 + tau / e_j),  e_k = beta_k + eps,
-// are evaluated in FP64 as d_k (e_k + tau) E_k / sum_j d_j (e_j + tau) E_j
-// with E_k = prod_{j != k} e_j, so each face value needs one reciprocal.  In
-// FP32 that cubic product of epsilons underflows (a uniform variable has
-// beta = 0 and 0.1 eps^3 < the smallest float), so FP32 takes the three
-// reciprocals 1 / e_k (shared by both faces) plus one per face value.
+// (plus) from f[0..4] = cells i-2 .. i+2.  With the second differences
+// d_k and the one-sided first-difference combinations g_k of the three
+// candidate stencils, written as D_k = d_k/12 and G_k = g_k/4:
+//   * every candidate value is the cell value plus D_k +- G_k (the plus face
+//     takes D0+G0, D1-G1, D2-G2; the minus face, whose stencils are the
+//     mirrored ones, D2+G2, D1+G1, D0-G0);
+//   * the Jiang-Shu smoothness indicator is beta_k = 13/12 d_k^2 + 1/4 g_k^2
+//     = 4 (39 D_k^2 + G_k^2); the weights are invariant under a common scale
+//     of beta, tau and epsilon, so the code works with beta/4 and epsilon/4;
+//   * the smoothness indicators are shared by both faces (the reversed
+//     stencils' are the same three in reverse order), and so is tau;
+//   * the normalised weights w_k = d_k (1 + tau / e_k) / sum_j (...),
+//     e_k = beta_k + eps, ideal weights (1, 6, 3)/10 (plus face; reversed on
+//     the minus face).
+// FP64 multiplies the unnormalised weights by e0 e1 e2 (no reciprocal per
+// stencil): P_k = e0 e1 e2 + tau prod_{j != k} e_j, and one reciprocal of the
+// product of the two faces' denominators serves both faces.  In FP32 these
+// products of epsilons underflow (a uniform variable has beta = 0), so FP32
+// takes the reciprocals 1 / e_k and one per face.
 template <class T>
 __device__ __forceinline__ void wenoz_pair(const T f[5], T& minus, T& plus) {
-  const T c1312 = T(13.0 / 12.0), q4 = T(0.25), sixth = T(1.0 / 6.0);
-  const T d0 = f[0] - T(2) * f[1] + f[2], g0 = f[0] - T(4) * f[1] + T(3) * f[2];
-  const T d1 = f[1] - T(2) * f[2] + f[3], g1 = f[1] - f[3];
-  const T d2 = f[2] - T(2) * f[3] + f[4], g2 = T(3) * f[2] - T(4) * f[3] + f[4];
-  const T b0 = c1312 * d0 * d0 + q4 * g0 * g0;
-  const T b1 = c1312 * d1 * d1 + q4 * g1 * g1;
-  const T b2 = c1312 * d2 * d2 + q4 * g2 * g2;
+  const T c12 = T(1.0 / 12.0), q4 = T(0.25), c39 = T(39);
+  const T D0 = c12 * (f[0] + f[2] - T(2) * f[1]);
+  const T D1 = c12 * (f[1] + f[3] - T(2) * f[2]);
+  const T D2 = c12 * (f[2] + f[4] - T(2) * f[3]);
+  const T G0 = q4 * (f[0] - T(4) * f[1] + T(3) * f[2]);
+  const T G1 = q4 * (f[1] - f[3]);
+  const T G2 = q4 * (T(3) * f[2] - T(4) * f[3] + f[4]);
+  const T b0 = c39 * D0 * D0 + G0 * G0;
+  const T b1 = c39 * D1 * D1 + G1 * G1;
+  const T b2 = c39 * D2 * D2 + G2 * G2;
+  const T eps = T(0.25) * WenoEps<T>::v;
   const T tau = tabs(b0 - b2);
-  const T e0 = b0 + WenoEps<T>::v, e1 = b1 + WenoEps<T>::v, e2 = b2 + WenoEps<T>::v;
-  // unnormalised weights; ideal weights 1/10, 6/10, 3/10 (plus face),
-  // reversed for the minus face
-  T ap0, ap1, ap2, am0, am1, am2;
+  const T e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+  T P0, P1, P2;
   if constexpr (sizeof(T) == 8) {
-    const T E0 = e1 * e2, E1 = e0 * e2, E2 = e0 * e1;
-    ap0 = T(0.1) * (e0 + tau) * E0, ap1 = T(0.6) * (e1 + tau) * E1,
-    ap2 = T(0.3) * (e2 + tau) * E2;
-    am0 = T(0.1) * (e2 + tau) * E2, am1 = T(0.6) * (e1 + tau) * E1,
-    am2 = T(0.3) * (e0 + tau) * E0;
+    const T E0 = e1 * e2, E2 = e0 * e1;
+    const T pi = e0 * E0;
+    P0 = pi + tau * E0, P1 = pi + tau * (e0 * e2), P2 = pi + tau * E2;
   } else {
-    const T z0 = T(1) + tau * rcp(e0), z1 = T(1) + tau * rcp(e1), z2 = T(1) + tau * rcp(e2);
-    ap0 = T(0.1) * z0, ap1 = T(0.6) * z1, ap2 = T(0.3) * z2;
-    am0 = T(0.1) * z2, am1 = T(0.6) * z1, am2 = T(0.3) * z0;
+    P0 = T(1) + tau * rcp(e0), P1 = T(1) + tau * rcp(e1), P2 = T(1) + tau * rcp(e2);
   }
-  const T qp0 = (T(2) * f[0] - T(7) * f[1] + T(11) * f[2]) * sixth;
-  const T qp1 = (-f[1] + T(5) * f[2] + T(2) * f[3]) * sixth;
-  const T qp2 = (T(2) * f[2] + T(5) * f[3] - f[4]) * sixth;
-  const T qm0 = (T(2) * f[4] - T(7) * f[3] + T(11) * f[2]) * sixth;
-  const T qm1 = (-f[3] + T(5) * f[2] + T(2) * f[1]) * sixth;
-  const T qm2 = (T(2) * f[2] + T(5) * f[1] - f[0]) * sixth;
-  plus = (ap0 * qp0 + ap1 * qp1 + ap2 * qp2) * rcp(ap0 + ap1 + ap2);
-  minus = (am0 * qm0 + am1 * qm1 + am2 * qm2) * rcp(am0 + am1 + am2);
+  const T S1 = T(6) * P1, T0 = T(3) * P0, T2 = T(3) * P2;
+  const T den_p = P0 + S1 + T2, den_m = P2 + S1 + T0;
+  const T num_p = P0 * (D0 + G0) + S1 * (D1 - G1) + T2 * (D2 - G2);
+  const T num_m = P2 * (D2 + G2) + S1 * (D1 + G1) + T0 * (D0 - G0);
+  if constexpr (sizeof(T) == 8) {
+    const T r = rcp(den_p * den_m);
+    plus = f[2] + num_p * den_m * r;
+    minus = f[2] + num_m * den_p * r;
+  } else {
+    plus = f[2] + num_p * rcp(den_p);
+    minus = f[2] + num_m * rcp(den_m);
+  }
 }
 
 // Face values of all 9 primitives of one cell from five cells c[0..4]
