@@ -118,6 +118,12 @@ def lib():
         _lib.orc_conserved_sums.argtypes = [P, D, D]
         _lib.orc_stage_padded.argtypes = [P, D, D, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                           ctypes.c_int, D]
+        _lib.orc_ct_run.argtypes = [P, D, D, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, D, D, LL]
+        _lib.orc_ct_run.restype = ctypes.c_double
+        _lib.orc_ct_divb.argtypes = [P, D, D]
+        _lib.orc_ct_stage1.argtypes = [P, D, D, ctypes.c_double, ctypes.c_double, D, D]
+        _lib.orc_ct_edge_emf.argtypes = [D, D, L]
     return _lib
 
 
@@ -232,6 +238,7 @@ class RunResult:
     dts: np.ndarray
     chs: np.ndarray
     floors: tuple = field(default=(0, 0))
+    b: np.ndarray | None = None  # constrained transport: face field (3, nz, ny, nx)
 
 
 def run(U0: np.ndarray, grid: Grid, nsteps: int, t0: float = 0.0, t_end: float = 0.0,
@@ -265,4 +272,57 @@ def conserved_sums(U: np.ndarray, grid: Grid) -> np.ndarray:
     out = np.empty(8)
     p = grid.c()
     lib().orc_conserved_sums(ctypes.byref(p), _d(U), _d(out))
+    return out
+
+
+# ----------------------------------------------------- constrained transport --
+# Face-field arrays have shape (3, nz, ny, nx): component d on each cell's
+# lower d-face.  Three active dimensions, periodic boundaries.
+
+def ct_run(U0: np.ndarray, b0: np.ndarray, grid: Grid, nsteps: int, t0: float = 0.0,
+           t_end: float = 0.0, dts=None, chs=None) -> RunResult:
+    """nsteps constrained-transport steps (RK2, or SSP-RK3 with
+    grid.rk_order == 3).  U0's cell-centred B must be the mean of b0's faces."""
+    U = _f64(U0).copy()
+    b = _f64(b0).copy()
+    if dts is None:
+        dts = np.zeros(nsteps)
+        chs = np.zeros(nsteps)
+    else:
+        dts = _f64(dts).copy()
+        chs = _f64(chs).copy()
+    cnt = (ctypes.c_longlong * 2)()
+    p = grid.c()
+    t = lib().orc_ct_run(ctypes.byref(p), _d(U), _d(b), nsteps, grid.cfl, t0, t_end, _d(dts),
+                         _d(chs), cnt)
+    return RunResult(U, t, dts, chs, (cnt[0], cnt[1]), b)
+
+
+def ct_stage1(W: np.ndarray, bw: np.ndarray, grid: Grid, dt: float, ch: float):
+    """One first RK stage with constrained transport: (W + dt L, b + dt db/dt)."""
+    W, bw = _f64(W), _f64(bw)
+    out, bout = np.empty_like(W), np.empty_like(bw)
+    p = grid.c()
+    lib().orc_ct_stage1(ctypes.byref(p), _d(W), _d(bw), dt, ch, _d(out), _d(bout))
+    return out, bout
+
+
+def ct_divb(b: np.ndarray, grid: Grid) -> np.ndarray:
+    """Face divergence per cell, sum_d (b_d(+1/2) - b_d(-1/2)) / dx_d."""
+    b = _f64(b)
+    out = np.empty(b.shape[1:])
+    p = grid.c()
+    lib().orc_ct_divb(ctypes.byref(p), _d(b), _d(out))
+    return out
+
+
+def ct_edge_emf(Ea, Fa, Eb, Fb, Ec) -> np.ndarray:
+    """CT-contact edge field for arrays of edges: Ea, Fa, Eb, Fb of shape
+    (2, n), Ec of shape (2, 2, n) indexed [a side][b side]."""
+    Ea, Fa, Eb, Fb, Ec = (np.asarray(x, dtype=np.float64) for x in (Ea, Fa, Eb, Fb, Ec))
+    n = Ea.shape[1]
+    inp = np.ascontiguousarray(np.concatenate(
+        [Ea, Fa, Eb, Fb, Ec.reshape(4, n)], axis=0))
+    out = np.empty(n)
+    lib().orc_ct_edge_emf(_d(inp), _d(out), n)
     return out

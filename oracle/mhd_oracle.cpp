@@ -467,6 +467,45 @@ void fill_ghosts(Field<S>& f, const Params& P) {
   }
 }
 
+// Step 3 of a stage (reconstruction): the left and right primitive states
+// of the face f = c[d] along d, which separates cells f-1 (left) and f
+// (right); the other two coordinates of c are the face's cell indices.
+template <class S>
+void face_states(const Params& P, const Field<S>& V, int d, const int c[3], S face[2][NV]) {
+  for (int side = 0; side < 2; ++side) {
+    const int cell = c[d] - 1 + side;  // f-1 (left), f (right)
+    auto at = [&](int k, int off) {
+      int a[3] = {c[0], c[1], c[2]};
+      a[d] = cell + off;
+      return V.at(k, a[0], a[1], a[2]);
+    };
+    S plus[NV], minus[NV];  // values at the cell's faces +1/2 and -1/2
+    if (P.limiter == LIM_WENOZ) {
+      for (int k = 0; k < NV; ++k) {
+        S st[5], rv[5];
+        for (int o = -2; o <= 2; ++o) st[o + 2] = at(k, o);
+        for (int o = 0; o < 5; ++o) rv[o] = st[4 - o];
+        plus[k] = wenoz_face(st);
+        minus[k] = wenoz_face(rv);
+      }
+    } else {
+      for (int k = 0; k < NV; ++k) {
+        S sig = limited_slope(at(k, 0) - at(k, -1), at(k, 1) - at(k, 0), P.limiter);
+        plus[k] = at(k, 0) + 0.5 * sig;
+        minus[k] = at(k, 0) - 0.5 * sig;
+      }
+    }
+    // Reading: if either face value of this cell has rho <= 0 or p <= 0, the
+    // cell falls back to its own (flat) value.
+    bool bad = val(plus[RHO]) <= 0.0 || val(minus[RHO]) <= 0.0 || val(plus[PRS]) <= 0.0 ||
+               val(minus[PRS]) <= 0.0;
+    for (int k = 0; k < NV; ++k) {
+      const S v0 = at(k, 0);
+      face[side][k] = bad ? v0 : (side == 0 ? plus[k] : minus[k]);
+    }
+  }
+}
+
 // One RK2 stage (Section 3.2, steps 1-5) on the input W.  Writes
 //   stage 1:  out = W + dt L(W)
 //   stage 2:  out = (Un + (W + dt L(W))) / 2
@@ -526,41 +565,9 @@ void rk_stage(const Params& P, Field<S>& W, const Field<S>* Un, double dt, doubl
     for (c[2] = 0; c[2] < fn[2]; ++c[2])
       for (c[1] = 0; c[1] < fn[1]; ++c[1])
         for (c[0] = 0; c[0] < fn[0]; ++c[0]) {
-          // Step 3: reconstruction.  Face f's left state comes from cell
-          // f-1 and its right state from cell f.
+          // Step 3: reconstruction.
           S face[2][NV];
-          for (int side = 0; side < 2; ++side) {
-            const int cell = c[d] - 1 + side;  // f-1 (left), f (right)
-            auto at = [&](int k, int off) {
-              int a[3] = {c[0], c[1], c[2]};
-              a[d] = cell + off;
-              return V.at(k, a[0], a[1], a[2]);
-            };
-            S plus[NV], minus[NV];  // values at the cell's faces +1/2 and -1/2
-            if (P.limiter == LIM_WENOZ) {
-              for (int k = 0; k < NV; ++k) {
-                S st[5], rv[5];
-                for (int o = -2; o <= 2; ++o) st[o + 2] = at(k, o);
-                for (int o = 0; o < 5; ++o) rv[o] = st[4 - o];
-                plus[k] = wenoz_face(st);
-                minus[k] = wenoz_face(rv);
-              }
-            } else {
-              for (int k = 0; k < NV; ++k) {
-                S sig = limited_slope(at(k, 0) - at(k, -1), at(k, 1) - at(k, 0), P.limiter);
-                plus[k] = at(k, 0) + 0.5 * sig;
-                minus[k] = at(k, 0) - 0.5 * sig;
-              }
-            }
-            // Reading: if either face value of this cell has rho <= 0 or
-            // p <= 0, the cell falls back to its own (flat) value.
-            bool bad = val(plus[RHO]) <= 0.0 || val(minus[RHO]) <= 0.0 ||
-                       val(plus[PRS]) <= 0.0 || val(minus[PRS]) <= 0.0;
-            for (int k = 0; k < NV; ++k) {
-              const S v0 = at(k, 0);
-              face[side][k] = bad ? v0 : (side == 0 ? plus[k] : minus[k]);
-            }
-          }
+          face_states(P, V, d, c, face);
           // Step 4: GLM + HLLD.
           S F[NV];
           interface_flux(face[0], face[1], d, ch, P.gamma, F);
@@ -679,6 +686,300 @@ void store_interior(const Field<S>& f, double* dst, double* tan) {
           if constexpr (sizeof(S) != sizeof(double))
             if (tan) tan[m] = f.at(v, i, j, k).d;
         }
+}
+
+
+// ------------------------------------------------- constrained transport --
+// The div-B control of the paper's weak-scaling runs (Section 4.2):
+// constrained transport (Evans & Hawley 1988; Londrillo & Del Zanna 2004).
+// The magnetic field is kept on cell faces, b_d on the faces normal to d, and
+// advanced by Faraday's law in integral (Stokes) form, db/dt = -curl E with
+// the electric field E = -v x B on cell edges, so the face divergence
+// sum_d (b_d(+1/2) - b_d(-1/2)) / dx_d does not change.  Readings (the paper
+// names the method only):
+//   * three active dimensions, periodic boundaries;
+//   * b_d stored at cell (i, j, k) is the one on the cell's lower d-face;
+//     the cell-centred B of the conservative state is the mean of the cell's
+//     two faces;
+//   * each face's Riemann problem (the same reconstruction and HLLD as with
+//     GLM) takes the staggered b_d as its normal field on both sides; psi is
+//     identically zero (with equal normal fields and psi = 0 the GLM interface
+//     step of interface_flux is the identity);
+//   * the edge electric field is the upwind "CT-contact" average of Gardiner
+//     & Stone (2005, J. Comput. Phys. 205, 509): the mean of the four face
+//     values plus the difference of upwinded edge-to-cell derivatives, the
+//     upwind side chosen by the sign of the face mass flux (their Eqs. 41,
+//     45 and 50-51); a mass flux with |F_rho| <= 1e-12 c_h rho (rho of the
+//     cell owning the face) counts as zero, so round-off cannot choose a side;
+//   * the face field is combined across Runge-Kutta stages like the
+//     conservative variables; there is no psi damping.
+struct Faces {
+  int n[3];
+  std::vector<double> b[3];
+  explicit Faces(const int nn[3]) {
+    for (int d = 0; d < 3; ++d) n[d] = nn[d];
+    for (int d = 0; d < 3; ++d) b[d].assign((size_t)n[0] * n[1] * n[2], 0.0);
+  }
+  // periodic wrap of any cell index
+  size_t idx(int i, int j, int k) const {
+    i = ((i % n[0]) + n[0]) % n[0];
+    j = ((j % n[1]) + n[1]) % n[1];
+    k = ((k % n[2]) + n[2]) % n[2];
+    return ((size_t)k * n[1] + j) * n[0] + i;
+  }
+  double& at(int d, int i, int j, int k) { return b[d][idx(i, j, k)]; }
+  double at(int d, int i, int j, int k) const { return b[d][idx(i, j, k)]; }
+};
+
+// A per-cell scalar array with periodic wrap (face, edge and cell-centred
+// electric fields).
+struct CellArray {
+  int n[3];
+  std::vector<double> a;
+  explicit CellArray(const int nn[3]) {
+    for (int d = 0; d < 3; ++d) n[d] = nn[d];
+    a.assign((size_t)n[0] * n[1] * n[2], 0.0);
+  }
+  double& at(int i, int j, int k) {
+    i = ((i % n[0]) + n[0]) % n[0];
+    j = ((j % n[1]) + n[1]) % n[1];
+    k = ((k % n[2]) + n[2]) % n[2];
+    return a[((size_t)k * n[1] + j) * n[0] + i];
+  }
+};
+
+// Upwind choice of Gardiner & Stone (2005): positive mass flux takes the
+// candidate of the low side, negative that of the high side, zero their mean.
+inline double ct_upwind(double F, double from_lo, double from_hi) {
+  if (F > 0.0) return from_lo;
+  if (F < 0.0) return from_hi;
+  return 0.5 * (from_lo + from_hi);
+}
+
+// CT-contact electric field on an edge along e.  a and b are the two other
+// directions.  The edge touches four faces and four cells:
+//   Ea[0], Ea[1]: values on the a-faces on the low and high b side, with mass
+//                 fluxes Fa[0], Fa[1];
+//   Eb[0], Eb[1]: values on the b-faces on the low and high a side, with mass
+//                 fluxes Fb[0], Fb[1];
+//   Ec[ia][ib]:   cell-centred values, ia / ib = 0 (low) or 1 (high) side.
+// Gardiner & Stone (2005), Eq. 41: E = (sum of the four faces)/4
+//   + (db/8) (dE/db at the low quarter - dE/db at the high quarter)
+//   + (da/8) (dE/da at the low quarter - dE/da at the high quarter),
+// with each quarter derivative 2 (face - cell) / d (or 2 (cell - face) / d)
+// taken from the cell upwind of the face whose mass flux it sits on
+// (Eqs. 50-51); the d/8 and 2/d factors combine to 1/4.
+double ct_contact_emf(const double Ea[2], const double Fa[2], const double Eb[2],
+                      const double Fb[2], const double Ec[2][2]) {
+  const double mean = 0.25 * (Ea[0] + Ea[1] + Eb[0] + Eb[1]);
+  // dE/db on the low-b a-face and on the high-b a-face (upwind along a)
+  const double db_lo = ct_upwind(Fa[0], Eb[0] - Ec[0][0], Eb[1] - Ec[1][0]);
+  const double db_hi = ct_upwind(Fa[1], Ec[0][1] - Eb[0], Ec[1][1] - Eb[1]);
+  // dE/da on the low-a b-face and on the high-a b-face (upwind along b)
+  const double da_lo = ct_upwind(Fb[0], Ea[0] - Ec[0][0], Ea[1] - Ec[0][1]);
+  const double da_hi = ct_upwind(Fb[1], Ec[1][0] - Ea[0], Ec[1][1] - Ea[1]);
+  return mean + 0.25 * (db_lo - db_hi) + 0.25 * (da_lo - da_hi);
+}
+
+// Cell-centred B = mean of the cell's two faces, written into U.
+inline void ct_cell_field(const Faces& b, Field<double>& U) {
+  for (int k = 0; k < b.n[2]; ++k)
+    for (int j = 0; j < b.n[1]; ++j)
+      for (int i = 0; i < b.n[0]; ++i) {
+        U.at(BX, i, j, k) = 0.5 * (b.at(0, i, j, k) + b.at(0, i + 1, j, k));
+        U.at(BY, i, j, k) = 0.5 * (b.at(1, i, j, k) + b.at(1, i, j + 1, k));
+        U.at(BZ, i, j, k) = 0.5 * (b.at(2, i, j, k) + b.at(2, i, j, k + 1));
+      }
+}
+
+// One Runge-Kutta stage with constrained transport: out / bout =
+// a_n (Un, bn) + a_w ((W, bw) + dt L(W, bw)) (stage 1: a_n = 0, a_w = 1).
+void ct_stage(const Params& P, Field<double>& W, const Faces& bw, const Field<double>* Un,
+              const Faces* bn, double dt, double ch, int stage, Field<double>& out,
+              Faces& bout, Counters* cnt) {
+  fill_ghosts(W, P);                                                  // step 1
+  Field<double> V(P.n, ghost_width(P));                               // step 2
+  {
+    int c[3];
+    for (c[2] = -W.g[2]; c[2] < W.n[2] + W.g[2]; ++c[2])
+      for (c[1] = -W.g[1]; c[1] < W.n[1] + W.g[1]; ++c[1])
+        for (c[0] = -W.g[0]; c[0] < W.n[0] + W.g[0]; ++c[0]) {
+          double u[NV], v[NV];
+          for (int k = 0; k < NV; ++k) u[k] = W.at(k, c[0], c[1], c[2]);
+          cons_to_prim(u, v, P, cnt);
+          for (int k = 0; k < NV; ++k) V.at(k, c[0], c[1], c[2]) = v[k];
+        }
+  }
+  const int* n = P.n;
+  const size_t ncell = (size_t)n[0] * n[1] * n[2];
+  auto lidx = [&](int v, int i, int j, int k) {
+    return (((size_t)v * n[2] + k) * n[1] + j) * n[0] + i;
+  };
+  std::vector<double> L((size_t)NV * ncell, 0.0);
+  // Face electric fields (two per face: e1 along the first, e2 along the
+  // second transverse axis in cyclic order) and mass fluxes, stored at the
+  // cell owning the face.
+  //   x-face: (Ey, Ez) = ( F[Bz], -F[By])
+  //   y-face: (Ez, Ex) = ( F[Bx], -F[Bz])
+  //   z-face: (Ex, Ey) = ( F[By], -F[Bx])
+  // (F[B_t] = v_n B_t - v_t B_n and E = -v x B.)
+  CellArray Ef[3][3] = {{CellArray(n), CellArray(n), CellArray(n)},
+                        {CellArray(n), CellArray(n), CellArray(n)},
+                        {CellArray(n), CellArray(n), CellArray(n)}};  // [face dir][E comp]
+  CellArray Fm[3] = {CellArray(n), CellArray(n), CellArray(n)};
+
+  for (int d = 0; d < 3; ++d) {
+    int fn[3] = {n[0], n[1], n[2]};
+    fn[d] += 1;
+    std::vector<double> Fd((size_t)NV * fn[0] * fn[1] * fn[2]);
+    auto fidx = [&](int v, int i, int j, int k) {
+      return (((size_t)v * fn[2] + k) * fn[1] + j) * fn[0] + i;
+    };
+    const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
+    int c[3];
+    for (c[2] = 0; c[2] < fn[2]; ++c[2])
+      for (c[1] = 0; c[1] < fn[1]; ++c[1])
+        for (c[0] = 0; c[0] < fn[0]; ++c[0]) {
+          double face[2][NV];
+          face_states(P, V, d, c, face);                               // step 3
+          const double bface = bw.at(d, c[0], c[1], c[2]);
+          for (int s = 0; s < 2; ++s) {
+            face[s][BX + d] = bface;
+            face[s][PSI] = 0.0;
+          }
+          double F[NV];
+          interface_flux(face[0], face[1], d, ch, P.gamma, F);         // step 4
+          for (int k = 0; k < NV; ++k) Fd[fidx(k, c[0], c[1], c[2])] = F[k];
+          if (c[d] < n[d]) {
+            // E_e1 = -(v x B)_e1 = F[B_e2]; E_e2 = -F[B_e1]
+            Ef[d][e1].at(c[0], c[1], c[2]) = F[BX + e2];
+            Ef[d][e2].at(c[0], c[1], c[2]) = -F[BX + e1];
+            const double thr = 1e-12 * ch * V.at(RHO, c[0], c[1], c[2]);
+            Fm[d].at(c[0], c[1], c[2]) = std::fabs(F[RHO]) > thr ? F[RHO] : 0.0;
+          }
+        }
+    for (c[2] = 0; c[2] < n[2]; ++c[2])                               // step 5
+      for (c[1] = 0; c[1] < n[1]; ++c[1])
+        for (c[0] = 0; c[0] < n[0]; ++c[0]) {
+          int a[3] = {c[0], c[1], c[2]};
+          a[d] += 1;
+          for (int k : {RHO, VX, VY, VZ, PRS}) {
+            const double fp = Fd[fidx(k, a[0], a[1], a[2])];
+            const double fm = Fd[fidx(k, c[0], c[1], c[2])];
+            L[lidx(k, c[0], c[1], c[2])] -= (fp - fm) / P.dx[d];
+          }
+        }
+  }
+
+  // Cell-centred electric field E = -v x B.
+  CellArray Ec[3] = {CellArray(n), CellArray(n), CellArray(n)};
+  for (int k = 0; k < n[2]; ++k)
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i) {
+        const double vx = V.at(VX, i, j, k), vy = V.at(VY, i, j, k), vz = V.at(VZ, i, j, k);
+        const double Bx = V.at(BX, i, j, k), By = V.at(BY, i, j, k), Bz = V.at(BZ, i, j, k);
+        Ec[0].at(i, j, k) = vz * By - vy * Bz;
+        Ec[1].at(i, j, k) = vx * Bz - vz * Bx;
+        Ec[2].at(i, j, k) = vy * Bx - vx * By;
+      }
+
+  // Edge electric fields.  E_e at cell (i, j, k) lives on the cell's edge
+  // along e at the low corner of the other two directions.
+  CellArray Ee[3] = {CellArray(n), CellArray(n), CellArray(n)};
+  for (int e = 0; e < 3; ++e) {
+    const int a = (e + 1) % 3, b = (e + 2) % 3;
+    for (int k = 0; k < n[2]; ++k)
+      for (int j = 0; j < n[1]; ++j)
+        for (int i = 0; i < n[0]; ++i) {
+          // cell (i, j, k) shifted by -1 along a and/or b
+          auto sh = [&](int da, int db, int out[3]) {
+            out[0] = i;
+            out[1] = j;
+            out[2] = k;
+            out[a] -= da;
+            out[b] -= db;
+          };
+          int q[3];
+          double Ea[2], Fa[2], Eb[2], Fb[2], Ecell[2][2];
+          // a-faces of the cells on the low-b (shifted along b) and high-b side
+          for (int s = 0; s < 2; ++s) {
+            sh(0, 1 - s, q);
+            Ea[s] = Ef[a][e].at(q[0], q[1], q[2]);
+            Fa[s] = Fm[a].at(q[0], q[1], q[2]);
+            sh(1 - s, 0, q);
+            Eb[s] = Ef[b][e].at(q[0], q[1], q[2]);
+            Fb[s] = Fm[b].at(q[0], q[1], q[2]);
+          }
+          for (int ia = 0; ia < 2; ++ia)
+            for (int ib = 0; ib < 2; ++ib) {
+              sh(1 - ia, 1 - ib, q);
+              Ecell[ia][ib] = Ec[e].at(q[0], q[1], q[2]);
+            }
+          Ee[e].at(i, j, k) = ct_contact_emf(Ea, Fa, Eb, Fb, Ecell);
+        }
+  }
+
+  // Faraday's law on the faces: db_d/dt = -(curl E)_d, with
+  // (curl E)_d = dE_b/da - dE_a/db for (d, a, b) cyclic.
+  double a_n, a_w;
+  rk_coeffs(P.rk_order, stage, &a_n, &a_w);
+  for (int d = 0; d < 3; ++d) {
+    const int a = (d + 1) % 3, b = (d + 2) % 3;
+    for (int k = 0; k < n[2]; ++k)
+      for (int j = 0; j < n[1]; ++j)
+        for (int i = 0; i < n[0]; ++i) {
+          int pa[3] = {i, j, k}, pb[3] = {i, j, k};
+          pa[a] += 1;
+          pb[b] += 1;
+          const double curl = (Ee[b].at(pa[0], pa[1], pa[2]) - Ee[b].at(i, j, k)) / P.dx[a] -
+                              (Ee[a].at(pb[0], pb[1], pb[2]) - Ee[a].at(i, j, k)) / P.dx[b];
+          const double s1 = bw.at(d, i, j, k) - dt * curl;
+          bout.at(d, i, j, k) = stage == 1 ? s1 : a_n * bn->at(d, i, j, k) + a_w * s1;
+        }
+  }
+
+  // Conservative variables: rho, m, E by the flux divergence; B from the faces.
+  for (int k = 0; k < n[2]; ++k)
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i) {
+        for (int q : {RHO, VX, VY, VZ, PRS}) {
+          const double s1 = W.at(q, i, j, k) + dt * L[lidx(q, i, j, k)];
+          out.at(q, i, j, k) = stage == 1 ? s1 : a_n * Un->at(q, i, j, k) + a_w * s1;
+        }
+        out.at(PSI, i, j, k) = 0.0;
+      }
+  ct_cell_field(bout, out);
+}
+
+// One full constrained-transport step (RK2 or SSP-RK3, frozen dt, c_h).
+void ct_step(const Params& P, Field<double>& U, Faces& b, double dt, double ch,
+             Counters* cnt) {
+  const int gw = ghost_width(P);
+  Field<double> U1(P.n, gw), Un1(P.n, gw);
+  Faces b1(P.n), bn1(P.n);
+  ct_stage(P, U, b, nullptr, nullptr, dt, ch, 1, U1, b1, cnt);
+  if (P.rk_order == 3) {
+    Field<double> U2(P.n, gw);
+    Faces b2(P.n);
+    ct_stage(P, U1, b1, &U, &b, dt, ch, 2, U2, b2, cnt);
+    ct_stage(P, U2, b2, &U, &b, dt, ch, 3, Un1, bn1, cnt);
+  } else {
+    ct_stage(P, U1, b1, &U, &b, dt, ch, 2, Un1, bn1, cnt);
+  }
+  for (int k = 0; k < P.n[2]; ++k)
+    for (int j = 0; j < P.n[1]; ++j)
+      for (int i = 0; i < P.n[0]; ++i)
+        for (int q = 0; q < NV; ++q) U.at(q, i, j, k) = Un1.at(q, i, j, k);
+  b = bn1;
+}
+
+inline void load_faces(Faces& f, const double* src) {
+  const size_t m = (size_t)f.n[0] * f.n[1] * f.n[2];
+  for (int d = 0; d < 3; ++d) std::memcpy(f.b[d].data(), src + d * m, m * sizeof(double));
+}
+inline void store_faces(const Faces& f, double* dst) {
+  const size_t m = (size_t)f.n[0] * f.n[1] * f.n[2];
+  for (int d = 0; d < 3; ++d) std::memcpy(dst + d * m, f.b[d].data(), m * sizeof(double));
 }
 
 }  // namespace orc
@@ -910,6 +1211,89 @@ void orc_conserved_sums(const orc_params* p, const double* U, double out[8]) {
       s = t;
     }
     out[q] = s;
+  }
+}
+
+
+// ---- constrained transport (face field arrays are [3][nz][ny][nx]: b_d on
+// ---- the lower d-face of each cell)
+
+// nsteps CT steps in place on (U, b); dt rule and dts/chs as orc_run.
+double orc_ct_run(const orc_params* p, double* U, double* b, int nsteps, double cfl, double t0,
+                  double t_end, double* dts, double* chs, long long counters[2]) {
+  Params P = to_params(p);
+  Field<double> f(P.n, ghost_width(P));
+  load_interior(f, U, nullptr);
+  Faces fb(P.n);
+  load_faces(fb, b);
+  Counters cnt = {0, 0};
+  double t = t0;
+  double inv_sum = 0.0;
+  for (int d = 0; d < 3; ++d) inv_sum += 1.0 / P.dx[d];
+  for (int s = 0; s < nsteps; ++s) {
+    if (t_end > 0.0 && t >= t_end) break;
+    double dt, ch;
+    if (dts && dts[s] > 0.0) {
+      dt = dts[s];
+      ch = chs[s];
+    } else {
+      ch = max_speed(P, f, &cnt);
+      dt = cfl / (ch * inv_sum);
+      if (t_end > 0.0 && t + dt > t_end) dt = t_end - t;
+      if (dts) {
+        dts[s] = dt;
+        chs[s] = ch;
+      }
+    }
+    ct_step(P, f, fb, dt, ch, &cnt);
+    t += dt;
+  }
+  store_interior(f, U, nullptr);
+  store_faces(fb, b);
+  if (counters) {
+    counters[0] = cnt.rho_floor_hits;
+    counters[1] = cnt.p_floor_hits;
+  }
+  return t;
+}
+
+// One first Runge-Kutta stage with constrained transport and the given dt,
+// c_h: (W, bw) -> (out, bout) = (W, bw) + dt L(W, bw).
+void orc_ct_stage1(const orc_params* p, const double* W, const double* bw, double dt, double ch,
+                   double* out, double* bout) {
+  Params P = to_params(p);
+  Field<double> w(P.n, ghost_width(P)), o(P.n, ghost_width(P));
+  load_interior(w, W, nullptr);
+  Faces fb(P.n), fo(P.n);
+  load_faces(fb, bw);
+  ct_stage(P, w, fb, nullptr, nullptr, dt, ch, 1, o, fo, (Counters*)nullptr);
+  store_interior(o, out, nullptr);
+  store_faces(fo, bout);
+}
+
+// Face divergence of b per cell: sum_d (b_d(+1/2) - b_d(-1/2)) / dx_d.
+void orc_ct_divb(const orc_params* p, const double* b, double* out) {
+  Params P = to_params(p);
+  Faces fb(P.n);
+  load_faces(fb, b);
+  size_t m = 0;
+  for (int k = 0; k < P.n[2]; ++k)
+    for (int j = 0; j < P.n[1]; ++j)
+      for (int i = 0; i < P.n[0]; ++i, ++m)
+        out[m] = (fb.at(0, i + 1, j, k) - fb.at(0, i, j, k)) / P.dx[0] +
+                 (fb.at(1, i, j + 1, k) - fb.at(1, i, j, k)) / P.dx[1] +
+                 (fb.at(2, i, j, k + 1) - fb.at(2, i, j, k)) / P.dx[2];
+}
+
+// CT-contact edge electric field for n edges; in is [12][n]:
+// Ea0, Ea1, Fa0, Fa1, Eb0, Eb1, Fb0, Fb1, Ec00, Ec01, Ec10, Ec11.
+void orc_ct_edge_emf(const double* in, double* out, long n) {
+  for (long e = 0; e < n; ++e) {
+    auto g = [&](int r) { return in[(long)r * n + e]; };
+    const double Ea[2] = {g(0), g(1)}, Fa[2] = {g(2), g(3)};
+    const double Eb[2] = {g(4), g(5)}, Fb[2] = {g(6), g(7)};
+    const double Ec[2][2] = {{g(8), g(9)}, {g(10), g(11)}};
+    out[e] = ct_contact_emf(Ea, Fa, Eb, Fb, Ec);
   }
 }
 

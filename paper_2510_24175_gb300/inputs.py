@@ -23,6 +23,7 @@ RHO, VX, VY, VZ, BX, BY, BZ, PRS, PSI = range(9)
 LIM_FLAT, LIM_MINMOD, LIM_MC, LIM_WENOZ = 0, 1, 2, 3
 BC_PERIODIC, BC_OUTFLOW = 0, 1
 FP64, FP32 = 0, 1
+DIVB_GLM, DIVB_CT = 0, 1
 
 
 @dataclass
@@ -43,6 +44,7 @@ class Problem:
     t_end: float = 0.0            # > 0: clamp the last step to reach t_end
     precision: int = FP64
     rk_order: int = 2             # 2: RK2; 3: SSP-RK3
+    divb: int = DIVB_GLM          # div-B control: GLM cleaning or constrained transport
     seed: int = 0
     params: dict = field(default_factory=dict)
 
@@ -65,6 +67,13 @@ class Problem:
 
     def prim(self) -> np.ndarray:
         return _GENERATORS[self.params.get("ic", self.name)](self)
+
+    def faces(self) -> np.ndarray:
+        """Staggered magnetic field for constrained transport, shape
+        (3, nz, ny, nx): component d on each cell's lower d-face (at
+        x_d = xmin_d + i_d dx_d, the other coordinates at cell centres).  The
+        cell-centred B of ``prim()`` is the mean of each cell's two faces."""
+        return _FACE_GENERATORS[self.params.get("ic", self.name)](self)
 
     def with_n(self, n) -> "Problem":
         return replace(self, n=tuple(n))
@@ -217,6 +226,161 @@ def _random_smooth(pb: Problem) -> np.ndarray:
     return V
 
 
+# ------------------------------------------- staggered (face) magnetic fields --
+def _cell_mean(b: np.ndarray) -> np.ndarray:
+    """Cell-centred field = mean of each cell's two faces (periodic)."""
+    return np.stack([0.5 * (b[0] + np.roll(b[0], -1, axis=2)),
+                     0.5 * (b[1] + np.roll(b[1], -1, axis=1)),
+                     0.5 * (b[2] + np.roll(b[2], -1, axis=0))])
+
+
+def _faces_from_cells(pb: Problem) -> np.ndarray:
+    """For fields whose component d does not vary along d (Orszag-Tang,
+    plane-parallel states with a constant normal component, z-polarised
+    waves in the x-y plane): the face value equals the cell value."""
+    V = pb.prim()
+    return np.ascontiguousarray(V[BX:BZ + 1])
+
+
+def _potential_modes(pb: Problem):
+    """Seeded Fourier modes of a smooth periodic vector potential on [0,1]^3:
+    per component, six (k, amplitude, phase) triples with |k_i| <= 3."""
+    rng = np.random.default_rng(pb.seed + 7919)
+    modes = []
+    for _ in range(3):
+        comp = []
+        while len(comp) < 6:
+            k = rng.integers(-3, 4, size=3)
+            if not k.any():
+                continue
+            amp = pb.params.get("a_amp", 0.08) * rng.standard_normal() / np.linalg.norm(k)
+            comp.append((k.astype(np.float64), amp, rng.uniform(0.0, 2.0 * math.pi)))
+        modes.append(comp)
+    return modes
+
+
+def _line_integral(comp_modes, c: int, mid, h: float):
+    """Exact integral of sum_m a_m sin(2 pi k_m . x + phi_m) along axis c over a
+    segment of length h centred at the points ``mid`` (tuple of broadcastable
+    x, y, z arrays): h sin(2 pi k . mid + phi) sinc(pi k_c h) per mode."""
+    out = 0.0
+    for k, a, ph in comp_modes:
+        arg = 2.0 * math.pi * (k[0] * mid[0] + k[1] * mid[1] + k[2] * mid[2]) + ph
+        u = math.pi * k[c] * h
+        sinc = math.sin(u) / u if u != 0.0 else 1.0
+        out = out + a * h * sinc * np.sin(arg)
+    return out
+
+
+def _potential_faces(pb: Problem) -> np.ndarray:
+    """Face averages of B = B_mean + curl A, each from Stokes' theorem as the
+    exact circulation of A around the face divided by its area, so the
+    discrete divergence vanishes to round-off."""
+    nx, ny, nz = pb.n
+    dx, dy, dz = pb.dx
+    xf = (np.arange(nx) * dx)[None, None, :]
+    yf = (np.arange(ny) * dy)[None, :, None]
+    zf = (np.arange(nz) * dz)[:, None, None]
+    xc, yc, zc = xf + 0.5 * dx, yf + 0.5 * dy, zf + 0.5 * dz
+    A = _potential_modes(pb)
+    shape = (nz, ny, nx)
+    b = np.zeros((3,) + shape)
+    # x-face at x = xf: circulation in the (y, z) plane
+    b[0] = ((_line_integral(A[2], 2, (xf, yf + dy, zc), dz)
+             - _line_integral(A[2], 2, (xf, yf, zc), dz))
+            - (_line_integral(A[1], 1, (xf, yc, zf + dz), dy)
+               - _line_integral(A[1], 1, (xf, yc, zf), dy))) / (dy * dz)
+    # y-face at y = yf: circulation in the (z, x) plane
+    b[1] = ((_line_integral(A[0], 0, (xc, yf, zf + dz), dx)
+             - _line_integral(A[0], 0, (xc, yf, zf), dx))
+            - (_line_integral(A[2], 2, (xf + dx, yf, zc), dz)
+               - _line_integral(A[2], 2, (xf, yf, zc), dz))) / (dz * dx)
+    # z-face at z = zf: circulation in the (x, y) plane
+    b[2] = ((_line_integral(A[1], 1, (xf + dx, yc, zf), dy)
+             - _line_integral(A[1], 1, (xf, yc, zf), dy))
+            - (_line_integral(A[0], 0, (xc, yf + dy, zf), dx)
+               - _line_integral(A[0], 0, (xc, yf, zf), dx))) / (dx * dy)
+    b += np.asarray(pb.params.get("B_mean", (0.3, -0.2, 0.1)))[:, None, None, None]
+    return b
+
+
+def _ct_random(pb: Problem) -> np.ndarray:
+    """Seeded smooth state (rho, v, p as the random smooth state, psi = 0)
+    with a divergence-free staggered field; cell B = face means."""
+    V = _random_smooth(pb)
+    V[PSI] = 0.0
+    V[BX:BZ + 1] = _cell_mean(_potential_faces(pb))
+    return V
+
+
+def _shock_pair(pb: Problem) -> np.ndarray:
+    """Two Brio-Wu shock tubes back to back along ``axis`` (periodic): the
+    Brio-Wu left state for s < 0.25 or s >= 0.75, the right state between;
+    normal field 0.75; the transverse field in the next axis (cyclic)."""
+    a = pb.params.get("axis", 0)
+    V = _empty(pb)
+    s = pb.centres()[a]
+    inner = np.broadcast_to((s >= 0.25) & (s < 0.75), V[0].shape)
+    V[RHO] = np.where(inner, 0.125, 1.0)
+    V[PRS] = np.where(inner, 0.1, 1.0)
+    V[BX + (a + 1) % 3] = np.where(inner, -1.0, 1.0)
+    V[BX + a] = 0.75
+    return V
+
+
+def _field_loop(pb: Problem) -> np.ndarray:
+    """Weak magnetic field loop (Gardiner & Stone 2005) advected by a uniform
+    flow: A_z = A0 max(R - r, 0) about the box centre, rho = p = 1."""
+    V = _empty(pb)
+    V[RHO] = 1.0
+    V[PRS] = 1.0
+    vel = pb.params.get("v", (1.0, 0.5, 0.0))
+    for d in range(3):
+        V[VX + d] = vel[d]
+    V[BX:BZ + 1] = _cell_mean(_field_loop_faces(pb))
+    return V
+
+
+def _field_loop_faces(pb: Problem) -> np.ndarray:
+    nx, ny, nz = pb.n
+    dx, dy, _ = pb.dx
+    a0 = pb.params.get("A0", 1e-3)
+    R = pb.params.get("R", 0.3)
+
+    def az(x, y):
+        r = np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2)
+        return a0 * np.maximum(R - r, 0.0)
+
+    xf = (np.arange(nx) * dx)[None, None, :]
+    yf = (np.arange(ny) * dy)[None, :, None]
+    b = np.zeros((3, nz, ny, nx))
+    b[0] = np.broadcast_to((az(xf, yf + dy) - az(xf, yf)) / dy, b[0].shape)
+    b[1] = np.broadcast_to(-(az(xf + dx, yf) - az(xf, yf)) / dx, b[1].shape)
+    return b
+
+
+def _alfven_oblique(pb: Problem) -> np.ndarray:
+    """Linear Alfven wave travelling along (1, 1, 0)/sqrt 2 with wave vector
+    2 pi (1, 1, 0): background B0 = |B0| (1, 1, 0)/sqrt 2, z-polarised
+    perturbation dv_z = A sin(2 pi (x + y)), dB_z = -A sqrt(rho) sin(...)."""
+    V = _empty(pb)
+    x, y, _ = pb.centres()
+    rho0 = pb.params.get("rho0", 1.0)
+    amp = pb.params.get("amp", 1e-6)
+    bpar = pb.params.get("B0", 1.0)
+    t = pb.params.get("t", 0.0)
+    vA = bpar / math.sqrt(rho0)
+    ph = 2.0 * math.pi * (x + y - math.sqrt(2.0) * vA * t)
+    sn = np.broadcast_to(np.sin(ph), V[0].shape)
+    V[RHO] = rho0
+    V[PRS] = pb.params.get("p0", 1.0)
+    V[BX] = bpar / math.sqrt(2.0)
+    V[BY] = bpar / math.sqrt(2.0)
+    V[VZ] = amp * sn
+    V[BZ] = -amp * math.sqrt(rho0) * sn
+    return V
+
+
 _GENERATORS = {
     "brio_wu": _brio_wu,
     "orszag_tang": _orszag_tang,
@@ -224,6 +388,19 @@ _GENERATORS = {
     "linear_wave": _linear_wave,
     "uniform": _uniform,
     "random_smooth": _random_smooth,
+    "ct_random": _ct_random,
+    "shock_pair": _shock_pair,
+    "field_loop": _field_loop,
+    "alfven_oblique": _alfven_oblique,
+}
+
+_FACE_GENERATORS = {
+    "orszag_tang": _faces_from_cells,
+    "uniform": _faces_from_cells,
+    "shock_pair": _faces_from_cells,
+    "alfven_oblique": _faces_from_cells,
+    "ct_random": _potential_faces,
+    "field_loop": _field_loop_faces,
 }
 
 
@@ -249,6 +426,40 @@ def turbulent_box(n: int = 512, steps: int = 50, seed: int = 3,
 def orszag_tang_2d(n: int = 512, steps: int = 200) -> Problem:
     """2-D Orszag-Tang (n x n x 1), used by the adjoint workload."""
     return Problem("orszag_tang", (n, n, 1), limiter=LIM_MC, steps=steps)
+
+
+def orszag_tang_3d_ct(n: int = 256, steps: int = 20, limiter: int = LIM_MC,
+                      rk_order: int = 2) -> Problem:
+    """3-D Orszag-Tang with constrained transport (periodic [0,1]^3)."""
+    return Problem("orszag_tang", (n, n, n), limiter=limiter, steps=steps, rk_order=rk_order,
+                   divb=DIVB_CT)
+
+
+def ct_random(n, seed: int = 11) -> Problem:
+    """Seeded smooth state with a divergence-free staggered field."""
+    n = tuple(n) if not isinstance(n, int) else (n, n, n)
+    return Problem("ct_random", n, limiter=LIM_MC, seed=seed, divb=DIVB_CT)
+
+
+def shock_pair(n_long: int, n_trans: int = 4, axis: int = 0) -> Problem:
+    """Two back-to-back Brio-Wu tubes along ``axis`` on a periodic 3-D grid
+    (gamma = 2, minmod), constant across the other two axes."""
+    n = [n_trans] * 3
+    n[axis] = n_long
+    return Problem("shock_pair", tuple(n), gamma=2.0, limiter=LIM_MINMOD, divb=DIVB_CT,
+                   params={"axis": axis})
+
+
+def field_loop(n: int, nz: int = 2, v=(1.0, 0.5, 0.0)) -> Problem:
+    """Weak field loop advected diagonally (periodic [0,1]^2 x nz planes)."""
+    return Problem("field_loop", (n, n, nz), limiter=LIM_MC, divb=DIVB_CT,
+                   params={"v": tuple(v)})
+
+
+def alfven_oblique(n: int, nz: int = 2, amp: float = 1e-6) -> Problem:
+    """Oblique linear Alfven wave in the x-y plane (periodic, nz planes)."""
+    return Problem("alfven_oblique", (n, n, nz), limiter=LIM_MC, divb=DIVB_CT,
+                   params={"amp": amp})
 
 
 def adjoint_perturbation(pb: Problem, seed: int = 4, rms: float = 1e-3,
