@@ -61,6 +61,18 @@ enum { MHD_HOST = 0, MHD_DEVICE = 1 };
 enum { MHD_CONS = 0, MHD_PRIM = 1 };
 /* mhd_config.flags */
 enum { MHD_FLAG_ADJOINT = 1 };
+/* Divergence control (Section 3.2: one of several mutually exclusive
+ * algorithms; Section 4.2: divergence cleaning in the strong-scaling runs,
+ * constrained transport in the weak-scaling runs).
+ * MHD_DIVB_GLM: Dedner et al. (2002) mixed GLM cleaning with the psi field.
+ * MHD_DIVB_CT: constrained transport (Evans & Hawley 1988): a staggered
+ *   face field b (b_d on each cell's lower d-face) advanced by Faraday's law
+ *   with edge electric fields from the upwind CT-contact average of Gardiner
+ *   & Stone (2005); the face divergence is preserved to round-off; psi is
+ *   identically 0; the cell-centred B of the state is the mean of each
+ *   cell's two faces.  Needs three active dimensions and periodic boundaries;
+ *   not available for the adjoint or the ensemble. */
+enum { MHD_DIVB_GLM = 0, MHD_DIVB_CT = 1 };
 
 typedef struct mhd_config {
   int n[3];              /* nx, ny, nz >= 1; active dims need n >= 2          */
@@ -78,12 +90,13 @@ typedef struct mhd_config {
   int flags;             /* MHD_FLAG_* (ADJOINT reserves adjoint buffers)     */
   int rk_order;          /* 2: RK2 (default); 3: SSP-RK3 of Shu & Osher,
                             the time integrator of the paper's runs          */
+  int divb;              /* MHD_DIVB_GLM (default) or MHD_DIVB_CT             */
 } mhd_config;
 
 typedef struct mhd_ctx mhd_ctx;
 
 /* Fills *cfg with defaults: gamma 5/3, cfl 0.8, glm_alpha 0.1, floors 1e-12,
- * MC limiter, periodic BCs, FP64, RK2, unit domain, n = (1,1,1). */
+ * MC limiter, periodic BCs, FP64, RK2, GLM, unit domain, n = (1,1,1). */
 int mhd_config_default(mhd_config* cfg);
 
 /* Device workspace the context needs for cfg (bytes, before alignment). */
@@ -110,6 +123,26 @@ int mhd_set_state(mhd_ctx* ctx, const double* U, int where, int kind);
  * the device and needs where = MHD_DEVICE).  where = MHD_HOST synchronises. */
 int mhd_get_state(mhd_ctx* ctx, double* U, int where, int kind);
 
+/* MHD_DIVB_CT only.  Sets the staggered face field from a float64 array b of
+ * [3][nz][ny][nx] (where = MHD_HOST or MHD_DEVICE): b[d] holds the normal
+ * field on each cell's lower d-face (at x_d = xmin_d + i_d dx_d).  Rounded to
+ * FP32 in FP32 mode.  The state's cell-centred B becomes the mean of each
+ * cell's two faces and its total energy is changed by the magnetic-energy
+ * difference, so the pressure is kept (a state whose B already equals the
+ * face means is unchanged).  Needs a state (mhd_set_state first); every
+ * mhd_set_state must be followed by a face field before mhd_step.  The field
+ * should be divergence free (mhd_divb_max): constrained transport preserves
+ * whatever divergence it starts with. */
+int mhd_set_face_field(mhd_ctx* ctx, const double* b, int where);
+
+/* MHD_DIVB_CT only: copies the face field out as float64 [3][nz][ny][nx].
+ * where = MHD_HOST synchronises. */
+int mhd_get_face_field(mhd_ctx* ctx, double* b, int where);
+
+/* MHD_DIVB_CT only: max over cells of |sum_d (b_d(+1/2) - b_d(-1/2)) / dx_d|
+ * of the face field, computed in FP64.  Synchronises. */
+int mhd_divb_max(mhd_ctx* ctx, double* out);
+
 /* CFL time step of the current state (Section 3.2's explicit scheme; the rule
  * is lambda = max over cells and active d of |v_d| + c_f,d, c_h = lambda,
  * dt = cfl / (c_h sum_d 1/dx_d)).  Synchronises.  Either pointer may be NULL. */
@@ -117,7 +150,9 @@ int mhd_dt(mhd_ctx* ctx, double* dt, double* ch);
 
 /* One Runge-Kutta step.  RK2:  U1 = U + dt L(U);  U' = (U + U1 + dt L(U1))/2.
  * SSP-RK3 (rk_order 3):  U1 = U + dt L(U);  U2 = 3/4 U + 1/4 (U1 + dt L(U1));
- * U' = 1/3 U + 2/3 (U2 + dt L(U2)).  Then psi' *= exp(-glm_alpha c_h dt / dh_min).  dt > 0 and ch > 0 are used as
+ * U' = 1/3 U + 2/3 (U2 + dt L(U2)).  GLM: then psi' *= exp(-glm_alpha c_h dt /
+ * dh_min).  CT: the face field takes the same stages (its L is -curl E), and
+ * c_h only enters the (unused) psi flux.  dt > 0 and ch > 0 are used as
  * given; dt <= 0 uses the CFL rule on the device (clamped to t_end when
  * t_end > 0); ch <= 0 uses c_h = lambda of the current state.  Does not
  * synchronise: dt and c_h stay on the device (see mhd_step_info). */
@@ -159,10 +194,11 @@ int mhd_adjoint_step(mhd_ctx* ctx, const double* U_n, const double* lam_np1, dou
  * the context's stream (off by default; the events are created on the host
  * when enabled).  Kernel classes: 0 = step prepare, 1 = first RK stage,
  * 2 = last RK stage, 3 = max-wave-speed reduction, 4 = middle stage of
- * SSP-RK3.  mhd_profile_read() synchronises, returns the launch count and
+ * SSP-RK3, 5 = constrained-transport edge / face / cell kernels (one record
+ * per stage).  mhd_profile_read() synchronises, returns the launch count and
  * total milliseconds per class since the last read, and clears the record. */
 int mhd_profile_enable(mhd_ctx* ctx, int enable);
-int mhd_profile_read(mhd_ctx* ctx, long long counts[5], double ms[5]);
+int mhd_profile_read(mhd_ctx* ctx, long long counts[6], double ms[6]);
 
 /* Conservation sums for callers that can't allocate device memory: a host
  * application whose GPU memory is owned by another allocator, a code that

@@ -31,12 +31,14 @@ MHD_FP64, MHD_FP32 = 0, 1
 MHD_HOST, MHD_DEVICE = 0, 1
 MHD_CONS, MHD_PRIM = 0, 1
 MHD_FLAG_ADJOINT = 1
+MHD_DIVB_GLM, MHD_DIVB_CT = 0, 1
 
 EXPORTED = ["mhd_config_default", "mhd_workspace_bytes", "mhd_create", "mhd_set_stream",
             "mhd_set_state", "mhd_get_state", "mhd_dt", "mhd_step", "mhd_step_info",
             "mhd_counters", "mhd_conserved_sums", "mhd_flux_batch", "mhd_adjoint_step",
             "mhd_profile_enable", "mhd_profile_read", "mhd_conserved_sums_noalloc",
-            "mhd_last_error", "mhd_destroy",
+            "mhd_last_error", "mhd_destroy", "mhd_set_face_field", "mhd_get_face_field",
+            "mhd_divb_max",
             "mhd_ensemble_workspace_bytes", "mhd_ensemble_create", "mhd_ensemble_set_state",
             "mhd_ensemble_get_state", "mhd_ensemble_step", "mhd_ensemble_info",
             "mhd_ensemble_autotune", "mhd_ensemble_last_error", "mhd_ensemble_destroy"]
@@ -55,7 +57,7 @@ class mhd_config(ctypes.Structure):
                 ("rho_floor", ctypes.c_double), ("p_floor", ctypes.c_double),
                 ("t_end", ctypes.c_double), ("limiter", ctypes.c_int),
                 ("bc", ctypes.c_int * 6), ("precision", ctypes.c_int), ("flags", ctypes.c_int),
-                ("rk_order", ctypes.c_int)]
+                ("rk_order", ctypes.c_int), ("divb", ctypes.c_int)]
 
 
 _lib = None
@@ -79,6 +81,9 @@ def lib():
         L.mhd_set_stream.argtypes = [vp, vp]
         L.mhd_set_state.argtypes = [vp, vp, i, i]
         L.mhd_get_state.argtypes = [vp, vp, i, i]
+        L.mhd_set_face_field.argtypes = [vp, vp, i]
+        L.mhd_get_face_field.argtypes = [vp, vp, i]
+        L.mhd_divb_max.argtypes = [vp, dp]
         L.mhd_dt.argtypes = [vp, dp, dp]
         L.mhd_step.argtypes = [vp, d, d]
         L.mhd_step_info.argtypes = [vp, dp]
@@ -161,6 +166,22 @@ def mhd_get_state(ctx, U, where=MHD_DEVICE, kind=MHD_CONS):
     _check(lib().mhd_get_state(ctx, p, where, kind), ctx, "mhd_get_state")
 
 
+def mhd_set_face_field(ctx, b, where=MHD_DEVICE):
+    p = _ptr(b) if where == MHD_DEVICE else b.ctypes.data_as(ctypes.c_void_p)
+    _check(lib().mhd_set_face_field(ctx, p, where), ctx, "mhd_set_face_field")
+
+
+def mhd_get_face_field(ctx, b, where=MHD_DEVICE):
+    p = _ptr(b) if where == MHD_DEVICE else b.ctypes.data_as(ctypes.c_void_p)
+    _check(lib().mhd_get_face_field(ctx, p, where), ctx, "mhd_get_face_field")
+
+
+def mhd_divb_max(ctx) -> float:
+    out = ctypes.c_double()
+    _check(lib().mhd_divb_max(ctx, ctypes.byref(out)), ctx, "mhd_divb_max")
+    return out.value
+
+
 def mhd_dt(ctx):
     dt, ch = ctypes.c_double(), ctypes.c_double()
     _check(lib().mhd_dt(ctx, ctypes.byref(dt), ctypes.byref(ch)), ctx, "mhd_dt")
@@ -218,6 +239,7 @@ class Config:
     precision: int = MHD_FP64
     flags: int = 0
     rk_order: int = 2
+    divb: int = MHD_DIVB_GLM
 
     @classmethod
     def from_problem(cls, pb, precision=None, flags: int = 0) -> "Config":
@@ -225,7 +247,7 @@ class Config:
                    cfl=pb.cfl, glm_alpha=pb.glm_alpha, rho_floor=pb.rho_floor,
                    p_floor=pb.p_floor, t_end=pb.t_end, limiter=pb.limiter, bc=tuple(pb.bc),
                    precision=pb.precision if precision is None else precision, flags=flags,
-                   rk_order=getattr(pb, "rk_order", 2))
+                   rk_order=getattr(pb, "rk_order", 2), divb=getattr(pb, "divb", MHD_DIVB_GLM))
 
     def c(self) -> mhd_config:
         c = mhd_config()
@@ -237,6 +259,7 @@ class Config:
         c.rho_floor, c.p_floor, c.t_end = self.rho_floor, self.p_floor, self.t_end
         c.limiter, c.precision, c.flags = int(self.limiter), int(self.precision), int(self.flags)
         c.rk_order = int(self.rk_order)
+        c.divb = int(self.divb)
         for s in range(6):
             c.bc[s] = int(self.bc[s])
         return c
@@ -284,6 +307,32 @@ class MHD:
             assert tuple(U.shape) == self.shape
             mhd_set_state(self.ctx, U, MHD_DEVICE, kind)
 
+    def set_face_field(self, b):
+        """Constrained transport: face field b of shape (3, nz, ny, nx), float64
+        (CUDA tensor or numpy array); b[d] on each cell's lower d-face."""
+        shape = (3,) + self.shape[1:]
+        if isinstance(b, np.ndarray):
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            assert b.shape == shape
+            mhd_set_face_field(self.ctx, b, MHD_HOST)
+        else:
+            torch = _torch()
+            assert b.is_cuda and b.dtype == torch.float64 and b.is_contiguous()
+            assert tuple(b.shape) == shape
+            mhd_set_face_field(self.ctx, b, MHD_DEVICE)
+
+    def get_face_field(self, out=None):
+        """Constrained transport: the face field as a float64 CUDA tensor (or
+        into ``out``; a numpy ``out`` receives a host copy)."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty((3,) + self.shape[1:], dtype=torch.float64, device="cuda")
+        mhd_get_face_field(self.ctx, out, MHD_HOST if isinstance(out, np.ndarray) else MHD_DEVICE)
+        return out
+
+    def divb_max(self) -> float:
+        return mhd_divb_max(self.ctx)
+
     def get_state(self, out=None, kind=MHD_CONS):
         """Returns the state as a float64 CUDA tensor (or fills ``out``; a
         numpy ``out`` receives a host copy)."""
@@ -322,11 +371,11 @@ class MHD:
 
     def profile_read(self):
         """{kernel class: (launches, total ms)} since the last read."""
-        cnt = (ctypes.c_longlong * 5)()
-        ms = (ctypes.c_double * 5)()
+        cnt = (ctypes.c_longlong * 6)()
+        ms = (ctypes.c_double * 6)()
         _check(lib().mhd_profile_read(self.ctx, cnt, ms), self.ctx, "mhd_profile_read")
-        names = ("prep", "stage1", "stage2", "max_speed", "stage_mid")
-        return {names[k]: (int(cnt[k]), float(ms[k])) for k in range(5)}
+        names = ("prep", "stage1", "stage2", "max_speed", "stage_mid", "ct")
+        return {names[k]: (int(cnt[k]), float(ms[k])) for k in range(6)}
 
     def adjoint_step(self, U_n, lam_np1, lam_n, dt: float, ch: float):
         mhd_adjoint_step(self.ctx, U_n, lam_np1, lam_n, dt, ch)

@@ -122,9 +122,21 @@ static int validate(const mhd_config* c, char* msg, size_t len) {
     return MHD_ERR_INVALID;
   }
   if ((c->flags & MHD_FLAG_ADJOINT) &&
-      (c->precision != MHD_FP64 || c->rk_order != 2 || c->limiter == MHD_LIM_WENOZ)) {
-    snprintf(msg, len, "the adjoint needs MHD_FP64, RK2 and a PLM limiter");
+      (c->precision != MHD_FP64 || c->rk_order != 2 || c->limiter == MHD_LIM_WENOZ ||
+       c->divb != MHD_DIVB_GLM)) {
+    snprintf(msg, len, "the adjoint needs MHD_FP64, RK2, a PLM limiter and GLM");
     return MHD_ERR_INVALID;
+  }
+  if (c->divb != MHD_DIVB_GLM && c->divb != MHD_DIVB_CT) {
+    snprintf(msg, len, "bad divb %d", c->divb);
+    return MHD_ERR_INVALID;
+  }
+  if (c->divb == MHD_DIVB_CT) {
+    for (int d = 0; d < 3; ++d)
+      if (c->n[d] < 2 || c->bc[2 * d] != MHD_BC_PERIODIC) {
+        snprintf(msg, len, "constrained transport needs three active periodic dimensions");
+        return MHD_ERR_INVALID;
+      }
   }
   return MHD_OK;
 }
@@ -176,6 +188,44 @@ static int choose_tz(const mhd::Grid& g, int ctas_per_sm, int ty) {
   return best;
 }
 
+// The face field that belongs to state buffer U (constrained transport).
+static void* faces_of(mhd_ctx* c, void* U) {
+  if (U == c->Ua) return c->fa;
+  if (U == c->Ub) return c->fb;
+  if (U == c->Uc) return c->fc;
+  return nullptr;
+}
+
+// One constrained-transport stage: the fused stage kernel (rho, m, E and the
+// face / cell electric fields), then edge fields, the face update with the
+// Runge-Kutta combination, and the cell-centred B (+ the wave-speed
+// reduction after the last stage).
+template <class T>
+static int ct_stage(mhd_ctx* c, int kind, int cls, void* win, void* un, void* out, double an,
+                    double aw) {
+  const T* bw[3];
+  const T* fw = static_cast<const T*>(faces_of(c, win));
+  for (int d = 0; d < 3; ++d) bw[d] = fw + (size_t)d * c->grid.ncell;
+  const T* fn = un ? static_cast<const T*>(faces_of(c, un)) : nullptr;
+  T* fo = static_cast<T*>(faces_of(c, out));
+  T* ctf = static_cast<T*>(c->ctf);
+  T* edge = static_cast<T*>(c->edge);
+  {
+    ProfScope ps(c, cls);
+    CK(c, mhd::launch_stage<T>(c->grid, kind, static_cast<const T*>(win),
+                               static_cast<const T*>(un), static_cast<T*>(out), &c->scal->sc,
+                               &c->scal->lam_bits, c->scal->floor_cnt, c->stream, an, aw, bw,
+                               ctf));
+  }
+  ProfScope ps(c, 5);
+  CK(c, mhd::launch_ct_edges<T>(c->grid, ctf, edge, c->stream));
+  CK(c, mhd::launch_ct_faces<T>(c->grid, kind == 1, edge, fw, fn, fo, &c->scal->sc, an, aw,
+                                c->stream));
+  CK(c, mhd::launch_ct_cells<T>(c->grid, kind == 2, fo, static_cast<T*>(out),
+                                &c->scal->lam_bits, c->scal->floor_cnt, c->stream));
+  return MHD_OK;
+}
+
 extern "C" {
 
 int mhd_config_default(mhd_config* cfg) {
@@ -197,6 +247,7 @@ int mhd_config_default(mhd_config* cfg) {
   cfg->precision = MHD_FP64;
   cfg->flags = 0;
   cfg->rk_order = 2;
+  cfg->divb = MHD_DIVB_GLM;
   return MHD_OK;
 }
 
@@ -211,6 +262,9 @@ int mhd_workspace_bytes(const mhd_config* cfg, size_t* bytes) {
   const int nstate = cfg->rk_order == 3 ? 3 : 2;
   size_t total = nstate * state + align256(sizeof(Scalars)) +
                  align256(kSumBlocks * 8 * sizeof(double));
+  if (cfg->divb == MHD_DIVB_CT)
+    total += nstate * align256((size_t)3 * g.ncell * es) +
+             align256((size_t)mhd::kCtPlanes * g.ncell * es) + align256((size_t)3 * g.ncell * es);
   if (cfg->flags & MHD_FLAG_ADJOINT) total += align256(mhd::adjoint_scratch_bytes(g));
   *bytes = total;
   return MHD_OK;
@@ -264,6 +318,23 @@ int mhd_create(const mhd_config* cfg, void* d_workspace, size_t bytes, void* str
   off += align256(sizeof(Scalars));
   c->partials = reinterpret_cast<double*>(c->ws + off);
   off += align256(kSumBlocks * 8 * sizeof(double));
+  c->fa = c->fb = c->fc = c->ctf = c->edge = nullptr;
+  c->faces_set = false;
+  if (cfg->divb == MHD_DIVB_CT) {
+    const size_t fbytes = align256((size_t)3 * c->grid.ncell * c->esize);
+    c->fa = c->ws + off;
+    off += fbytes;
+    c->fb = c->ws + off;
+    off += fbytes;
+    if (cfg->rk_order == 3) {
+      c->fc = c->ws + off;
+      off += fbytes;
+    }
+    c->ctf = c->ws + off;
+    off += align256((size_t)mhd::kCtPlanes * c->grid.ncell * c->esize);
+    c->edge = c->ws + off;
+    off += fbytes;
+  }
   c->adj = nullptr;
   c->adj_bytes = 0;
   if (cfg->flags & MHD_FLAG_ADJOINT) {
@@ -346,6 +417,77 @@ int mhd_set_state(mhd_ctx* c, const double* U, int where, int kind) {
   CK(c, cudaMemsetAsync(c->scal, 0, sizeof(Scalars), c->stream));
   c->have_state = true;
   c->lam_valid = false;
+  c->faces_set = false;
+  return MHD_OK;
+}
+
+int mhd_set_face_field(mhd_ctx* c, const double* b, int where) {
+  if (!c) return MHD_ERR_INVALID;
+  if (c->cfg.divb != MHD_DIVB_CT)
+    return fail(c, MHD_ERR_STATE, "mhd_set_face_field needs MHD_DIVB_CT");
+  if (!b || (where != MHD_HOST && where != MHD_DEVICE))
+    return fail(c, MHD_ERR_INVALID, "mhd_set_face_field: bad argument");
+  if (!c->have_state) return fail(c, MHD_ERR_STATE, "mhd_set_face_field before mhd_set_state");
+  const long long n = 3 * c->grid.ncell;
+  const cudaMemcpyKind mk = where == MHD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (c->esize == 8) {
+    CK(c, cudaMemcpyAsync(c->fa, b, n * 8, mk, c->stream));
+    CK(c, mhd::launch_ct_set_cells<double>(c->grid, static_cast<const double*>(c->fa),
+                                           static_cast<double*>(c->Ua), c->stream));
+  } else {
+    const double* src = b;
+    if (where == MHD_HOST) {  // Ub holds 9 FP32 planes = 4.5 FP64 planes >= 3
+      CK(c, cudaMemcpyAsync(c->Ub, b, n * 8, mk, c->stream));
+      src = static_cast<const double*>(c->Ub);
+    }
+    CK(c, mhd::launch_f64_to_f32(src, static_cast<float*>(c->fa), n, c->stream));
+    CK(c, mhd::launch_ct_set_cells<float>(c->grid, static_cast<const float*>(c->fa),
+                                          static_cast<float*>(c->Ua), c->stream));
+  }
+  c->faces_set = true;
+  c->lam_valid = false;
+  return MHD_OK;
+}
+
+int mhd_get_face_field(mhd_ctx* c, double* b, int where) {
+  if (!c) return MHD_ERR_INVALID;
+  if (c->cfg.divb != MHD_DIVB_CT)
+    return fail(c, MHD_ERR_STATE, "mhd_get_face_field needs MHD_DIVB_CT");
+  if (!b || (where != MHD_HOST && where != MHD_DEVICE))
+    return fail(c, MHD_ERR_INVALID, "mhd_get_face_field: bad argument");
+  if (!c->faces_set) return fail(c, MHD_ERR_STATE, "no face field set");
+  const long long n = 3 * c->grid.ncell;
+  if (c->esize == 8) {
+    CK(c, cudaMemcpyAsync(b, c->fa, n * 8,
+                          where == MHD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                          c->stream));
+  } else if (where == MHD_DEVICE) {
+    CK(c, mhd::launch_f32_to_f64(static_cast<const float*>(c->fa), b, n, c->stream));
+  } else {
+    double* B = static_cast<double*>(c->Ub);
+    CK(c, mhd::launch_f32_to_f64(static_cast<const float*>(c->fa), B, n, c->stream));
+    CK(c, cudaMemcpyAsync(b, B, n * 8, cudaMemcpyDeviceToHost, c->stream));
+  }
+  if (where == MHD_HOST) CK(c, cudaStreamSynchronize(c->stream));
+  return MHD_OK;
+}
+
+int mhd_divb_max(mhd_ctx* c, double* out) {
+  if (!c || !out) return MHD_ERR_INVALID;
+  if (c->cfg.divb != MHD_DIVB_CT) return fail(c, MHD_ERR_STATE, "mhd_divb_max needs MHD_DIVB_CT");
+  if (!c->faces_set) return fail(c, MHD_ERR_STATE, "no face field set");
+  CK(c, cudaMemsetAsync(&c->scal->aux_bits, 0, sizeof(unsigned long long), c->stream));
+  if (c->esize == 8)
+    CK(c, mhd::launch_ct_divb<double>(c->grid, static_cast<const double*>(c->fa),
+                                      &c->scal->aux_bits, c->stream));
+  else
+    CK(c, mhd::launch_ct_divb<float>(c->grid, static_cast<const float*>(c->fa),
+                                     &c->scal->aux_bits, c->stream));
+  unsigned long long bits = 0;
+  CK(c, cudaMemcpyAsync(&bits, &c->scal->aux_bits, sizeof(bits), cudaMemcpyDeviceToHost,
+                        c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  memcpy(out, &bits, sizeof(*out));
   return MHD_OK;
 }
 
@@ -419,6 +561,8 @@ int mhd_dt(mhd_ctx* c, double* dt, double* ch) {
 int mhd_step(mhd_ctx* c, double dt, double ch) {
   if (!c) return MHD_ERR_INVALID;
   if (!c->have_state) return fail(c, MHD_ERR_STATE, "mhd_step before mhd_set_state");
+  if (c->cfg.divb == MHD_DIVB_CT && !c->faces_set)
+    return fail(c, MHD_ERR_STATE, "constrained transport: mhd_set_face_field after mhd_set_state");
   if (std::isnan(dt) || std::isnan(ch) || std::isinf(dt) || std::isinf(ch))
     return fail(c, MHD_ERR_INVALID, "mhd_step: non-finite dt or ch");
   if (!(dt > 0.0) || !(ch > 0.0)) {
@@ -457,6 +601,12 @@ int mhd_step(mhd_ctx* c, double dt, double ch) {
   }
   for (int i = 0; i < nst; ++i) {
     const St& q = seq[i];
+    int rc = c->cfg.divb == MHD_DIVB_CT
+                 ? (c->esize == 8 ? ct_stage<double>(c, q.kind, q.cls, q.win, q.un, q.out, q.an, q.aw)
+                                  : ct_stage<float>(c, q.kind, q.cls, q.win, q.un, q.out, q.an, q.aw))
+                 : MHD_OK;
+    if (rc != MHD_OK) return rc;
+    if (c->cfg.divb == MHD_DIVB_CT) continue;
     ProfScope ps(c, q.cls);
     if (c->esize == 8)
       CK(c, mhd::launch_stage<double>(c->grid, q.kind, static_cast<const double*>(q.win),
@@ -553,9 +703,9 @@ int mhd_profile_enable(mhd_ctx* c, int enable) {
   return MHD_OK;
 }
 
-int mhd_profile_read(mhd_ctx* c, long long counts[5], double ms[5]) {
+int mhd_profile_read(mhd_ctx* c, long long counts[6], double ms[6]) {
   if (!c || !counts || !ms) return MHD_ERR_INVALID;
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < 6; ++k) {
     counts[k] = 0;
     ms[k] = 0.0;
   }

@@ -20,6 +20,7 @@ struct Scalars {  // device block at the start of the scalar region
   unsigned int status;
   unsigned int pad;
   double sums[8];
+  unsigned long long aux_bits;  // scratch max (face divergence)
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -36,6 +37,15 @@ struct mhd_ctx {
   void* Ua;              // U^n (and U^{n+1}, in place)
   void* Ub;              // U1 / staging
   void* Uc;              // U2 of SSP-RK3 (rk_order 3), else null
+  // constrained transport (cfg.divb == MHD_DIVB_CT), else null: the face
+  // fields belonging to Ua / Ub / Uc, the CT buffer of the stage kernels and
+  // the edge fields
+  void* fa;
+  void* fb;
+  void* fc;
+  void* ctf;
+  void* edge;
+  bool faces_set;
   mhd::Scalars* scal;
   double* partials;
   void* adj;             // adjoint scratch (MHD_FLAG_ADJOINT)

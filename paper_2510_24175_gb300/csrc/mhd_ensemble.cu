@@ -174,7 +174,7 @@ static int ens_validate(const mhd_config* cfgs, int nbox) {
     if (mhd_workspace_bytes(&cfgs[b], &bytes) != MHD_OK) return MHD_ERR_INVALID;
     if (cfgs[b].precision != MHD_FP32 || cfgs[b].n[1] < 2 || cfgs[b].n[2] < 2 ||
         (cfgs[b].flags & MHD_FLAG_ADJOINT) || cfgs[b].rk_order != 2 ||
-        cfgs[b].limiter == MHD_LIM_WENOZ)
+        cfgs[b].limiter == MHD_LIM_WENOZ || cfgs[b].divb != MHD_DIVB_GLM)
       return MHD_ERR_INVALID;
   }
   return MHD_OK;

@@ -30,11 +30,35 @@ Phys<T> make_phys(const Grid& g);
 // Stage kernel (mhd_stage_f64.cu / mhd_stage_f32.cu).  stage 1: first stage;
 // 2: last stage (combination with a_n, a_w + damping + wave-speed
 // reduction); 3: SSP-RK3 middle stage (combination only).
+// Constrained transport (bw, ctf non-null; 3-D): bw = the input's face field
+// (three planes), ctf = the kCtPlanes-plane CT buffer.
 template <class T>
 cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T* uout,
                          const StepScalars* sc, unsigned long long* lam_bits,
                          unsigned long long* floor_cnt, cudaStream_t stream,
-                         double a_n = 0.5, double a_w = 0.5);
+                         double a_n = 0.5, double a_w = 0.5, const T* const* bw = nullptr,
+                         T* ctf = nullptr);
+
+// Constrained-transport kernels (mhd_ct.cu); face / edge arrays are three
+// planes of ncell values, b_d on each cell's lower d-face.
+template <class T>
+cudaError_t launch_ct_edges(const Grid& g, const T* ctf, T* edge, cudaStream_t s);
+// first: bout = bw - dt curl E; else bout = a_n bn + a_w (bw - dt curl E).
+template <class T>
+cudaError_t launch_ct_faces(const Grid& g, bool first, const T* edge, const T* bw, const T* bn,
+                            T* bout, const StepScalars* sc, double a_n, double a_w,
+                            cudaStream_t s);
+// U's cell-centred B := face means; last: also the max wave speed into lam_bits.
+template <class T>
+cudaError_t launch_ct_cells(const Grid& g, bool last, const T* b, T* U,
+                            unsigned long long* lam_bits, unsigned long long* floor_cnt,
+                            cudaStream_t s);
+// U's cell-centred B := face means with the pressure kept (after a new face field).
+template <class T>
+cudaError_t launch_ct_set_cells(const Grid& g, const T* b, T* U, cudaStream_t s);
+template <class T>
+cudaError_t launch_ct_divb(const Grid& g, const T* b, unsigned long long* out_bits,
+                           cudaStream_t s);
 
 // Shared-memory bytes and threads of the stage kernel for this grid.
 template <class T>

@@ -54,7 +54,70 @@ struct StageParams {
   const StepScalars* sc;
   unsigned long long* lam_bits;   // stage 2: max wave speed as FP64 bits
   unsigned long long* floor_cnt;  // [2] floor activations
+  // constrained transport (kernels instantiated with CT = true)
+  const T* bw[3];  // the stage input's face field: b_d on each cell's lower d-face
+  T* ctf;          // kCtPlanes planes of ncell values (layout below)
 };
+
+// Planes of the constrained-transport buffer written by a CT stage kernel,
+// per cell: the electric field E = -v x B on the cell's lower x, y and z
+// faces (the two components after the face normal in cyclic order, from the
+// face flux: on a d-face E_{d+1} = F[B_{d+2}] and E_{d+2} = -F[B_{d+1}]), the
+// mass flux through each of those faces (set to zero when
+// |F_rho| <= delta c_h rho, delta = 1e-12 in FP64 and 1e-4 in FP32, so that
+// round-off cannot pick an upwind side), and the cell-centred E.
+enum : int {
+  kCtXEy = 0, kCtXEz, kCtXFm, kCtYEz, kCtYEx, kCtYFm, kCtZEx, kCtZEy, kCtZFm,
+  kCtEcx, kCtEcy, kCtEcz, kCtPlanes
+};
+
+template <class T>
+__device__ __forceinline__ T ct_mass_flux(T f, T rho, T ch) {
+  const T thr = T(sizeof(T) == 8 ? 1e-12 : 1e-4) * ch * rho;
+  return tabs(f) > thr ? f : T(0);
+}
+
+// Constrained-transport data of the cell a column owner updates: the
+// cell-centred E and rho (read in phase C, before the next plane's loads may
+// reuse the ring slot) and the z flux through the cell's lower face.
+template <class T>
+struct CtCell {
+  T ex, ey, ez, rho;
+  T fz_bx, fz_by, fz_rho;
+  __device__ __forceinline__ void from_prims(const T* v, int st) {
+    const T vx = v[kVX * st], vy = v[kVY * st], vz = v[kVZ * st];
+    const T bx = v[kBX * st], by = v[kBY * st], bz = v[kBZ * st];
+    ex = vz * by - vy * bz;
+    ey = vx * bz - vz * bx;
+    ez = vy * bx - vx * by;
+    rho = v[kRHO * st];
+  }
+  // fx / fy: the x and y fluxes of the cell's lower faces (variables sx / sy
+  // apart)
+  __device__ __forceinline__ void write(T* ctf, long long sv, long long off, const T* fx,
+                                        int sx, const T* fy, int sy, T ch) const {
+    ctf[kCtXEy * sv + off] = fx[kBZ * sx];
+    ctf[kCtXEz * sv + off] = -fx[kBY * sx];
+    ctf[kCtXFm * sv + off] = ct_mass_flux(fx[kRHO * sx], rho, ch);
+    ctf[kCtYEz * sv + off] = fy[kBX * sy];
+    ctf[kCtYEx * sv + off] = -fy[kBZ * sy];
+    ctf[kCtYFm * sv + off] = ct_mass_flux(fy[kRHO * sy], rho, ch);
+    ctf[kCtZEx * sv + off] = fz_by;
+    ctf[kCtZEy * sv + off] = -fz_bx;
+    ctf[kCtZFm * sv + off] = ct_mass_flux(fz_rho, rho, ch);
+    ctf[kCtEcx * sv + off] = ex;
+    ctf[kCtEcy * sv + off] = ey;
+    ctf[kCtEcz * sv + off] = ez;
+  }
+};
+
+// Constrained transport: both sides of a d-face carry the staggered normal
+// field and psi = 0 (the GLM interface step is then the identity).
+template <class T>
+__device__ __forceinline__ void ct_face_field(T vl[kNV], T vr[kNV], int d, T bn) {
+  vl[kBX + d] = vr[kBX + d] = bn;
+  vl[kPSI] = vr[kPSI] = T(0);
+}
 
 // Remaps a possibly out-of-range index (>= -2) into [0, n): periodic wraps,
 // outflow clamps.  Indices beyond n+1 only occur in the unused part of a
@@ -123,7 +186,11 @@ __device__ __forceinline__ void cell_slopes(const T* m, int sm, const T* c, int 
 
 // One tile (bx, by, bz) of one RK stage; called by every thread of a CTA of
 // NW warps.  smem_raw: TileGeom::WORDS elements of T; wmax: NW doubles.
-template <class T, int TY, int NW, int STAGE, bool ZACT>
+// CT (constrained transport, 3-D only): face-normal fields from p.bw, only
+// rho, m and E are updated (psi is written as 0; the magnetic field is left to
+// the face update), the face / cell electric fields go to p.ctf, and the last
+// stage has no damping and no wave-speed reduction (done after the face update).
+template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT = false>
 __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepScalars& sc,
                                            int bx, int by, int bz, unsigned char* smem_raw,
                                            double* wmax) {
@@ -212,6 +279,15 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
     *st = G::NINT;
     return cur + r * TX + c;
   };
+  static_assert(!CT || ZACT, "constrained transport is 3-D only");
+  // staggered normal field on the lower d-face of tile cell (r, c) of plane zz
+  auto bface = [&](int d, int zz, int r, int c) -> T {
+    const int gz = remap(zz, nz, p.bc_lo[2], p.bc_hi[2]);
+    const int gx = remap(x0 + c, nx, p.bc_lo[0], p.bc_hi[0]);
+    const int gy = remap(y0 + r, ny, p.bc_lo[1], p.bc_hi[1]);
+    return p.bw[d][(long long)gz * p.sz + (long long)gy * p.sy + gx];
+  };
+  CtCell<T> ctc;
 
   if constexpr (ZACT) {
     // prologue: z face state of cell z0-1 and z flux at face z0-1/2
@@ -243,6 +319,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
         M[k] = v - T(0.5) * sig[k];
         zP[k * G::NINT + oidx] = v + T(0.5) * sig[k];
       }
+      if constexpr (CT) ct_face_field(Pprev, M, 2, bface(2, z0, orow, ocol));
       glm_hlld_flux<2>(Pprev, M, ch, half_chi, ph, F);
 #pragma unroll
       for (int k = 0; k < kNV; ++k) zF[k * G::NINT + oidx] = F[k];
@@ -323,6 +400,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
           vl[q] = a[q * sa] + T(0.5) * ga[q * G::SXN];
           vr[q] = b[q * sb] - T(0.5) * gb[q * G::SXN];
         }
+        if constexpr (CT) ct_face_field(vl, vr, 0, bface(0, k, r, fi));
         dir = 0;
         out = Fx + r * (TX + 1) + fi;
         os = G::FXN;
@@ -339,6 +417,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
           vl[q] = a[q * sa] + T(0.5) * ga[q * G::SYN];
           vr[q] = b[q * sb] - T(0.5) * gb[q * G::SYN];
         }
+        if constexpr (CT) ct_face_field(vl, vr, 1, bface(1, k, fj, c));
         dir = 1;
         out = Fy + j;
         os = G::FYN;
@@ -360,6 +439,13 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
         for (int q = 0; q < kNV; ++q) {
           vl[q] = zP[q * G::NINT + oidx];
           vr[q] = c[q * G::NINT] - T(0.5) * zS[q * G::NINT + oidx];
+        }
+        if constexpr (CT) {
+          ct_face_field(vl, vr, 2, bface(2, k + 1, orow, ocol));
+          ctc.from_prims(cur + oidx, G::NINT);
+          ctc.fz_bx = zF[kBX * G::NINT + oidx];
+          ctc.fz_by = zF[kBY * G::NINT + oidx];
+          ctc.fz_rho = zF[kRHO * G::NINT + oidx];
         }
         glm_hlld_flux<2>(vl, vr, ch, half_chi, ph, F);
 #pragma unroll
@@ -395,10 +481,18 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
             unew[q] = p.a_n * p.un[q * p.sv + off] + p.a_w * s1;
           }
         }
-        if constexpr (STAGE == 2) unew[kPSI] *= damp;
+        if constexpr (CT) {
 #pragma unroll
-        for (int q = 0; q < kNV; ++q) p.uout[q * p.sv + off] = unew[q];
-        if constexpr (STAGE == 2) {
+          for (int q = 0; q < kNV; ++q)
+            if (q != kBX && q != kBY && q != kBZ) p.uout[q * p.sv + off] = q == kPSI ? T(0) : unew[q];
+          ctc.write(p.ctf, p.sv, off, Fx + orow * (TX + 1) + ocol, G::FXN,
+                    Fy + orow * TX + ocol, G::FYN, ch);
+        } else {
+          if constexpr (STAGE == 2) unew[kPSI] *= damp;
+#pragma unroll
+          for (int q = 0; q < kNV; ++q) p.uout[q * p.sv + off] = unew[q];
+        }
+        if constexpr (STAGE == 2 && !CT) {
           const int ndim = 1 + (G::GY > 0) + (ZACT ? 1 : 0);
           const T s = cell_max_speed(unew, ph, ndim, flags);
           lam = nan_max(lam, s);
@@ -407,7 +501,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
     }
   }
 
-  if constexpr (STAGE == 2) {
+  if constexpr (STAGE == 2 && !CT) {
     // block max of the wave speed -> one FP64-bit atomicMax per CTA
     double l = (double)lam;
 #pragma unroll
@@ -434,12 +528,13 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
   __syncthreads();  // the CTA may start another tile on the same shared memory
 }
 
-template <class T, int TY, int NW, int STAGE, bool ZACT>
+template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT>
 __global__ void __launch_bounds__(NW * 32, 1) rk_stage_kernel(const StageParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double wmax[NW];
   const StepScalars sc = *p.sc;
-  stage_tile<T, TY, NW, STAGE, ZACT>(p, sc, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw, wmax);
+  stage_tile<T, TY, NW, STAGE, ZACT, CT>(p, sc, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw,
+                                         wmax);
 }
 
 }  // namespace mhd

@@ -4,6 +4,7 @@
 namespace mhd {
 template cudaError_t launch_stage<float>(const Grid&, int, const float*, const float*, float*,
                                          const StepScalars*, unsigned long long*,
-                                         unsigned long long*, cudaStream_t, double, double);
+                                         unsigned long long*, cudaStream_t, double, double,
+                                         const float* const*, float*);
 template void stage_shape<float>(const Grid&, size_t*, int*, int*);
 }  // namespace mhd

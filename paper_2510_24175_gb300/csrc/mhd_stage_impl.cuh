@@ -18,11 +18,11 @@ struct StageShape3D {
   static constexpr int NW = sizeof(T) == 8 ? 13 : 8;
 };
 
-template <class T, int TY, int NW, int STAGE, bool ZACT>
+template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT = false>
 static cudaError_t launch_one(const StageParams<T>& p, dim3 grid, cudaStream_t s) {
   using G = TileGeom<TY, ZACT>;
   const size_t smem = (size_t)G::WORDS * sizeof(T);
-  auto kern = rk_stage_kernel<T, TY, NW, STAGE, ZACT>;
+  auto kern = rk_stage_kernel<T, TY, NW, STAGE, ZACT, CT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -30,11 +30,11 @@ static cudaError_t launch_one(const StageParams<T>& p, dim3 grid, cudaStream_t s
   return cudaGetLastError();
 }
 
-template <class T, int TY, int NW, int STAGE, bool ZACT>
+template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT = false>
 static cudaError_t launch_weno(const StageParams<T>& p, dim3 grid, cudaStream_t s) {
   using G = WenoGeom<TY, ZACT>;
   const size_t smem = (size_t)G::WORDS * sizeof(T);
-  auto kern = rk_stage_weno_kernel<T, TY, NW, STAGE, ZACT>;
+  auto kern = rk_stage_weno_kernel<T, TY, NW, STAGE, ZACT, CT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -82,7 +82,7 @@ template <class T>
 cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T* uout,
                          const StepScalars* sc, unsigned long long* lam_bits,
                          unsigned long long* floor_cnt, cudaStream_t stream, double a_n,
-                         double a_w) {
+                         double a_w, const T* const* bw, T* ctf) {
   StageParams<T> p;
   p.a_n = T(a_n);
   p.a_w = T(a_w);
@@ -103,6 +103,23 @@ cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T*
   p.sc = sc;
   p.lam_bits = lam_bits;
   p.floor_cnt = floor_cnt;
+  for (int d = 0; d < 3; ++d) p.bw[d] = bw ? bw[d] : nullptr;
+  p.ctf = ctf;
+  if (ctf) {
+    // constrained transport: 3-D grids only (checked when the context is made)
+    if (g.ndim != 3 || !bw) return cudaErrorInvalidValue;
+    if (g.limiter == kLimWenoz) {
+      dim3 grid((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, (g.n[2] + p.tz - 1) / p.tz);
+      if (stage == 1) return launch_weno<T, 4, 8, 1, true, true>(p, grid, stream);
+      if (stage == 2) return launch_weno<T, 4, 8, 2, true, true>(p, grid, stream);
+      return launch_weno<T, 4, 8, 3, true, true>(p, grid, stream);
+    }
+    using S = StageShape3D<T>;
+    dim3 grid((g.n[0] + 31) / 32, (g.n[1] + S::TY - 1) / S::TY, (g.n[2] + p.tz - 1) / p.tz);
+    if (stage == 1) return launch_one<T, S::TY, S::NW, 1, true, true>(p, grid, stream);
+    if (stage == 2) return launch_one<T, S::TY, S::NW, 2, true, true>(p, grid, stream);
+    return launch_one<T, S::TY, S::NW, 3, true, true>(p, grid, stream);
+  }
   if (g.limiter == kLimWenoz) {
     if (g.ndim == 3) {
       dim3 grid((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, (g.n[2] + p.tz - 1) / p.tz);

@@ -128,7 +128,8 @@ struct WenoGeom {
   static constexpr int ITEMS = IT_X + IT_Y + IT_XE;
 };
 
-template <class T, int TY, int NW, int STAGE, bool ZACT>
+// CT: constrained transport, as in stage_tile() (mhd_stage.cuh).
+template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT>
 __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StageParams<T> p) {
   using G = WenoGeom<TY, ZACT>;
   constexpr int NT = NW * 32;
@@ -213,6 +214,15 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
     *st = G::NINT;
     return cur + r * TX + c;
   };
+  static_assert(!CT || ZACT, "constrained transport is 3-D only");
+  // staggered normal field on the lower d-face of tile cell (r, c) of plane zz
+  auto bface = [&](int d, int zz, int r, int c) -> T {
+    const int gz = remap3(zz, nz, p.bc_lo[2], p.bc_hi[2]);
+    const int gx = remap3(x0 + c, nx, p.bc_lo[0], p.bc_hi[0]);
+    const int gy = remap3(y0 + r, ny, p.bc_lo[1], p.bc_hi[1]);
+    return p.bw[d][(long long)gz * p.sz + (long long)gy * p.sy + gx];
+  };
+  CtCell<T> ctc;
   // face values of the owned column's cell in plane zc (planes zc-2..zc+2)
   auto z_cell = [&](int zc, T M[kNV], T P[kNV]) {
     const T* c[5];
@@ -242,6 +252,7 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
     if (owner) {
       T M[kNV], P[kNV], F[kNV];
       z_cell(z0, M, P);
+      if constexpr (CT) ct_face_field(Pprev, M, 2, bface(2, z0, orow, ocol));
       glm_hlld_flux<2>(Pprev, M, ch, half_chi, ph, F);
 #pragma unroll
       for (int k = 0; k < kNV; ++k) {
@@ -324,6 +335,7 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
           vl[q] = xP[q * G::SXN + ia];
           vr[q] = xM[q * G::SXN + ia + 1];
         }
+        if constexpr (CT) ct_face_field(vl, vr, 0, bface(0, k, r, fi));
         out = Fx + r * (TX + 1) + fi;
         os = G::FXN;
       } else {
@@ -335,6 +347,7 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
           vl[q] = yP[q * G::SYN + ia];
           vr[q] = yM[q * G::SYN + ia + TX];
         }
+        if constexpr (CT) ct_face_field(vl, vr, 1, bface(1, k, fj, c));
         out = Fy + j;
         os = G::FYN;
       }
@@ -353,6 +366,13 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
         for (int q = 0; q < kNV; ++q) {
           vl[q] = zP[q * G::NINT + oidx];
           vr[q] = zM[q * G::NINT + oidx];
+        }
+        if constexpr (CT) {
+          ct_face_field(vl, vr, 2, bface(2, k + 1, orow, ocol));
+          ctc.from_prims(cur + oidx, G::NINT);
+          ctc.fz_bx = zF[kBX * G::NINT + oidx];
+          ctc.fz_by = zF[kBY * G::NINT + oidx];
+          ctc.fz_rho = zF[kRHO * G::NINT + oidx];
         }
         glm_hlld_flux<2>(vl, vr, ch, half_chi, ph, F);
 #pragma unroll
@@ -388,10 +408,18 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
             unew[q] = p.a_n * p.un[q * p.sv + off] + p.a_w * s1;
           }
         }
-        if constexpr (STAGE == 2) unew[kPSI] *= damp;
+        if constexpr (CT) {
 #pragma unroll
-        for (int q = 0; q < kNV; ++q) p.uout[q * p.sv + off] = unew[q];
-        if constexpr (STAGE == 2) {
+          for (int q = 0; q < kNV; ++q)
+            if (q != kBX && q != kBY && q != kBZ) p.uout[q * p.sv + off] = q == kPSI ? T(0) : unew[q];
+          ctc.write(p.ctf, p.sv, off, Fx + orow * (TX + 1) + ocol, G::FXN,
+                    Fy + orow * TX + ocol, G::FYN, ch);
+        } else {
+          if constexpr (STAGE == 2) unew[kPSI] *= damp;
+#pragma unroll
+          for (int q = 0; q < kNV; ++q) p.uout[q * p.sv + off] = unew[q];
+        }
+        if constexpr (STAGE == 2 && !CT) {
           const int ndim = 1 + (G::GY > 0) + (ZACT ? 1 : 0);
           lam = nan_max(lam, cell_max_speed(unew, ph, ndim, flags));
         }
@@ -399,7 +427,7 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
     }
   }
 
-  if constexpr (STAGE == 2) {
+  if constexpr (STAGE == 2 && !CT) {
     double l = (double)lam;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) l = nan_max(l, __shfl_xor_sync(0xffffffffu, l, o));

@@ -29,6 +29,8 @@ def rel_l1(a: np.ndarray, b: np.ndarray, floor: float = 1e-3) -> np.ndarray:
 def oracle_run(pb: Problem, nsteps: int, t_end: float = 0.0):
     g = grid_of(pb)
     U0 = orc.prim_to_cons(pb.prim(), pb.gamma)
+    if getattr(pb, "divb", 0) == 1:
+        return orc.ct_run(U0, pb.faces(), g, nsteps, t_end=t_end)
     return orc.run(U0, g, nsteps, t_end=t_end)
 
 
@@ -40,6 +42,8 @@ def gpu_run(pb: Problem, nsteps: int, precision=None, record=False):
     cfg = m.Config.from_problem(pb, precision=precision)
     s = m.MHD(cfg)
     s.set_state(torch.from_numpy(pb.prim()).cuda(), kind=m.MHD_PRIM)
+    if getattr(pb, "divb", 0) == m.MHD_DIVB_CT:
+        s.set_face_field(torch.from_numpy(pb.faces()).cuda())
     hist = []
     for _ in range(nsteps):
         s.step()
