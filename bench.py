@@ -353,29 +353,39 @@ def main():
         del ss
         torch.cuda.empty_cache()
 
-    # ---- the paper's own scheme: WENO-Z + SSP-RK3 (+ GLM), OT 256^3 ----------
+    # ---- the paper's own schemes, OT 256^3: WENO-Z + SSP-RK3 with GLM ------
+    # ---- (its strong-scaling runs) or constrained transport (weak scaling) --
     paper_scheme = None
     if not args.no_paper_scheme:
         paper_scheme = {}
         Kp = max(3, min(K, 5))
-        for prec, tag in ((m.MHD_FP64, "fp64"), (m.MHD_FP32, "fp32")):
-            pw = inputs.orszag_tang_3d(args.n)
-            pw.limiter, pw.rk_order = m.MHD_LIM_WENOZ, 3
-            sw = m.MHD(m.Config.from_problem(pw, precision=prec))
-            sw.set_state(torch.from_numpy(pw.prim()).cuda(), kind=m.MHD_PRIM)
-            for _ in range(W):
-                sw.step()
-            sw.step_info()
-            msw, profw = timed_steps(sw, torch, Kp, dist, world)
-            sw.step_info()
-            paper_scheme[tag] = {
-                "workload": f"orszag_tang_3d_{args.n}^3_wenoz_rk3_{tag}",
-                "value": world * pw.ncell * Kp / (msw * 1e-3), "unit": "zone-updates/s",
-                "steps": Kp, "ms_per_step": msw / Kp,
-                "kernels": {k: {"launches": c, "total_ms": t} for k, (c, t) in profw.items()}}
-            launches += sum(c for c, _ in profw.values())
-            del sw
-            torch.cuda.empty_cache()
+        for divb, dtag in ((m.MHD_DIVB_GLM, "glm"), (m.MHD_DIVB_CT, "ct")):
+            for prec, tag in ((m.MHD_FP64, "fp64"), (m.MHD_FP32, "fp32")):
+                pw = inputs.orszag_tang_3d(args.n)
+                pw.limiter, pw.rk_order, pw.divb = m.MHD_LIM_WENOZ, 3, divb
+                sw = m.MHD(m.Config.from_problem(pw, precision=prec))
+                sw.set_state(torch.from_numpy(pw.prim()).cuda(), kind=m.MHD_PRIM)
+                if divb == m.MHD_DIVB_CT:
+                    sw.set_face_field(torch.from_numpy(pw.faces()).cuda())
+                for _ in range(W):
+                    sw.step()
+                sw.step_info()
+                msw, profw = timed_steps(sw, torch, Kp, dist, world)
+                sw.step_info()
+                key = tag if divb == m.MHD_DIVB_GLM else f"ct_{tag}"
+                paper_scheme[key] = {
+                    "workload": f"orszag_tang_3d_{args.n}^3_wenoz_rk3_{dtag}_{tag}",
+                    "value": world * pw.ncell * Kp / (msw * 1e-3), "unit": "zone-updates/s",
+                    "steps": Kp, "ms_per_step": msw / Kp,
+                    "kernels": {k: {"launches": c, "total_ms": t}
+                                for k, (c, t) in profw.items() if c}}
+                if divb == m.MHD_DIVB_CT:
+                    paper_scheme[key]["divb_max_after"] = sw.divb_max()
+                launches += sum(c for c, _ in profw.values())
+                if divb == m.MHD_DIVB_CT:  # edge, face and cell kernels per stage record
+                    launches += 2 * profw["ct"][0]
+                del sw
+                torch.cuda.empty_cache()
 
     # ---- adjoint / forward step-time ratio: 2-D Orszag-Tang 512^2 FP64 ------
     adjoint = None
