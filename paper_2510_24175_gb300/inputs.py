@@ -272,17 +272,20 @@ def _line_integral(comp_modes, c: int, mid, h: float):
     return out
 
 
-def _potential_faces(pb: Problem) -> np.ndarray:
+def _potential_faces(pb: Problem, A=None, mean=None) -> np.ndarray:
     """Face averages of B = B_mean + curl A, each from Stokes' theorem as the
     exact circulation of A around the face divided by its area, so the
-    discrete divergence vanishes to round-off."""
+    discrete divergence vanishes to round-off.  A: per component a list of
+    (integer k, amplitude, phase) modes of sin(2 pi k.x + phase) (default: the
+    seeded smooth potential)."""
     nx, ny, nz = pb.n
     dx, dy, dz = pb.dx
     xf = (np.arange(nx) * dx)[None, None, :]
     yf = (np.arange(ny) * dy)[None, :, None]
     zf = (np.arange(nz) * dz)[:, None, None]
     xc, yc, zc = xf + 0.5 * dx, yf + 0.5 * dy, zf + 0.5 * dz
-    A = _potential_modes(pb)
+    if A is None:
+        A = _potential_modes(pb)
     shape = (nz, ny, nx)
     b = np.zeros((3,) + shape)
     # x-face at x = xf: circulation in the (y, z) plane
@@ -300,7 +303,9 @@ def _potential_faces(pb: Problem) -> np.ndarray:
              - _line_integral(A[1], 1, (xf, yc, zf), dy))
             - (_line_integral(A[0], 0, (xc, yf + dy, zf), dx)
                - _line_integral(A[0], 0, (xc, yf, zf), dx))) / (dx * dy)
-    b += np.asarray(pb.params.get("B_mean", (0.3, -0.2, 0.1)))[:, None, None, None]
+    if mean is None:
+        mean = pb.params.get("B_mean", (0.3, -0.2, 0.1))
+    b += np.asarray(mean, dtype=np.float64)[:, None, None, None]
     return b
 
 
@@ -359,6 +364,66 @@ def _field_loop_faces(pb: Problem) -> np.ndarray:
     return b
 
 
+def _cpa_geometry(pb: Problem):
+    """Wave vector (integer multiples of 2 pi on [0,1]^3), unit vectors of the
+    circularly polarised Alfven wave, and its parameters."""
+    kint = np.asarray(pb.params.get("k", (1, 1, 1)), dtype=np.float64)
+    khat = kint / np.linalg.norm(kint)
+    # e1: a unit vector normal to k (in the plane of k and the axis least
+    # aligned with it); e2 = k x e1
+    axis = np.zeros(3)
+    axis[int(np.argmin(np.abs(khat)))] = 1.0
+    e1 = axis - khat * (axis @ khat)
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(khat, e1)
+    amp = pb.params.get("amp", 0.1)
+    bpar = pb.params.get("B0", 1.0)
+    rho0 = pb.params.get("rho0", 1.0)
+    return kint, khat, e1, e2, amp, bpar, rho0
+
+
+def _cpa(pb: Problem) -> np.ndarray:
+    """Circularly polarised Alfven wave (the paper's second gPLUTO test, an
+    exact nonlinear solution; set-up of Toth 2000): uniform rho and p,
+    B = B0 k + A (sin phi e1 + cos phi e2), v = -(B - B0 k)/sqrt(rho), phase
+    phi = 2 pi k.x - omega t travelling along k at v_A = B0/sqrt(rho).  The
+    magnetic pressure is uniform, so the wave keeps its shape.  With GLM the
+    cell B is sampled at centres; the CT face field (``faces()``) holds exact
+    face averages from the vector potential and the cell B is their mean."""
+    kint, khat, e1, e2, amp, bpar, rho0 = _cpa_geometry(pb)
+    V = _empty(pb)
+    x, y, z = pb.centres()
+    t = pb.params.get("t", 0.0)
+    vA = bpar / math.sqrt(rho0)
+    ph = 2.0 * math.pi * (kint[0] * x + kint[1] * y + kint[2] * z
+                          - np.linalg.norm(kint) * vA * t)
+    sn = np.broadcast_to(np.sin(ph), V[0].shape)
+    cs = np.broadcast_to(np.cos(ph), V[0].shape)
+    V[RHO] = rho0
+    V[PRS] = pb.params.get("p0", 0.1)
+    for c in range(3):
+        dB = amp * (sn * e1[c] + cs * e2[c])
+        V[BX + c] = bpar * khat[c] + dB
+        V[VX + c] = -dB / math.sqrt(rho0)
+    if pb.divb == DIVB_CT:
+        V[BX:BZ + 1] = _cell_mean(_cpa_faces(pb))
+    return V
+
+
+def _cpa_faces(pb: Problem) -> np.ndarray:
+    """Exact face averages of the CPA field: dB = curl a with
+    a = (A / |2 pi k|) (sin phi e1 + cos phi e2), plus the uniform B0 k."""
+    kint, khat, e1, e2, amp, bpar, _ = _cpa_geometry(pb)
+    t = pb.params.get("t", 0.0)
+    vA = bpar / math.sqrt(pb.params.get("rho0", 1.0))
+    kn = np.linalg.norm(kint)
+    ph0 = -2.0 * math.pi * kn * vA * t
+    scale = amp / (2.0 * math.pi * kn)
+    A = [[(kint, scale * e1[c], ph0), (kint, scale * e2[c], ph0 + 0.5 * math.pi)]
+         for c in range(3)]
+    return _potential_faces(pb, A=A, mean=bpar * khat)
+
+
 def _alfven_oblique(pb: Problem) -> np.ndarray:
     """Linear Alfven wave travelling along (1, 1, 0)/sqrt 2 with wave vector
     2 pi (1, 1, 0): background B0 = |B0| (1, 1, 0)/sqrt 2, z-polarised
@@ -392,6 +457,7 @@ _GENERATORS = {
     "shock_pair": _shock_pair,
     "field_loop": _field_loop,
     "alfven_oblique": _alfven_oblique,
+    "cpa": _cpa,
 }
 
 _FACE_GENERATORS = {
@@ -401,6 +467,7 @@ _FACE_GENERATORS = {
     "alfven_oblique": _faces_from_cells,
     "ct_random": _potential_faces,
     "field_loop": _field_loop_faces,
+    "cpa": _cpa_faces,
 }
 
 
@@ -454,6 +521,15 @@ def field_loop(n: int, nz: int = 2, v=(1.0, 0.5, 0.0)) -> Problem:
     """Weak field loop advected diagonally (periodic [0,1]^2 x nz planes)."""
     return Problem("field_loop", (n, n, nz), limiter=LIM_MC, divb=DIVB_CT,
                    params={"v": tuple(v)})
+
+
+def cpa_wave(n: int, k=(1, 1, 1), divb: int = DIVB_GLM, limiter: int = LIM_MC,
+             rk_order: int = 2) -> Problem:
+    """Circularly polarised Alfven wave on a periodic n^3 grid, wave vector
+    2 pi k, amplitude 0.1, B0 = 1, rho = 1, p = 0.1, gamma = 5/3; one period
+    is 1 / |k|."""
+    return Problem("cpa", (n, n, n), limiter=limiter, rk_order=rk_order, divb=divb,
+                   params={"k": tuple(k)})
 
 
 def alfven_oblique(n: int, nz: int = 2, amp: float = 1e-6) -> Problem:

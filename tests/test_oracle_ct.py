@@ -268,3 +268,36 @@ def test_stage_is_the_composition_of_the_pinned_pieces():
     cell = np.stack([0.5 * (bref[d] + sh(bref[d], d, 1)) for d in range(3)])
     assert rel(out[4:7], cell) <= 1e-13
     assert np.abs(out[8]).max() == 0.0
+
+
+@pytest.mark.parametrize("divb", [0, 1])
+def test_cpa_wave_is_an_exact_solution_and_converges(divb):
+    """The circularly polarised Alfven wave (the paper's second test problem):
+    its closed form at time t is the initial state translated along k; after
+    one period both the GLM and the CT scheme return to it with an error that
+    falls at (about) second order."""
+    errs = []
+    for n in (8, 16):
+        pb = inputs.cpa_wave(n, divb=divb)
+        g = grid_of(pb)
+        U = orc.prim_to_cons(pb.prim(), pb.gamma)
+        T = 1.0 / math.sqrt(3.0)
+        if divb:
+            b = pb.faces()
+            assert np.abs(orc.ct_divb(b, g)).max() <= 1e-13 * n
+            r = orc.ct_run(U, b, g, 100000, t_end=T)
+        else:
+            r = orc.run(U, g, 100000, t_end=T)
+        assert abs(r.t - T) < 1e-12 and r.floors == (0, 0)
+        errs.append(np.abs(r.U[4:7] - U[4:7]).mean() / 0.1)
+    assert math.log2(errs[0] / errs[1]) >= 1.6, errs
+    assert errs[1] < 0.07
+    # the closed form: a quarter period later the state is the initial one
+    # shifted by a quarter wavelength along k = (1, 1, 1)
+    pb = inputs.cpa_wave(8, divb=divb)
+    q = inputs.cpa_wave(8, divb=divb)
+    q.params = dict(q.params, t=0.25 / math.sqrt(3.0))
+    # phase 2 pi (x + y + z - sqrt3 t): a quarter period advances the phase
+    # as a shift of 1/4 (2 of 8 cells) along x does
+    shifted = np.roll(pb.prim(), 2, axis=3)
+    assert np.abs(q.prim() - shifted).max() <= 1e-12
