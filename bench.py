@@ -39,9 +39,15 @@ sys.path.insert(0, ROOT)
 # FP64-pipe lane-instructions (DADD, DMUL, DFMA, DSETP, DMNMX, conversions)
 # per cell executed by the FP64 stage kernel, stage 1 and stage 2 (which adds
 # the GLM damping and the next step's wave-speed reduction): ncu
-# smsp__inst_executed_pipe_fp64 x 32 / cells on Orszag-Tang 128^3 (per-cell
-# figures; see profiles/).  They change whenever the kernel does.
-FP64_INST_PER_CELL = {1: 1294.0, 2: 1474.0}
+# smsp__inst_executed_pipe_fp64 x 32 / cells over the timed steps of this
+# bench's Orszag-Tang 256^3 run (profiles/).  They change whenever the kernel
+# does.
+FP64_INST_PER_CELL = {1: 1315.0, 2: 1444.0}
+# DRAM bytes per cell of the stage kernel's launches (ncu dram__bytes_read +
+# dram__bytes_write over the timed steps of this bench's 256^3 FP64 and 512^3
+# FP32 runs, profiles/); reported as the roofline's traffic per launch.  Set
+# to None whenever the kernel changes until they are captured again.
+TRAFFIC_BYTES_PER_CELL = {8: {1: 149.7, 2: 221.6}, 4: {1: 75.6, 2: 111.4}}
 # FP64 pipe peak: 2 lanes/clk/SM (a DFMA probe measured 1.9) x 152 SMs x
 # 2.07 GHz = 629 G lane-instructions/s (1.26 TFLOP/s counting an FMA as 2).
 FP64_PEAK_GINST = 2 * 152 * 2.07
@@ -225,8 +231,10 @@ def roofline_of(prof, ncell, esize, hbm_peak, peak_kind, fp64):
     n2, ms2 = prof["stage2"]
     avg_ms = (ms1 + ms2) / max(n1 + n2, 1)
     bytes_launch = ncell * esize * (WORDS_STAGE[1] + WORDS_STAGE[2]) / 2.0
+    tb = TRAFFIC_BYTES_PER_CELL.get(esize) if TRAFFIC_BYTES_PER_CELL else None
+    traffic = ncell * (tb[1] * n1 + tb[2] * n2) / max(n1 + n2, 1) if tb else None
     hbm = {"bound": "hbm", "achieved": bytes_launch / (avg_ms * 1e-3) / 1e9, "peak": hbm_peak,
-           "unit": "GB/s", "traffic": None, "kernel": "rk_stage_kernel",
+           "unit": "GB/s", "traffic": traffic, "kernel": "rk_stage_kernel",
            "avg_launch_ms": avg_ms, "bytes_per_launch": bytes_launch,
            "peak_source": peak_kind}
     hbm["frac"] = hbm["achieved"] / hbm_peak
@@ -235,7 +243,7 @@ def roofline_of(prof, ncell, esize, hbm_peak, peak_kind, fp64):
     inst = ncell * (FP64_INST_PER_CELL[1] * n1 + FP64_INST_PER_CELL[2] * n2) / max(n1 + n2, 1)
     ach = inst / (avg_ms * 1e-3) / 1e9
     alu = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GINST,
-           "unit": "G FP64-lane-inst/s", "frac": ach / FP64_PEAK_GINST, "traffic": None,
+           "unit": "G FP64-lane-inst/s", "frac": ach / FP64_PEAK_GINST, "traffic": traffic,
            "kernel": "rk_stage_kernel", "avg_launch_ms": avg_ms,
            "fp64_inst_per_cell": FP64_INST_PER_CELL,
            "peak_source": "2 FP64 lanes/clk/SM x 152 SMs x 2.07 GHz (GB300 nominal 1.25 "
