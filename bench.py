@@ -51,6 +51,15 @@ TRAFFIC_BYTES_PER_CELL = {8: {1: 149.7, 2: 221.6}, 4: {1: 75.6, 2: 111.4}}
 # FP64 pipe peak: 2 lanes/clk/SM (a DFMA probe measured 1.9) x 152 SMs x
 # 2.07 GHz = 629 G lane-instructions/s (1.26 TFLOP/s counting an FMA as 2).
 FP64_PEAK_GINST = 2 * 152 * 2.07
+# Warp-instructions per cell of the FP32 stage kernel (ncu smsp__inst_executed
+# / cells, turbulent box 160^3, stage 1 / stage 2; profiles/) and the issue
+# peak they run against: 4 warp-instructions per clock per SM (one per
+# scheduler) x 152 SMs x 2.07 GHz.
+FP32_WARP_INST_PER_CELL = {1: 86.2, 2: 93.7}
+ISSUE_PEAK_GINST = 4 * 152 * 2.07
+# FP64-pipe lane-instructions per cell of the FP64 WENO-Z stage kernel (ncu,
+# Orszag-Tang 128^3; first / middle / last SSP-RK3 stage).
+WENO_FP64_INST_PER_CELL = {"stage1": 3648.0, "stage_mid": 3666.0, "stage2": 3773.0}
 # Algorithmic HBM bytes per cell: stage 1 reads U^n and writes U1 (18 words),
 # stage 2 reads U1 and U^n and writes U^{n+1} (27 words).
 WORDS_STAGE = {1: 18, 2: 27}
@@ -373,8 +382,18 @@ def main():
         ms32, prof32 = timed_steps(s32, torch, K, dist, world)
         s32.step_info()
         hbm32, _ = roofline_of(prof32, N32, 4, hbm_peak, peak_kind, False)
+        n1, t1 = prof32["stage1"]
+        n2, t2 = prof32["stage2"]
+        winst = N32 * (FP32_WARP_INST_PER_CELL[1] * n1 + FP32_WARP_INST_PER_CELL[2] * n2)
+        ach32 = winst / ((t1 + t2) * 1e-3) / 1e9
+        issue32 = {"bound": "alu", "achieved": ach32, "peak": ISSUE_PEAK_GINST,
+                   "unit": "G warp-inst/s", "frac": ach32 / ISSUE_PEAK_GINST,
+                   "kernel": "rk_stage_kernel",
+                   "peak_source": "4 warp-instructions/clk/SM (instruction issue) x 152 SMs x "
+                                  "2.07 GHz; the FP32 kernel is issue-bound (ncu)"}
         fp32 = {"workload": f"turbulent_box_{args.n32}^3_fp32", "value": world * N32 * K / (ms32 * 1e-3),
                 "unit": "zone-updates/s", "ms_per_step": ms32 / K, "roofline": hbm32,
+                "roofline_issue": issue32,
                 "kernels": {k: {"launches": c, "total_ms": t} for k, (c, t) in prof32.items()},
                 "dtype": "f32 (FP64 dt reduction, sums, pressure-floor branch)"}
         launches += sum(c for c, _ in prof32.values())
@@ -427,6 +446,15 @@ def main():
                                 for k, (c, t) in profw.items() if c}}
                 if divb == m.MHD_DIVB_CT:
                     paper_scheme[key]["divb_max_after"] = sw.divb_max()
+                if prec == m.MHD_FP64 and divb == m.MHD_DIVB_GLM:
+                    inst = sum(pw.ncell * WENO_FP64_INST_PER_CELL[c] * profw[c][0]
+                               for c in WENO_FP64_INST_PER_CELL)
+                    ms_k = sum(profw[c][1] for c in WENO_FP64_INST_PER_CELL)
+                    ach = inst / (ms_k * 1e-3) / 1e9
+                    paper_scheme[key]["roofline"] = {
+                        "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GINST,
+                        "unit": "G FP64-lane-inst/s", "frac": ach / FP64_PEAK_GINST,
+                        "kernel": "rk_stage_weno_kernel"}
                 launches += sum(c for c, _ in profw.values())
                 if divb == m.MHD_DIVB_CT:  # edge, face and cell kernels per stage record
                     launches += 2 * profw["ct"][0]
