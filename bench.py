@@ -42,20 +42,20 @@ sys.path.insert(0, ROOT)
 # smsp__inst_executed_pipe_fp64 x 32 / cells over the timed steps of this
 # bench's Orszag-Tang 256^3 run (profiles/).  They change whenever the kernel
 # does.
-FP64_INST_PER_CELL = {1: 1315.0, 2: 1444.0}
+FP64_INST_PER_CELL = {1: 1208.1, 2: 1326.4}
 # DRAM bytes per cell of the stage kernel's launches (ncu dram__bytes_read +
 # dram__bytes_write over the timed steps of this bench's 256^3 FP64 and 512^3
 # FP32 runs, profiles/); reported as the roofline's traffic per launch.  Set
 # to None whenever the kernel changes until they are captured again.
-TRAFFIC_BYTES_PER_CELL = {8: {1: 149.7, 2: 221.6}, 4: {1: 75.6, 2: 111.4}}
+TRAFFIC_BYTES_PER_CELL = {8: {1: 149.5, 2: 221.7}, 4: {1: 75.6, 2: 111.2}}
 # FP64 pipe peak: 2 lanes/clk/SM (a DFMA probe measured 1.9) x 152 SMs x
 # 2.07 GHz = 629 G lane-instructions/s (1.26 TFLOP/s counting an FMA as 2).
 FP64_PEAK_GINST = 2 * 152 * 2.07
 # Warp-instructions per cell of the FP32 stage kernel (ncu smsp__inst_executed
-# / cells, turbulent box 160^3, stage 1 / stage 2; profiles/) and the issue
+# / cells, turbulent box 512^3, stage 1 / stage 2; profiles/) and the issue
 # peak they run against: 4 warp-instructions per clock per SM (one per
 # scheduler) x 152 SMs x 2.07 GHz.
-FP32_WARP_INST_PER_CELL = {1: 86.2, 2: 93.7}
+FP32_WARP_INST_PER_CELL = {1: 82.75, 2: 88.27}
 ISSUE_PEAK_GINST = 4 * 152 * 2.07
 # FP64-pipe lane-instructions per cell of the FP64 WENO-Z stage kernel (ncu,
 # Orszag-Tang 128^3; first / middle / last SSP-RK3 stage).
@@ -345,7 +345,7 @@ def main():
     if not args.no_e2e:
         U_host = torch.empty((9,) + tuple(V0.shape[1:]), dtype=torch.float64, pin_memory=True)
         s.get_state(U_host.numpy())
-        out_host = torch.empty_like(U_host)
+        out_host = torch.empty(U_host.shape, dtype=torch.float64, pin_memory=True)
         Kx = max(3, min(K, 10))
         torch.cuda.synchronize()
         if dist is not None:

@@ -75,9 +75,104 @@ MHD_HD float tmin(float a, float b) { return fminf(a, b); }
 MHD_HD double tmax(double a, double b) { return fmax(a, b); }
 MHD_HD float tmax(float a, float b) { return fmaxf(a, b); }
 
-// max that keeps a NaN once either operand has one (fmax drops NaNs).
-MHD_HD double nan_max(double a, double b) { return (a != a || b > a || b != b) ? (a != a ? a : b) : a; }
+// Bit-pattern helpers (the host build, used only by host-side harnesses,
+// goes through memcpy).
+MHD_HD long long dbits(double x) {
+#ifdef __CUDA_ARCH__
+  return __double_as_longlong(x);
+#else
+  long long b;
+  memcpy(&b, &x, sizeof(b));
+  return b;
+#endif
+}
+MHD_HD double bits2d(long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double(b);
+#else
+  double x;
+  memcpy(&x, &b, sizeof(x));
+  return x;
+#endif
+}
+
+// max that keeps a NaN once either operand has one (fmax drops NaNs).  Its
+// operands are wave speeds or magnitudes: +0, positive, +inf or NaN.  For
+// those, the unsigned order of the FP64 bit patterns is the numeric order
+// with every NaN above +inf, so the device takes the FP64 max on the
+// integer pipe (the FP64 pipe is the bound of the FP64 kernels).
+MHD_HD double nan_max(double a, double b) {
+#ifdef __CUDA_ARCH__
+  const unsigned long long x = (unsigned long long)dbits(a), y = (unsigned long long)dbits(b);
+  return bits2d((long long)(x > y ? x : y));
+#else
+  return (a != a || b > a || b != b) ? (a != a ? a : b) : a;
+#endif
+}
 MHD_HD float nan_max(float a, float b) { return (a != a || b > a || b != b) ? (a != a ? a : b) : a; }
+MHD_HD bool is_nan(double x) {
+  return ((unsigned long long)dbits(x) & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
+}
+MHD_HD bool is_nan(float x) { return x != x; }
+
+// Sign tests and min / max with IEEE results (-0, subnormals, infinities and
+// NaN included: a NaN compares false, and tmin2 / tmax2 return the other
+// operand like fmin / fmax).  FP64 takes them on the integer pipe from the
+// bit patterns: x > 0 exactly when the pattern lies in [1, +inf], x < 0 when
+// it lies in [-0 + 1 ulp, -inf] (sign-magnitude order), and two doubles order
+// like their patterns once the magnitude bits of negative ones are flipped.
+MHD_HD bool gt0(double x) {
+  return (unsigned long long)dbits(x) - 1ull < 0x7ff0000000000000ull;
+}
+MHD_HD bool lt0(double x) {
+  return (unsigned long long)dbits(x) - 0x8000000000000001ull < 0x7ff0000000000000ull;
+}
+MHD_HD bool ge0(double x) {
+  const unsigned long long b = (unsigned long long)dbits(x);
+  return b <= 0x7ff0000000000000ull || b == 0x8000000000000000ull;
+}
+MHD_HD bool gt0(float x) { return x > 0.0f; }
+MHD_HD bool lt0(float x) { return x < 0.0f; }
+MHD_HD bool ge0(float x) { return x >= 0.0f; }
+MHD_HD long long order_key(long long b) { return b ^ ((b >> 63) & 0x7fffffffffffffffll); }
+MHD_HD double tmin2(double a, double b) {
+  const long long x = dbits(a), y = dbits(b);
+  const bool pick_a = is_nan(b) || (!is_nan(a) && order_key(x) <= order_key(y));
+  return pick_a ? a : b;
+}
+MHD_HD double tmax2(double a, double b) {
+  const long long x = dbits(a), y = dbits(b);
+  const bool pick_a = is_nan(b) || (!is_nan(a) && order_key(x) >= order_key(y));
+  return pick_a ? a : b;
+}
+MHD_HD float tmin2(float a, float b) { return fminf(a, b); }
+MHD_HD float tmax2(float a, float b) { return fmaxf(a, b); }
+// |a| < t, IEEE (false when either is NaN)
+MHD_HD bool abs_lt(double a, double t) {
+  const long long x = dbits(a) & 0x7fffffffffffffffll, y = dbits(t);
+  return x < y && y <= 0x7ff0000000000000ll;
+}
+MHD_HD bool abs_lt(float a, float t) { return fabsf(a) < t; }
+// max(x, 0) for the square-root discriminant (fmax(NaN, 0) = 0 as well)
+MHD_HD double pos_part(double x) { return gt0(x) ? x : 0.0; }
+MHD_HD float pos_part(float x) { return fmaxf(x, 0.0f); }
+
+// Exact 2x and x/2 of a non-negative double (or +inf / NaN, which are kept)
+// from its bit pattern: a power-of-two scaling moves the exponent field; a
+// subnormal doubles by a shift, and halving into the subnormal range
+// shifts the significand right with the dropped bit rounded to nearest even
+// (the IEEE results of x + x and 0.5 * x, overflow to +inf included).
+MHD_HD long long twice_bits(long long b) {
+  const long long e = b >> 52;
+  if (e == 0) return b << 1;
+  if (e < 2046) return b + (1ll << 52);
+  return e == 2047 ? b : 0x7ff0000000000000ll;
+}
+MHD_HD long long half_bits(long long b) {
+  const long long e = b >> 52;
+  if (e >= 2) return e == 2047 ? b : b - (1ll << 52);
+  return (b >> 1) + ((b & 1) & ((b >> 1) & 1));
+}
 
 // Pressure floor.  FP64: plain comparison.  FP32: when the FP32 pressure is
 // within the cancellation-dominated range (internal energy below 1e-3 of the
@@ -151,23 +246,35 @@ MHD_HD void prim_to_cons(const T v[kNV], T u[kNV], const Phys<T>& ph) {
   u[kPSI] = v[kPSI];
 }
 
-// Fast magnetosonic speed from 1/rho, gamma p, |B|^2 and B_n^2:
-// c_f^2 = (a + sqrt(a^2 - 4 gamma p B_n^2 / rho^2)) / 2, a = (gamma p + |B|^2)/rho.
-template <class T>
-MHD_HD T fast_speed(T rho_i, T gp, T b2, T bn2) {
-  const T a = (gp + b2) * rho_i;
-  T disc = a * a - T(4) * gp * bn2 * (rho_i * rho_i);
-  disc = tmax(disc, T(0));
-  return tsqrt(T(0.5) * (a + tsqrt(disc)));
+// -4x and x/2 with IEEE results; FP64 moves the exponent field on the
+// integer pipe (twice_bits / half_bits, exact including subnormals and
+// overflow).
+MHD_HD double neg4(double x) {
+  const long long b = dbits(x), sign = b & (long long)0x8000000000000000ull;
+  return bits2d(twice_bits(twice_bits(b ^ sign)) | (sign ^ (long long)0x8000000000000000ull));
 }
+MHD_HD float neg4(float x) { return -4.0f * x; }
+MHD_HD double half_of(double x) {
+  const long long b = dbits(x), sign = b & (long long)0x8000000000000000ull;
+  return bits2d(half_bits(b ^ sign) | sign);
+}
+MHD_HD float half_of(float x) { return 0.5f * x; }
 
-// c_f^2 (see fast_speed).
+// Fast magnetosonic speed squared from 1/rho, gamma p, |B|^2 and B_n^2:
+// with g = gamma p / rho, a = g + |B|^2 / rho and c_an^2 = B_n^2 / rho,
+// c_f^2 = (a + sqrt(a^2 - 4 g c_an^2)) / 2.
 template <class T>
 MHD_HD T fast_speed2(T rho_i, T gp, T b2, T bn2) {
-  const T a = (gp + b2) * rho_i;
-  T disc = a * a - T(4) * gp * bn2 * (rho_i * rho_i);
-  disc = tmax(disc, T(0));
-  return T(0.5) * (a + tsqrt(disc));
+  const T g = gp * rho_i;
+  const T a = b2 * rho_i + g;
+  const T disc = pos_part(a * a + neg4(g * (bn2 * rho_i)));
+  return half_of(a + tsqrt(disc));
+}
+
+// Fast magnetosonic speed (see fast_speed2).
+template <class T>
+MHD_HD T fast_speed(T rho_i, T gp, T b2, T bn2) {
+  return tsqrt(fast_speed2(rho_i, gp, b2, bn2));
 }
 
 // max over active directions of |v_d| + c_f,d for one conservative cell.
@@ -183,29 +290,8 @@ MHD_HD T cell_max_speed(const T u[kNV], const Phys<T>& ph, int ndim,
   if (ndim > 1) lam = nan_max(lam, tabs(v[kVY]) + fast_speed(ri, gp, b2, v[kBY] * v[kBY]));
   if (ndim > 2) lam = nan_max(lam, tabs(v[kVZ]) + fast_speed(ri, gp, b2, v[kBZ] * v[kBZ]));
   // NaN anywhere in the cell (psi included) makes the speed NaN
-  if (!(v[kPSI] == v[kPSI]) || !(lam == lam)) lam = T(NAN);
+  if (is_nan(v[kPSI]) || is_nan(lam)) lam = T(NAN);
   return lam;
-}
-
-// Bit-pattern helpers (the host build, used only by host-side harnesses,
-// goes through memcpy).
-MHD_HD long long dbits(double x) {
-#ifdef __CUDA_ARCH__
-  return __double_as_longlong(x);
-#else
-  long long b;
-  memcpy(&b, &x, sizeof(b));
-  return b;
-#endif
-}
-MHD_HD double bits2d(long long b) {
-#ifdef __CUDA_ARCH__
-  return __longlong_as_double(b);
-#else
-  double x;
-  memcpy(&x, &b, sizeof(x));
-  return x;
-#endif
 }
 
 // Limited slope (van Leer 1977): 0 when the one-sided differences disagree in
@@ -221,9 +307,10 @@ MHD_HD T limited_slope(T dm, T dp, int lim) {
 
 // FP64 specialisation with the same result: the sign and zero tests, |.|,
 // the magnitude comparisons (non-negative doubles order like their bit
-// patterns) and the sign transfer run on the integer pipe; only the additions
-// and the halving use the (scarce) FP64 pipe.  For equal signs
-// |dm + dp| = |dm| + |dp| exactly, so the central slope is (|dm|+|dp|)/2.
+// patterns), the doubling and halving of the MC limiter and the sign
+// transfer run on the integer pipe; only |dm| + |dp| uses the (scarce) FP64
+// pipe.  For equal signs |dm + dp| = |dm| + |dp| exactly, so the central
+// slope is (|dm|+|dp|)/2.
 template <>
 MHD_HD double limited_slope<double>(double dm, double dp, int lim) {
   const long long a = dbits(dm), b = dbits(dp);
@@ -232,9 +319,8 @@ MHD_HD double limited_slope<double>(double dm, double dp, int lim) {
   if (lim == kLimFlat || (a ^ b) < 0 || am == 0 || bm == 0) return 0.0;
   long long mb = am < bm ? am : bm;
   if (lim == kLimMC) {
-    const double mag = bits2d(mb);
-    const long long two = dbits(mag + mag);
-    const long long cen = dbits(0.5 * (bits2d(am) + bits2d(bm)));
+    const long long two = twice_bits(mb);
+    const long long cen = half_bits(dbits(bits2d(am) + bits2d(bm)));
     mb = cen < two ? cen : two;
   }
   return bits2d(mb | (a & ~mask));
@@ -259,10 +345,10 @@ MHD_HD void plm_face_pair(const T* c0, const T* c1, const T* c2,
     vr[k] = q2;
   }
   // zero-slope fallback per cell if a face density or pressure is <= 0
-  const bool ok1 = (vl[kRHO] - T(0.5) * tabs(s1[kRHO]) > T(0)) &&
-                   (vl[kPRS] - T(0.5) * tabs(s1[kPRS]) > T(0));
-  const bool ok2 = (vr[kRHO] - T(0.5) * tabs(s2[kRHO]) > T(0)) &&
-                   (vr[kPRS] - T(0.5) * tabs(s2[kPRS]) > T(0));
+  const bool ok1 = gt0(vl[kRHO] - T(0.5) * tabs(s1[kRHO])) &&
+                   gt0(vl[kPRS] - T(0.5) * tabs(s1[kPRS]));
+  const bool ok2 = gt0(vr[kRHO] - T(0.5) * tabs(s2[kRHO])) &&
+                   gt0(vr[kPRS] - T(0.5) * tabs(s2[kPRS]));
 #pragma unroll
   for (int k = 0; k < kNV; ++k) {
     if (ok1) vl[k] = vl[k] + T(0.5) * s1[k];
@@ -319,9 +405,9 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
   const T cf2R = fast_speed2(rL * qr, ph.gamma * pR, b2R, bx2);
 
   // wave-speed estimates (MK05 Eq. 67), contact speed and total pressure
-  const T cmax = tsqrt(tmax(cf2L, cf2R));
-  const T SL = tmin(uL, uR) - cmax;
-  const T SR = tmax(uL, uR) + cmax;
+  const T cmax = tsqrt(tmax2(cf2L, cf2R));
+  const T SL = tmin2(uL, uR) - cmax;
+  const T SR = tmax2(uL, uR) + cmax;
   const T dL = (SL - uL) * rL, dR = (SR - uR) * rR;
   const T Di = rcp(dR - dL);
   const T SM = (dR * uR - dL * uL - ptR + ptL) * Di;
@@ -332,8 +418,8 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
   // of the two denominators
   const T smL = SL - SM, smR = SR - SM;
   const T denL = dL * smL - bx2, denR = dR * smR - bx2;
-  const bool degL = tabs(denL) < T(1e-8) * pts;
-  const bool degR = tabs(denR) < T(1e-8) * pts;
+  const bool degL = abs_lt(denL, T(1e-8) * pts);
+  const bool degR = abs_lt(denR, T(1e-8) * pts);
   const T dnL = degL ? T(1) : denL, dnR = degR ? T(1) : denR;
   const T ps = smL * smR, pd = dnL * dnR;
   const T q4 = rcp(ps * pd);  // one reciprocal for the four divisors
@@ -374,7 +460,7 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
   const T abx = tabs(bx);
   const T SLs = SM - abx * iqL;
   const T SRs = SM + abx * iqR;
-  const T sg = bx >= T(0) ? T(1) : T(-1);
+  const T sg = ge0(bx) ? T(1) : T(-1);
   const T isum = rcp(sqL + sqR);
   const T vss = (sqL * vsL + sqR * vsR + (bysR - bysL) * sg) * isum;
   const T wss = (sqL * wsL + sqR * wsR + (bzsR - bzsL) * sg) * isum;
@@ -385,9 +471,10 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
   // Fan region: side a = L if (S_L > 0) or (S_R >= 0 and S_M >= 0), else R.
   // F = F_a + c1 (U*_a - U_a) + c2 (U**_a - U*_a) with c1 = S_a unless the
   // interface is supersonic, c2 = S*_a inside the Alfven fan.
-  const bool sup = (SL > T(0)) || (SR < T(0));
-  const bool useL = (SL > T(0)) || (!(SR < T(0)) && SM >= T(0));
-  const bool inner = !sup && (useL ? !(SLs > T(0)) : !(SRs < T(0)));
+  // (sign tests on the integer pipe in FP64: gt0 / lt0 / ge0)
+  const bool sup = gt0(SL) || lt0(SR);
+  const bool useL = gt0(SL) || (!lt0(SR) && ge0(SM));
+  const bool inner = !sup && (useL ? !gt0(SLs) : !lt0(SRs));
   const T r = useL ? rL : rR, u = useL ? uL : uR, v = useL ? vL : vR, w = useL ? wL : wR;
   const T by = useL ? byL : byR, bz = useL ? bzL : bzR, e = useL ? eL : eR;
   const T pt = useL ? ptL : ptR;

@@ -176,8 +176,8 @@ __device__ __forceinline__ void cell_slopes(const T* m, int sm, const T* c, int 
     const T q = c[k * sc];
     sig[k] = limited_slope(q - m[k * sm], p[k * sp] - q, lim);
   }
-  const bool ok = (c[kRHO * sc] - T(0.5) * tabs(sig[kRHO]) > T(0)) &&
-                  (c[kPRS * sc] - T(0.5) * tabs(sig[kPRS]) > T(0));
+  const bool ok = gt0(c[kRHO * sc] - T(0.5) * tabs(sig[kRHO])) &&
+                  gt0(c[kPRS * sc] - T(0.5) * tabs(sig[kPRS]));
   if (!ok) {
 #pragma unroll
     for (int k = 0; k < kNV; ++k) sig[k] = T(0);
@@ -517,7 +517,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
       for (int w = 1; w < NW; ++w)
         m = nan_max(m, wmax[w]);
       unsigned long long bits = (unsigned long long)__double_as_longlong(m);
-      if (m != m) bits = 0x7ff8000000000000ull;
+      if (is_nan(m)) bits = 0x7ff8000000000000ull;
       atomicMax(p.lam_bits, bits);
     }
   }

@@ -1,0 +1,95 @@
+// Host-only check (compiled by tests/test_fp64_bit_helpers.py): the FP64
+// helpers that the kernels evaluate on the integer pipe -- sign tests,
+// min / max, |a| < t, max(x, 0), exact doubling and halving, -4x, x/2,
+// the limited slope -- against the IEEE operations of the host compiler, on random and
+// special doubles (signed zeros, subnormals, extremes, infinities, NaNs).
+// Prints the number of disagreements and exits non-zero if there is any.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <random>
+
+#include "../paper_2510_24175_gb300/csrc/mhd_physics.cuh"
+
+using namespace mhd;
+
+static unsigned long long bits(double x) {
+  unsigned long long b;
+  memcpy(&b, &x, 8);
+  return b;
+}
+static bool same(double a, double b) { return bits(a) == bits(b) || (a != a && b != b); }
+
+// the limited slope written with plain IEEE operations
+static double slope_ref(double dm, double dp, int lim) {
+  if (lim == kLimFlat || !(dm * dp > 0.0)) return 0.0;
+  const double am = fabs(dm), ap = fabs(dp);
+  double mag = am < ap ? am : ap;
+  if (lim == kLimMC) {
+    const double two = mag + mag, cen = 0.5 * (am + ap);
+    mag = cen < two ? cen : two;
+  }
+  return dm > 0.0 ? mag : -mag;
+}
+
+int main() {
+  std::mt19937_64 g(2024);
+  const double sp[] = {0.0, -0.0, 1.0, -1.0, 0.5, 3.0, 4.9e-324, -4.9e-324, 2.2250738585072014e-308,
+                       -2.2250738585072014e-308, 4.450147717014403e-308, 1.1125369292536007e-308,
+                       1.7976931348623157e308, -1.7976931348623157e308, 8.98846567431158e307,
+                       HUGE_VAL, -HUGE_VAL, NAN, -NAN, 1e-300, 1e300};
+  const int nsp = sizeof(sp) / sizeof(sp[0]);
+  auto draw = [&](int k) -> double {
+    double x;
+    if (k % 4 == 0) return sp[g() % nsp];
+    if (k % 4 == 1) {  // any pattern; NaNs quiet (arithmetic never makes a
+      unsigned long long b = g();  // signalling one, and host fmin / fmax
+      if ((b & 0x7ff0000000000000ull) == 0x7ff0000000000000ull && (b << 12))
+        b |= 0x0008000000000000ull;  // treat those by the older maxNum rule)
+      memcpy(&x, &b, 8);
+      return x;
+    }
+    if (k % 4 == 2) {  // subnormal / smallest normals
+      unsigned long long b = (g() & 0x801fffffffffffffull);
+      memcpy(&x, &b, 8);
+      return x;
+    }
+    std::normal_distribution<double> n(0.0, 1.0);
+    return n(g);
+  };
+  long long bad = 0, n = 0;
+  for (long long i = 0; i < 4000000; ++i) {
+    const double a = draw((int)i), b = draw((int)(i / 4 + 1)), c = (i & 1) ? a : -a;
+    ++n;
+    bad += gt0(a) != (a > 0.0);
+    bad += lt0(a) != (a < 0.0);
+    bad += ge0(a) != (a >= 0.0);
+    bad += is_nan(a) != (a != a);
+    bad += abs_lt(a, b) != (fabs(a) < b);
+    bad += !same(pos_part(a), fmax(a, 0.0)) && !(a == 0.0 && pos_part(a) == 0.0);
+    // fmin / fmax: equal values (+0 / -0) may return either operand
+    const double mn = tmin2(a, b), mx = tmax2(a, b);
+    bad += !(same(mn, fmin(a, b)) || (a == b && (same(mn, a) || same(mn, b))));
+    bad += !(same(mx, fmax(a, b)) || (a == b && (same(mx, a) || same(mx, b))));
+    bad += !same(neg4(a), -4.0 * a);
+    bad += !same(half_of(a), 0.5 * a);
+    const double m = fabs(a);
+    if (!(m != m)) {
+      bad += !same(bits2d(twice_bits(dbits(m))), m + m);
+      bad += !same(bits2d(half_bits(dbits(m))), 0.5 * m);
+    }
+    // slopes: unrelated pairs and same-sign pairs of comparable magnitude
+    // (the reference's dm * dp > 0 test fails when the product underflows,
+    // where the sign test keeps the slope: such pairs are skipped)
+    std::uniform_real_distribution<double> u(0.2, 5.0);
+    const double pairs[2][2] = {{a, c + b}, {a, a * u(g)}};
+    for (const auto& q : pairs) {
+      const double dm = q[0], dp = q[1];
+      if (!std::isfinite(dm) || !std::isfinite(dp) || (dm != 0.0 && dp != 0.0 && dm * dp == 0.0))
+        continue;
+      for (int lim = 0; lim <= 2; ++lim) bad += !same(limited_slope<double>(dm, dp, lim), slope_ref(dm, dp, lim));
+    }
+  }
+  printf("%lld disagreements in %lld cases\n", bad, n);
+  return bad ? 1 : 0;
+}
