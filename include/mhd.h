@@ -158,6 +158,23 @@ int mhd_dt(mhd_ctx* ctx, double* dt, double* ch);
  * synchronise: dt and c_h stay on the device (see mhd_step_info). */
 int mhd_step(mhd_ctx* ctx, double dt, double ch);
 
+/* One step of a state that lives in host memory: U_in (host, float64,
+ * conservative, [9][nz][ny][nx]) becomes the context's state, is advanced by
+ * mhd_step(dt, ch), and the result is copied to U_out (host; may be U_in).
+ * The same result, time and counters as mhd_set_state(U_in, MHD_HOST,
+ * MHD_CONS) + mhd_step(dt, ch) + mhd_get_state(U_out, MHD_HOST, MHD_CONS)
+ * (the time restarts at 0).  FP64 3-D contexts with nz >= 8 overlap the copies
+ * with the device work: U_in goes over in eight z slabs on a second stream,
+ * made on first use, each followed by its part of the wave-speed reduction,
+ * and the last Runge-Kutta stage runs as two half-depth launches whose
+ * outputs are copied back while the other half computes.  Other contexts run
+ * the three calls in sequence.  Page-locked host buffers (cudaHostAlloc /
+ * cudaHostRegister) are needed for the overlap.  Synchronous: returns when
+ * U_out holds the new state.  MHD_DIVB_CT is rejected (it needs a face field:
+ * use the separate calls).  Not to be mixed with other work on the context's
+ * state from other streams while it runs. */
+int mhd_step_host(mhd_ctx* ctx, const double* U_in, double* U_out, double dt, double ch);
+
 /* out[0] = time t, out[1] = dt and out[2] = c_h of the last step,
  * out[3] = steps taken since set_state.  Synchronises; reports
  * MHD_ERR_NONFINITE if the device flagged a non-finite dt or state. */

@@ -34,7 +34,8 @@ MHD_FLAG_ADJOINT = 1
 MHD_DIVB_GLM, MHD_DIVB_CT = 0, 1
 
 EXPORTED = ["mhd_config_default", "mhd_workspace_bytes", "mhd_create", "mhd_set_stream",
-            "mhd_set_state", "mhd_get_state", "mhd_dt", "mhd_step", "mhd_step_info",
+            "mhd_set_state", "mhd_get_state", "mhd_dt", "mhd_step", "mhd_step_host",
+            "mhd_step_info",
             "mhd_counters", "mhd_conserved_sums", "mhd_flux_batch", "mhd_adjoint_step",
             "mhd_profile_enable", "mhd_profile_read", "mhd_conserved_sums_noalloc",
             "mhd_last_error", "mhd_destroy", "mhd_set_face_field", "mhd_get_face_field",
@@ -86,6 +87,7 @@ def lib():
         L.mhd_divb_max.argtypes = [vp, dp]
         L.mhd_dt.argtypes = [vp, dp, dp]
         L.mhd_step.argtypes = [vp, d, d]
+        L.mhd_step_host.argtypes = [vp, vp, vp, d, d]
         L.mhd_step_info.argtypes = [vp, dp]
         L.mhd_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
         L.mhd_conserved_sums.argtypes = [vp, dp]
@@ -190,6 +192,14 @@ def mhd_dt(ctx):
 
 def mhd_step(ctx, dt: float = 0.0, ch: float = 0.0):
     _check(lib().mhd_step(ctx, float(dt), float(ch)), ctx, "mhd_step")
+
+
+def mhd_step_host(ctx, U_in, U_out, dt: float = 0.0, ch: float = 0.0):
+    """U_in, U_out: float64 numpy arrays (9, nz, ny, nx) in host memory
+    (page-locked for the copy overlap); U_out may be U_in."""
+    _check(lib().mhd_step_host(ctx, U_in.ctypes.data_as(ctypes.c_void_p),
+                               U_out.ctypes.data_as(ctypes.c_void_p), float(dt), float(ch)),
+           ctx, "mhd_step_host")
 
 
 def mhd_adjoint_step(ctx, U_n, lam_np1, lam_n, dt: float, ch: float):
@@ -350,6 +360,14 @@ class MHD:
 
     def step(self, dt: float = 0.0, ch: float = 0.0):
         mhd_step(self.ctx, dt, ch)
+
+    def step_host(self, U_in, U_out, dt: float = 0.0, ch: float = 0.0):
+        """One step of a host-resident state (mhd_step_host): U_in, U_out are
+        float64 numpy arrays (9, nz, ny, nx), contiguous; U_out may be U_in."""
+        for a in (U_in, U_out):
+            assert isinstance(a, np.ndarray) and a.dtype == np.float64
+            assert a.flags["C_CONTIGUOUS"] and a.shape == self.shape
+        mhd_step_host(self.ctx, U_in, U_out, dt, ch)
 
     def step_info(self):
         out = (ctypes.c_double * 4)()

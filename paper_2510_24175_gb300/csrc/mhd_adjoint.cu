@@ -74,10 +74,10 @@ __global__ void __launch_bounds__(128) adj_faces_kernel(const double* __restrict
       sa[k] = limited_slope_d(V[1][k] - V[0][k], V[2][k] - V[1][k], a.limiter, dma[k], dpa[k]);
       sb[k] = limited_slope_d(V[2][k] - V[1][k], V[3][k] - V[2][k], a.limiter, dmb[k], dpb[k]);
     }
-    const bool oka = (V[1][kRHO] - 0.5 * fabs(sa[kRHO]) > 0.0) &&
-                     (V[1][kPRS] - 0.5 * fabs(sa[kPRS]) > 0.0);
-    const bool okb = (V[2][kRHO] - 0.5 * fabs(sb[kRHO]) > 0.0) &&
-                     (V[2][kPRS] - 0.5 * fabs(sb[kPRS]) > 0.0);
+    const bool oka = gt0(V[1][kRHO] - 0.5 * fabs(sa[kRHO])) &&
+                     gt0(V[1][kPRS] - 0.5 * fabs(sa[kPRS]));
+    const bool okb = gt0(V[2][kRHO] - 0.5 * fabs(sb[kRHO])) &&
+                     gt0(V[2][kPRS] - 0.5 * fabs(sb[kPRS]));
     double vl[kNV], vr[kNV];
 #pragma unroll
     for (int k = 0; k < kNV; ++k) {
@@ -110,10 +110,11 @@ __global__ void __launch_bounds__(128) adj_faces_kernel(const double* __restrict
       const double g1 = vlb[k] + (dma[k] - dpa[k]) * ga - dmb[k] * gb;
       const double g2 = dpa[k] * ga + vrb[k] + (dmb[k] - dpb[k]) * gb;
       const double g3 = dpb[k] * gb;
-      if (g0 != 0.0) atomicAdd(&gV[k * a.sv + off[0]], g0);
-      if (g1 != 0.0) atomicAdd(&gV[k * a.sv + off[1]], g1);
-      if (g2 != 0.0) atomicAdd(&gV[k * a.sv + off[2]], g2);
-      if (g3 != 0.0) atomicAdd(&gV[k * a.sv + off[3]], g3);
+      // (zero tests on the integer pipe)
+      if (nonzero(g0)) atomicAdd(&gV[k * a.sv + off[0]], g0);
+      if (nonzero(g1)) atomicAdd(&gV[k * a.sv + off[1]], g1);
+      if (nonzero(g2)) atomicAdd(&gV[k * a.sv + off[2]], g2);
+      if (nonzero(g3)) atomicAdd(&gV[k * a.sv + off[3]], g3);
     }
   }
 }

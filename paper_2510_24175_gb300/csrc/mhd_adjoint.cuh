@@ -16,6 +16,7 @@ template <class T>
 struct Side {
   // outer state
   T r, u, v, w, by, bz, p, b2, pt, e, ri, gp, a, disc, sd, cf;
+  T isd, icf;  // 1 / sd, 1 / cf (from reciprocal square roots)
   // single-star state
   T S, d, sm, smi, rs, den, deni, fv, fb, vs, ws, bys, bzs, vb, vbs, es, sq;
   bool deg, clamp;
@@ -47,10 +48,15 @@ MHD_HD void side_outer(Side<T>& s, T bx2, const Phys<T>& ph) {
   s.gp = ph.gamma * s.p;
   s.a = (s.gp + s.b2) * s.ri;
   const T disc = s.a * s.a - T(4) * s.gp * bx2 * (s.ri * s.ri);
-  s.clamp = !(disc > T(0));
-  s.disc = tmax(disc, T(0));
-  s.sd = tsqrt(s.disc);
-  s.cf = tsqrt(half * (s.a + s.sd));
+  // sqrt and the reciprocals the reverse needs from reciprocal square roots
+  // (sd = disc / sqrt(disc), cf likewise); a clamped discriminant gives sd = 0
+  s.clamp = !gt0(disc);
+  s.disc = s.clamp ? T(0) : disc;
+  s.isd = trsqrt(s.disc);
+  s.sd = s.clamp ? T(0) : s.disc * s.isd;
+  const T c2 = half * (s.a + s.sd);
+  s.icf = trsqrt(c2);
+  s.cf = c2 * s.icf;
 }
 
 template <class T>
@@ -59,7 +65,7 @@ MHD_HD void side_star(Side<T>& s, T bx, T bx2, T SM, T pts) {
   s.smi = rcp(s.sm);
   s.rs = s.d * s.smi;
   s.den = s.d * s.sm - bx2;
-  s.deg = tabs(s.den) < T(1e-8) * pts;
+  s.deg = abs_lt(s.den, T(1e-8) * pts);
   s.deni = rcp(s.deg ? T(1) : s.den);
   s.fv = bx * (SM - s.u) * s.deni;
   s.fb = (s.d * (s.S - s.u) - bx2) * s.deni;
@@ -151,11 +157,11 @@ MHD_HD void side_outer_bar(const Side<T>& s, SideBar<T>& sb, T bx2, const Phys<T
                            T& bx2b) {
   const T half = T(0.5);
   // cf = sqrt(half (a + sd))
-  const T cf2b = sb.cf * half / s.cf;
+  const T cf2b = sb.cf * half * s.icf;
   sb.a += half * cf2b;
   sb.sd += half * cf2b;
   // sd = sqrt(disc) (disc clamped at 0: no derivative through the clamp)
-  if (!s.clamp && s.sd > T(0)) sb.disc += sb.sd * half / s.sd;
+  if (!s.clamp && gt0(s.sd)) sb.disc += sb.sd * half * s.isd;
   // disc = a^2 - 4 gp bx2 ri^2
   sb.a += sb.disc * T(2) * s.a;
   sb.gp -= sb.disc * T(4) * bx2 * s.ri * s.ri;
@@ -214,10 +220,11 @@ MHD_HD void glm_hlld_flux_vjp(const T vl[kNV], const T vr[kNV], int dir, T ch, T
   const T bx2 = bx * bx;
   side_outer(L, bx2, ph);
   side_outer(R, bx2, ph);
-  const bool cfL_max = !(R.cf > L.cf);  // cmax = cfL on ties
+  // (comparisons on the integer pipe in FP64: lt_ieee, gt0, lt0, ge0)
+  const bool cfL_max = !lt_ieee(L.cf, R.cf);  // cmax = cfL on ties
   const T cmax = cfL_max ? L.cf : R.cf;
-  const bool uL_min = !(R.u < L.u);     // min(uL, uR) picks uL on ties
-  const bool uL_max = !(R.u > L.u);     // max(uL, uR) picks uL on ties
+  const bool uL_min = !lt_ieee(R.u, L.u);     // min(uL, uR) picks uL on ties
+  const bool uL_max = !lt_ieee(L.u, R.u);     // max(uL, uR) picks uL on ties
   L.S = (uL_min ? L.u : R.u) - cmax;
   R.S = (uL_max ? L.u : R.u) + cmax;
   L.d = (L.S - L.u) * L.r;
@@ -229,13 +236,13 @@ MHD_HD void glm_hlld_flux_vjp(const T vl[kNV], const T vr[kNV], int dir, T ch, T
   const T pts = Np * Di;
   side_star(L, bx, bx2, SM, pts);
   side_star(R, bx, bx2, SM, pts);
-  L.sq = tsqrt(L.rs);
-  R.sq = tsqrt(R.rs);
+  const T iqL = trsqrt(L.rs), iqR = trsqrt(R.rs);
+  L.sq = L.rs * iqL;
+  R.sq = R.rs * iqR;
   const T abx = tabs(bx);
-  const T iqL = rcp(L.sq), iqR = rcp(R.sq);
   const T SLs = SM - abx * iqL;
   const T SRs = SM + abx * iqR;
-  const T sg = bx >= T(0) ? T(1) : T(-1);
+  const T sg = ge0(bx) ? T(1) : T(-1);
   const T isum = rcp(L.sq + R.sq);
   const T Nv = L.sq * L.vs + R.sq * R.vs + (R.bys - L.bys) * sg;
   const T Nw = L.sq * L.ws + R.sq * R.ws + (R.bzs - L.bzs) * sg;
@@ -243,9 +250,9 @@ MHD_HD void glm_hlld_flux_vjp(const T vl[kNV], const T vr[kNV], int dir, T ch, T
   const T Nbz = L.sq * R.bzs + R.sq * L.bzs + L.sq * R.sq * (R.ws - L.ws) * sg;
   const T vss = Nv * isum, wss = Nw * isum, byss = Nby * isum, bzss = Nbz * isum;
   const T vbss = SM * bx + vss * byss + wss * bzss;
-  const bool sup = (L.S > T(0)) || (R.S < T(0));
-  const bool useL = (L.S > T(0)) || (!(R.S < T(0)) && SM >= T(0));
-  const bool inner = !sup && (useL ? !(SLs > T(0)) : !(SRs < T(0)));
+  const bool sup = gt0(L.S) || lt0(R.S);
+  const bool useL = gt0(L.S) || (!lt0(R.S) && ge0(SM));
+  const bool inner = !sup && (useL ? !gt0(SLs) : !lt0(SRs));
   // selected side a
   const T r = useL ? L.r : R.r, u = useL ? L.u : R.u, v = useL ? L.v : R.v;
   const T w = useL ? L.w : R.w, by = useL ? L.by : R.by, bz = useL ? L.bz : R.bz;
@@ -549,6 +556,38 @@ MHD_HD T limited_slope_d(T dm, T dp, int lim, T& ddm, T& ddp) {
   return s;
 }
 
+// FP64: the same values from the bit patterns, as limited_slope<double>: the
+// zero test, the minmod choice, the MC doubling / halving and the MC
+// decision on the integer pipe; |dm| + |dp| is the only FP64 operation.
+template <>
+MHD_HD double limited_slope_d<double>(double dm, double dp, int lim, double& ddm, double& ddp) {
+  ddm = 0.0;
+  ddp = 0.0;
+  const long long a = dbits(dm), b = dbits(dp);
+  const long long mask = 0x7fffffffffffffffll;
+  const long long am = a & mask, bm = b & mask;
+  if (lim == kLimFlat || (a ^ b) < 0 || am == 0 || bm == 0) return 0.0;
+  const bool m_is_dm = !(bm < am);  // the smaller magnitude; dm on ties
+  long long mb = m_is_dm ? am : bm;
+  double gdm = m_is_dm ? 1.0 : 0.0, gdp = m_is_dm ? 0.0 : 1.0;
+  if (lim == kLimMC) {
+    const long long two = twice_bits(mb);
+    const long long cen = half_bits(dbits(bits2d(am) + bits2d(bm)));
+    if (cen < two) {  // central slope selected
+      mb = cen;
+      gdm = 0.5;
+      gdp = 0.5;
+    } else {
+      mb = two;
+      gdm = m_is_dm ? 2.0 : 0.0;
+      gdp = m_is_dm ? 0.0 : 2.0;
+    }
+  }
+  ddm = gdm;
+  ddp = gdp;
+  return bits2d(mb | (a & ~mask));
+}
+
 // Reverse of cons_to_prim (floors inactive: a floored value has zero
 // derivative).  vb: adjoint of the primitives; ub: adjoint of the
 // conservatives (overwritten).
@@ -561,8 +600,8 @@ MHD_HD void cons_to_prim_vjp(const T u[kNV], const T vb[kNV], const Phys<T>& ph,
   const T kin = T(0.5) * (u[kVX] * vx + u[kVY] * vy + u[kVZ] * vz);
   const T b2 = u[kBX] * u[kBX] + u[kBY] * u[kBY] + u[kBZ] * u[kBZ];
   const T p = ph.gm1 * (u[kPRS] - kin - T(0.5) * b2);
-  const bool rfl = rho < ph.rho_floor;
-  const bool pfl = p < ph.p_floor;
+  const bool rfl = lt_ieee(rho, ph.rho_floor);
+  const bool pfl = lt_ieee(p, ph.p_floor);
   const T pb = pfl ? T(0) : vb[kPRS];
   // p = gm1 (E - |m|^2/(2 rho) - |B|^2/2)
   T rhob = rfl ? T(0) : vb[kRHO];

@@ -358,6 +358,13 @@ int mhd_create(const mhd_config* cfg, void* d_workspace, size_t bytes, void* str
     mhd::stage_shape<float>(c->grid, &smem, &threads, &ty);
   const int per_sm = (int)(228 * 1024 / (smem + 1024));
   c->grid.tz = choose_tz(c->grid, per_sm < 1 ? 1 : per_sm, ty);
+  {
+    mhd::Grid gh = c->grid;  // the half-depth grid of mhd_step_host's last stage
+    gh.n[2] = (gh.n[2] + 1) / 2;
+    c->tz_half = choose_tz(gh, per_sm < 1 ? 1 : per_sm, ty);
+  }
+  c->xfer_ready = false;
+  c->xfer = nullptr;
   c->have_state = false;
   c->lam_valid = false;
   snprintf(c->err, sizeof(c->err), "no error");
@@ -558,7 +565,29 @@ int mhd_dt(mhd_ctx* c, double* dt, double* ch) {
   return MHD_OK;
 }
 
-int mhd_step(mhd_ctx* c, double dt, double ch) {
+// Host output of mhd_step_host: the last stage runs as two launches over the
+// z planes [0, zh) and [zh, nz); each half of U^{n+1} is copied to U on the
+// transfer stream as soon as its launch is done.
+struct HostOut {
+  double* U;
+  int zh;
+};
+
+static int copy_planes(mhd_ctx* c, double* dst, const double* src, int z0, int z1,
+                       cudaMemcpyKind kind) {
+  const long long plane = (long long)c->grid.n[0] * c->grid.n[1];
+  const long long n = c->grid.ncell;
+  for (int k = 0; k < 9; ++k)
+    CK(c, cudaMemcpyAsync(dst + k * n + z0 * plane, src + k * n + z0 * plane,
+                          (size_t)(z1 - z0) * plane * sizeof(double), kind, c->xfer));
+  return MHD_OK;
+}
+
+static int step_impl(mhd_ctx* c, double dt, double ch, const HostOut* ho);
+
+int mhd_step(mhd_ctx* c, double dt, double ch) { return step_impl(c, dt, ch, nullptr); }
+
+static int step_impl(mhd_ctx* c, double dt, double ch, const HostOut* ho) {
   if (!c) return MHD_ERR_INVALID;
   if (!c->have_state) return fail(c, MHD_ERR_STATE, "mhd_step before mhd_set_state");
   if (c->cfg.divb == MHD_DIVB_CT && !c->faces_set)
@@ -607,6 +636,26 @@ int mhd_step(mhd_ctx* c, double dt, double ch) {
                  : MHD_OK;
     if (rc != MHD_OK) return rc;
     if (c->cfg.divb == MHD_DIVB_CT) continue;
+    if (ho && i == nst - 1) {  // FP64, GLM, 3-D (checked by mhd_step_host)
+      const int zs[3] = {0, ho->zh, c->grid.n[2]};
+      for (int h = 0; h < 2; ++h) {
+        {
+          ProfScope ps(c, q.cls);
+          CK(c, mhd::launch_stage<double>(c->grid, q.kind, static_cast<const double*>(q.win),
+                                          static_cast<const double*>(q.un),
+                                          static_cast<double*>(q.out), &c->scal->sc,
+                                          &c->scal->lam_bits, c->scal->floor_cnt, c->stream,
+                                          q.an, q.aw, nullptr, nullptr, zs[h], zs[h + 1],
+                                          c->tz_half));
+        }
+        CK(c, cudaEventRecord(c->xev[10 + h], c->stream));
+        CK(c, cudaStreamWaitEvent(c->xfer, c->xev[10 + h], 0));
+        rc = copy_planes(c, ho->U, static_cast<const double*>(q.out), zs[h], zs[h + 1],
+                         cudaMemcpyDeviceToHost);
+        if (rc != MHD_OK) return rc;
+      }
+      continue;
+    }
     ProfScope ps(c, q.cls);
     if (c->esize == 8)
       CK(c, mhd::launch_stage<double>(c->grid, q.kind, static_cast<const double*>(q.win),
@@ -621,6 +670,62 @@ int mhd_step(mhd_ctx* c, double dt, double ch) {
                                      c->stream, q.an, q.aw));
   }
   c->lam_valid = true;
+  return MHD_OK;
+}
+
+int mhd_step_host(mhd_ctx* c, const double* U_in, double* U_out, double dt, double ch) {
+  if (!c) return MHD_ERR_INVALID;
+  if (!U_in || !U_out) return fail(c, MHD_ERR_INVALID, "mhd_step_host: null buffer");
+  if (c->cfg.divb == MHD_DIVB_CT)
+    return fail(c, MHD_ERR_INVALID,
+                "mhd_step_host: constrained transport needs a face field; use mhd_set_state, "
+                "mhd_set_face_field, mhd_step and mhd_get_state");
+  if (std::isnan(dt) || std::isnan(ch) || std::isinf(dt) || std::isinf(ch))
+    return fail(c, MHD_ERR_INVALID, "mhd_step_host: non-finite dt or ch");
+  const int nz = c->grid.n[2];
+  if (!(c->esize == 8 && c->grid.ndim == 3 && nz >= 8)) {
+    // no overlap: the three calls in sequence
+    int rc = mhd_set_state(c, U_in, MHD_HOST, MHD_CONS);
+    if (rc == MHD_OK) rc = mhd_step(c, dt, ch);
+    if (rc == MHD_OK) rc = mhd_get_state(c, U_out, MHD_HOST, MHD_CONS);
+    return rc;
+  }
+  if (!c->xfer_ready) {
+    CK(c, cudaStreamCreateWithFlags(&c->xfer, cudaStreamNonBlocking));
+    for (int i = 0; i < 12; ++i) CK(c, cudaEventCreateWithFlags(&c->xev[i], cudaEventDisableTiming));
+    c->xfer_ready = true;
+  }
+  double* A = static_cast<double*>(c->Ua);
+  const long long plane = (long long)c->grid.n[0] * c->grid.n[1];
+  // the copies start once the work already enqueued on the context's stream
+  // (which may read the state) is done
+  CK(c, cudaEventRecord(c->xev[0], c->stream));
+  CK(c, cudaStreamWaitEvent(c->xfer, c->xev[0], 0));
+  // as mhd_set_state: the time, counters and wave speed restart
+  CK(c, cudaMemsetAsync(c->scal, 0, sizeof(Scalars), c->stream));
+  c->have_state = true;
+  c->lam_valid = false;
+  c->faces_set = false;
+  const bool need_lam = !(dt > 0.0) || !(ch > 0.0);
+  // eight input slabs; the wave-speed reduction follows each as it lands
+  for (int k = 0; k < 8; ++k) {
+    const int z0 = (int)((long long)nz * k / 8), z1 = (int)((long long)nz * (k + 1) / 8);
+    int rc = copy_planes(c, A, U_in, z0, z1, cudaMemcpyHostToDevice);
+    if (rc != MHD_OK) return rc;
+    CK(c, cudaEventRecord(c->xev[1 + k], c->xfer));
+    CK(c, cudaStreamWaitEvent(c->stream, c->xev[1 + k], 0));
+    if (need_lam) {
+      ProfScope ps(c, 3);
+      CK(c, mhd::launch_max_speed_range<double>(c->grid, A, z0 * plane, z1 * plane,
+                                                &c->scal->lam_bits, c->scal->floor_cnt,
+                                                c->stream));
+    }
+  }
+  c->lam_valid = need_lam;
+  HostOut ho{U_out, nz / 2};
+  int rc = step_impl(c, dt, ch, &ho);
+  if (rc != MHD_OK) return rc;
+  CK(c, cudaStreamSynchronize(c->xfer));
   return MHD_OK;
 }
 
@@ -732,6 +837,11 @@ int mhd_destroy(mhd_ctx* c) {
     cudaEventDestroy(r.b);
   }
   for (auto e : c->prof_pool) cudaEventDestroy(e);
+  if (c->xfer_ready) {
+    cudaStreamSynchronize(c->xfer);
+    for (auto e : c->xev) cudaEventDestroy(e);
+    cudaStreamDestroy(c->xfer);
+  }
   delete c;
   return MHD_OK;
 }

@@ -63,12 +63,12 @@ cudaError_t launch_prep(const PrepArgs& a, StepScalars* sc, unsigned long long* 
 // ---------------------------------------------------------- max wave speed --
 template <class T>
 __global__ void __launch_bounds__(256) max_speed_kernel(const T* __restrict__ U, long long ncell,
-                                                        int ndim, Phys<T> ph,
-                                                        unsigned long long* lam_bits,
+                                                        long long c0, long long c1, int ndim,
+                                                        Phys<T> ph, unsigned long long* lam_bits,
                                                         unsigned long long* floor_cnt) {
   unsigned flags = 0;
   double lam = 0.0;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+  for (long long c = c0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; c < c1;
        c += (long long)gridDim.x * blockDim.x) {
     T u[kNV];
 #pragma unroll
@@ -101,18 +101,32 @@ cudaError_t launch_max_speed(const Grid& g, const T* U, unsigned long long* lam_
                              unsigned long long* floor_cnt, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(lam_bits, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
-  long long blocks = (g.ncell + 255) / 256;
+  return launch_max_speed_range<T>(g, U, 0, g.ncell, lam_bits, floor_cnt, stream);
+}
+
+template <class T>
+cudaError_t launch_max_speed_range(const Grid& g, const T* U, long long c0, long long c1,
+                                   unsigned long long* lam_bits, unsigned long long* floor_cnt,
+                                   cudaStream_t stream) {
+  if (c0 < 0 || c1 > g.ncell || c0 >= c1) return cudaErrorInvalidValue;
+  long long blocks = (c1 - c0 + 255) / 256;
   const long long cap = (long long)g.nsm * 8;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  max_speed_kernel<T><<<(unsigned)blocks, 256, 0, stream>>>(U, g.ncell, g.ndim, make_phys<T>(g),
-                                                            lam_bits, floor_cnt);
+  max_speed_kernel<T><<<(unsigned)blocks, 256, 0, stream>>>(U, g.ncell, c0, c1, g.ndim,
+                                                            make_phys<T>(g), lam_bits, floor_cnt);
   return cudaGetLastError();
 }
 template cudaError_t launch_max_speed<double>(const Grid&, const double*, unsigned long long*,
                                               unsigned long long*, cudaStream_t);
 template cudaError_t launch_max_speed<float>(const Grid&, const float*, unsigned long long*,
                                              unsigned long long*, cudaStream_t);
+template cudaError_t launch_max_speed_range<double>(const Grid&, const double*, long long,
+                                                    long long, unsigned long long*,
+                                                    unsigned long long*, cudaStream_t);
+template cudaError_t launch_max_speed_range<float>(const Grid&, const float*, long long,
+                                                   long long, unsigned long long*,
+                                                   unsigned long long*, cudaStream_t);
 
 // ------------------------------------------------------ conservation sums --
 // Pass 1: CTA b sums the contiguous cell range [b*chunk, (b+1)*chunk) of the

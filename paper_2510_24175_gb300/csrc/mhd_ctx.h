@@ -54,6 +54,12 @@ struct mhd_ctx {
   bool have_state;
   bool lam_valid;
   double inv_dx_sum, dh_min;
+  // mhd_step_host: a transfer stream and its events (made on first use), and
+  // the z-chunk depth of the last stage's half launches
+  bool xfer_ready;
+  cudaStream_t xfer;
+  cudaEvent_t xev[12];
+  int tz_half;
   // CUDA-event timing (mhd_profile_enable)
   bool prof_on;
   struct Rec { cudaEvent_t a, b; int kind; };

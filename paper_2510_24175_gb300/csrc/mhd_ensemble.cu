@@ -187,6 +187,8 @@ static int ens_layout(mhd_ensemble* e) {
     EnsBox& B = e->h[b];
     const mhd::Grid& g = e->ctx[b]->grid;
     B.p.tz = e->tz[b];
+    B.p.zlo = 0;
+    B.p.zhi = g.n[2];
     B.ntx = (g.n[0] + 31) / 32;
     B.nty = (g.n[1] + mhd::kEnsTY - 1) / mhd::kEnsTY;
     B.ntz = (g.n[2] + B.p.tz - 1) / B.p.tz;

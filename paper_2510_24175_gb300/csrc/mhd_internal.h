@@ -31,13 +31,16 @@ Phys<T> make_phys(const Grid& g);
 // 2: last stage (combination with a_n, a_w + damping + wave-speed
 // reduction); 3: SSP-RK3 middle stage (combination only).
 // Constrained transport (bw, ctf non-null; 3-D): bw = the input's face field
-// (three planes), ctf = the kCtPlanes-plane CT buffer.
+// (three planes), ctf = the kCtPlanes-plane CT buffer.  3-D grids: the launch
+// covers z planes [zlo, zhi) (zhi < 0: all) in chunks of tz planes per CTA
+// (tz <= 0: the grid's own choice); the result of a cell does not depend on
+// the decomposition.
 template <class T>
 cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T* uout,
                          const StepScalars* sc, unsigned long long* lam_bits,
                          unsigned long long* floor_cnt, cudaStream_t stream,
                          double a_n = 0.5, double a_w = 0.5, const T* const* bw = nullptr,
-                         T* ctf = nullptr);
+                         T* ctf = nullptr, int zlo = 0, int zhi = -1, int tz = 0);
 
 // Constrained-transport kernels (mhd_ct.cu); face / edge arrays are three
 // planes of ncell values, b_d on each cell's lower d-face.
@@ -77,6 +80,12 @@ cudaError_t launch_prep(const PrepArgs& a, StepScalars* sc, unsigned long long* 
 template <class T>
 cudaError_t launch_max_speed(const Grid& g, const T* U, unsigned long long* lam_bits,
                              unsigned long long* floor_cnt, cudaStream_t stream);
+// The same reduction over cells [c0, c1) only, accumulated into lam_bits
+// (not cleared first).
+template <class T>
+cudaError_t launch_max_speed_range(const Grid& g, const T* U, long long c0, long long c1,
+                                   unsigned long long* lam_bits, unsigned long long* floor_cnt,
+                                   cudaStream_t stream);
 
 template <class T>
 cudaError_t launch_sums(const Grid& g, const T* U, double* partials, int nblocks,

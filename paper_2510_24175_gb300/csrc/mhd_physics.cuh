@@ -147,6 +147,17 @@ MHD_HD double tmax2(double a, double b) {
 }
 MHD_HD float tmin2(float a, float b) { return fminf(a, b); }
 MHD_HD float tmax2(float a, float b) { return fmaxf(a, b); }
+// a < b with IEEE semantics (NaN unordered, -0 == +0): a double's pattern,
+// with negative ones mapped to minus their magnitude, is a signed integer in
+// the numeric order.
+MHD_HD long long num_key(long long b) { return b < 0 ? -(b & 0x7fffffffffffffffll) : b; }
+MHD_HD bool lt_ieee(double a, double b) {
+  return !is_nan(a) && !is_nan(b) && num_key(dbits(a)) < num_key(dbits(b));
+}
+MHD_HD bool lt_ieee(float a, float b) { return a < b; }
+// x != 0 (true for NaN, as the IEEE comparison)
+MHD_HD bool nonzero(double x) { return (dbits(x) << 1) != 0; }
+MHD_HD bool nonzero(float x) { return x != 0.0f; }
 // |a| < t, IEEE (false when either is NaN)
 MHD_HD bool abs_lt(double a, double t) {
   const long long x = dbits(a) & 0x7fffffffffffffffll, y = dbits(t);
@@ -180,7 +191,7 @@ MHD_HD long long half_bits(long long b) {
 // conservative inputs and the floor decision is taken in FP64.
 MHD_HD double pressure_floor(double p, const double u[kNV], double rho,
                                                  const Phys<double>& ph, unsigned& flags) {
-  if (p < ph.p_floor) {
+  if (lt_ieee(p, ph.p_floor)) {
     flags |= kFloorP;
     return ph.p_floor;
   }
@@ -208,7 +219,7 @@ template <class T>
 MHD_HD void cons_to_prim(const T u[kNV], T v[kNV], const Phys<T>& ph,
                                              unsigned& flags) {
   T rho = u[kRHO];
-  if (rho < ph.rho_floor) {
+  if (lt_ieee(rho, ph.rho_floor)) {
     rho = ph.rho_floor;
     flags |= kFloorRho;
   }

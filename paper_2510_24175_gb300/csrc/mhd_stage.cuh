@@ -49,6 +49,7 @@ struct StageParams {
   int bc_lo[3], bc_hi[3];
   int limiter;
   int tz;         // planes per CTA
+  int zlo, zhi;   // z planes [zlo, zhi) of this launch (blockIdx.z counts tz-plane chunks)
   T a_n, a_w;     // combining stages: out = a_n U^n + a_w (W + dt L(W))
   Phys<T> ph;
   const StepScalars* sc;
@@ -213,8 +214,8 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
   const int tid = threadIdx.x;
   const int x0 = bx * TX;
   const int y0 = by * TY;
-  const int z0 = bz * p.tz;
-  const int z1 = min(z0 + p.tz, p.n[2]);
+  const int z0 = p.zlo + bz * p.tz;
+  const int z1 = min(z0 + p.tz, p.zhi);
   const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
   const bool owner = tid >= ZT0;
   const int oidx = tid - ZT0;  // owned column = interior cell index r * TX + c

@@ -82,7 +82,7 @@ template <class T>
 cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T* uout,
                          const StepScalars* sc, unsigned long long* lam_bits,
                          unsigned long long* floor_cnt, cudaStream_t stream, double a_n,
-                         double a_w, const T* const* bw, T* ctf) {
+                         double a_w, const T* const* bw, T* ctf, int zlo, int zhi, int tz) {
   StageParams<T> p;
   p.a_n = T(a_n);
   p.a_w = T(a_w);
@@ -98,7 +98,11 @@ cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T*
   p.sz = (long long)g.n[0] * g.n[1];
   p.sv = g.ncell;
   p.limiter = g.limiter;
-  p.tz = g.ndim == 3 ? g.tz : 1;
+  p.tz = g.ndim == 3 ? (tz > 0 ? tz : g.tz) : 1;
+  p.zlo = g.ndim == 3 ? zlo : 0;
+  p.zhi = g.ndim == 3 && zhi >= 0 ? zhi : g.n[2];
+  if (p.zlo < 0 || p.zhi > g.n[2] || p.zlo >= p.zhi) return cudaErrorInvalidValue;
+  const int nzc = (p.zhi - p.zlo + p.tz - 1) / p.tz;  // z chunks of this launch
   p.ph = make_phys<T>(g);
   p.sc = sc;
   p.lam_bits = lam_bits;
@@ -109,20 +113,20 @@ cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T*
     // constrained transport: 3-D grids only (checked when the context is made)
     if (g.ndim != 3 || !bw) return cudaErrorInvalidValue;
     if (g.limiter == kLimWenoz) {
-      dim3 grid((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, (g.n[2] + p.tz - 1) / p.tz);
+      dim3 grid((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, nzc);
       if (stage == 1) return launch_weno<T, 4, 8, 1, true, true>(p, grid, stream);
       if (stage == 2) return launch_weno<T, 4, 8, 2, true, true>(p, grid, stream);
       return launch_weno<T, 4, 8, 3, true, true>(p, grid, stream);
     }
     using S = StageShape3D<T>;
-    dim3 grid((g.n[0] + 31) / 32, (g.n[1] + S::TY - 1) / S::TY, (g.n[2] + p.tz - 1) / p.tz);
+    dim3 grid((g.n[0] + 31) / 32, (g.n[1] + S::TY - 1) / S::TY, nzc);
     if (stage == 1) return launch_one<T, S::TY, S::NW, 1, true, true>(p, grid, stream);
     if (stage == 2) return launch_one<T, S::TY, S::NW, 2, true, true>(p, grid, stream);
     return launch_one<T, S::TY, S::NW, 3, true, true>(p, grid, stream);
   }
   if (g.limiter == kLimWenoz) {
     if (g.ndim == 3) {
-      dim3 grid((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, (g.n[2] + p.tz - 1) / p.tz);
+      dim3 grid((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, nzc);
       if (stage == 1) return launch_weno<T, 4, 8, 1, true>(p, grid, stream);
       if (stage == 2) return launch_weno<T, 4, 8, 2, true>(p, grid, stream);
       return launch_weno<T, 4, 8, 3, true>(p, grid, stream);
@@ -140,7 +144,7 @@ cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T*
   }
   if (g.ndim == 3) {
     using S = StageShape3D<T>;
-    dim3 grid((g.n[0] + 31) / 32, (g.n[1] + S::TY - 1) / S::TY, (g.n[2] + p.tz - 1) / p.tz);
+    dim3 grid((g.n[0] + 31) / 32, (g.n[1] + S::TY - 1) / S::TY, nzc);
     if (stage == 1) return launch_one<T, S::TY, S::NW, 1, true>(p, grid, stream);
     if (stage == 2) return launch_one<T, S::TY, S::NW, 2, true>(p, grid, stream);
     return launch_one<T, S::TY, S::NW, 3, true>(p, grid, stream);

@@ -155,8 +155,8 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
   const int tid = threadIdx.x;
   const int x0 = blockIdx.x * TX;
   const int y0 = blockIdx.y * TY;
-  const int z0 = blockIdx.z * p.tz;
-  const int z1 = min(z0 + p.tz, p.n[2]);
+  const int z0 = p.zlo + blockIdx.z * p.tz;
+  const int z1 = min(z0 + p.tz, p.zhi);
   const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
   const bool owner = tid >= ZT0;
   const int oidx = tid - ZT0;

@@ -1,7 +1,7 @@
 // Host-only check (compiled by tests/test_fp64_bit_helpers.py): the FP64
-// helpers that the kernels evaluate on the integer pipe -- sign tests,
+// helpers that the kernels evaluate on the integer pipe -- sign tests, a < b,
 // min / max, |a| < t, max(x, 0), exact doubling and halving, -4x, x/2,
-// the limited slope -- against the IEEE operations of the host compiler, on random and
+// the limited slope and its derivative flags -- against the IEEE operations of the host compiler, on random and
 // special doubles (signed zeros, subnormals, extremes, infinities, NaNs).
 // Prints the number of disagreements and exits non-zero if there is any.
 #include <cmath>
@@ -9,7 +9,7 @@
 #include <cstring>
 #include <random>
 
-#include "../paper_2510_24175_gb300/csrc/mhd_physics.cuh"
+#include "../paper_2510_24175_gb300/csrc/mhd_adjoint.cuh"
 
 using namespace mhd;
 
@@ -30,6 +30,28 @@ static double slope_ref(double dm, double dp, int lim) {
     mag = cen < two ? cen : two;
   }
   return dm > 0.0 ? mag : -mag;
+}
+
+// the limited slope's derivative flags written with plain IEEE operations
+static double slope_d_ref(double dm, double dp, int lim, double& ddm, double& ddp) {
+  ddm = ddp = 0.0;
+  const double s = slope_ref(dm, dp, lim);
+  if (s == 0.0) return s;
+  const double am = fabs(dm), ap = fabs(dp);
+  const bool m_is_dm = !(ap < am);
+  double gdm = m_is_dm ? 1.0 : 0.0, gdp = m_is_dm ? 0.0 : 1.0;
+  if (lim == kLimMC) {
+    const double two = 2.0 * (m_is_dm ? am : ap), cen = 0.5 * (am + ap);
+    if (cen < two) {
+      gdm = gdp = 0.5;
+    } else {
+      gdm *= 2.0;
+      gdp *= 2.0;
+    }
+  }
+  ddm = gdm;
+  ddp = gdp;
+  return s;
 }
 
 int main() {
@@ -66,6 +88,9 @@ int main() {
     bad += ge0(a) != (a >= 0.0);
     bad += is_nan(a) != (a != a);
     bad += abs_lt(a, b) != (fabs(a) < b);
+    bad += lt_ieee(a, b) != (a < b);
+    bad += lt_ieee(a, c) != (a < c);
+    bad += nonzero(a) != (a != 0.0);
     bad += !same(pos_part(a), fmax(a, 0.0)) && !(a == 0.0 && pos_part(a) == 0.0);
     // fmin / fmax: equal values (+0 / -0) may return either operand
     const double mn = tmin2(a, b), mx = tmax2(a, b);
@@ -87,7 +112,13 @@ int main() {
       const double dm = q[0], dp = q[1];
       if (!std::isfinite(dm) || !std::isfinite(dp) || (dm != 0.0 && dp != 0.0 && dm * dp == 0.0))
         continue;
-      for (int lim = 0; lim <= 2; ++lim) bad += !same(limited_slope<double>(dm, dp, lim), slope_ref(dm, dp, lim));
+      for (int lim = 0; lim <= 2; ++lim) {
+        bad += !same(limited_slope<double>(dm, dp, lim), slope_ref(dm, dp, lim));
+        double d1, d2, r1, r2;
+        const double s1 = limited_slope_d<double>(dm, dp, lim, d1, d2);
+        const double s2 = slope_d_ref(dm, dp, lim, r1, r2);
+        bad += !same(s1, s2) || d1 != r1 || d2 != r2;
+      }
     }
   }
   printf("%lld disagreements in %lld cases\n", bad, n);
