@@ -539,10 +539,12 @@ static int ensure_lambda(mhd_ctx* c) {
   ProfScope ps(c, 3);
   if (c->esize == 8)
     CK(c, mhd::launch_max_speed<double>(c->grid, static_cast<const double*>(c->Ua),
-                                        &c->scal->lam_bits, c->scal->floor_cnt, c->stream));
+                                        &c->scal->lam_bits, &c->scal->est_bits,
+                                        c->scal->floor_cnt, c->stream));
   else
     CK(c, mhd::launch_max_speed<float>(c->grid, static_cast<const float*>(c->Ua),
-                                       &c->scal->lam_bits, c->scal->floor_cnt, c->stream));
+                                       &c->scal->lam_bits, nullptr, c->scal->floor_cnt,
+                                       c->stream));
   c->lam_valid = true;
   return MHD_OK;
 }
@@ -612,7 +614,8 @@ static int step_impl(mhd_ctx* c, double dt, double ch, const HostOut* ho) {
   }
   {
     ProfScope ps(c, 0);
-    CK(c, mhd::launch_prep(a, &c->scal->sc, &c->scal->lam_bits, &c->scal->status, c->stream));
+    CK(c, mhd::launch_prep(a, &c->scal->sc, &c->scal->lam_bits, &c->scal->est_bits,
+                           &c->scal->status, c->stream));
   }
   // stage sequence: (kernel stage, profile class, input, U^n, output, a_n, a_w)
   struct St { int kind, cls; void *win, *un, *out; double an, aw; };
@@ -646,7 +649,7 @@ static int step_impl(mhd_ctx* c, double dt, double ch, const HostOut* ho) {
                                           static_cast<double*>(q.out), &c->scal->sc,
                                           &c->scal->lam_bits, c->scal->floor_cnt, c->stream,
                                           q.an, q.aw, nullptr, nullptr, zs[h], zs[h + 1],
-                                          c->tz_half));
+                                          c->tz_half, &c->scal->est_bits));
         }
         CK(c, cudaEventRecord(c->xev[10 + h], c->stream));
         CK(c, cudaStreamWaitEvent(c->xfer, c->xev[10 + h], 0));
@@ -654,20 +657,34 @@ static int step_impl(mhd_ctx* c, double dt, double ch, const HostOut* ho) {
                          cudaMemcpyDeviceToHost);
         if (rc != MHD_OK) return rc;
       }
+      ProfScope ps(c, 3);
+      CK(c, mhd::launch_speed_exact(c->grid, static_cast<const double*>(q.out),
+                                    &c->scal->est_bits, &c->scal->lam_bits, c->scal->floor_cnt,
+                                    c->stream));
       continue;
     }
-    ProfScope ps(c, q.cls);
-    if (c->esize == 8)
-      CK(c, mhd::launch_stage<double>(c->grid, q.kind, static_cast<const double*>(q.win),
-                                      static_cast<const double*>(q.un),
-                                      static_cast<double*>(q.out), &c->scal->sc,
-                                      &c->scal->lam_bits, c->scal->floor_cnt, c->stream, q.an,
-                                      q.aw));
-    else
+    if (c->esize == 8) {
+      {
+        ProfScope ps(c, q.cls);
+        CK(c, mhd::launch_stage<double>(c->grid, q.kind, static_cast<const double*>(q.win),
+                                        static_cast<const double*>(q.un),
+                                        static_cast<double*>(q.out), &c->scal->sc,
+                                        &c->scal->lam_bits, c->scal->floor_cnt, c->stream, q.an,
+                                        q.aw, nullptr, nullptr, 0, -1, 0, &c->scal->est_bits));
+      }
+      if (i == nst - 1) {  // the exact maximum speed of the new state (pass 2)
+        ProfScope ps(c, 3);
+        CK(c, mhd::launch_speed_exact(c->grid, static_cast<const double*>(q.out),
+                                      &c->scal->est_bits, &c->scal->lam_bits,
+                                      c->scal->floor_cnt, c->stream));
+      }
+    } else {
+      ProfScope ps(c, q.cls);
       CK(c, mhd::launch_stage<float>(c->grid, q.kind, static_cast<const float*>(q.win),
                                      static_cast<const float*>(q.un), static_cast<float*>(q.out),
                                      &c->scal->sc, &c->scal->lam_bits, c->scal->floor_cnt,
                                      c->stream, q.an, q.aw));
+    }
   }
   c->lam_valid = true;
   return MHD_OK;
@@ -714,12 +731,16 @@ int mhd_step_host(mhd_ctx* c, const double* U_in, double* U_out, double dt, doub
     if (rc != MHD_OK) return rc;
     CK(c, cudaEventRecord(c->xev[1 + k], c->xfer));
     CK(c, cudaStreamWaitEvent(c->stream, c->xev[1 + k], 0));
-    if (need_lam) {
+    if (need_lam) {  // pass 1 of the wave-speed maximum, slab by slab
       ProfScope ps(c, 3);
-      CK(c, mhd::launch_max_speed_range<double>(c->grid, A, z0 * plane, z1 * plane,
-                                                &c->scal->lam_bits, c->scal->floor_cnt,
-                                                c->stream));
+      CK(c, mhd::launch_speed_estimate(c->grid, A, z0 * plane, z1 * plane, &c->scal->est_bits,
+                                       c->stream));
     }
+  }
+  if (need_lam) {  // pass 2 once the whole state is on the device
+    ProfScope ps(c, 3);
+    CK(c, mhd::launch_speed_exact(c->grid, A, &c->scal->est_bits, &c->scal->lam_bits,
+                                  c->scal->floor_cnt, c->stream));
   }
   c->lam_valid = need_lam;
   HostOut ho{U_out, nz / 2};

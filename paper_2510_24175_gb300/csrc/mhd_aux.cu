@@ -28,7 +28,7 @@ template Phys<float> make_phys<float>(const Grid&);
 // A non-finite or non-positive dt / c_h sets status bit 1 and turns the step
 // into a no-op (dt = 0, damping 1), so the state is preserved for inspection.
 __global__ void prep_kernel(const PrepArgs a, StepScalars* sc, unsigned long long* lam_bits,
-                            unsigned int* status) {
+                            unsigned int* est_bits, unsigned int* status) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double lam = __longlong_as_double((long long)*lam_bits);
   double ch = a.ch_req > 0.0 ? a.ch_req : lam;
@@ -51,82 +51,150 @@ __global__ void prep_kernel(const PrepArgs a, StepScalars* sc, unsigned long lon
   sc->t = t + dt;
   sc->lam = lam;
   sc->steps += 1.0;
-  *lam_bits = 0ull;  // the stage-2 epilogue accumulates lambda of the new state
+  *lam_bits = 0ull;  // the last stage accumulates lambda of the new state
+  *est_bits = 0u;
 }
 
 cudaError_t launch_prep(const PrepArgs& a, StepScalars* sc, unsigned long long* lam_bits,
-                        unsigned int* status, cudaStream_t stream) {
-  prep_kernel<<<1, 32, 0, stream>>>(a, sc, lam_bits, status);
+                        unsigned int* est_bits, unsigned int* status, cudaStream_t stream) {
+  prep_kernel<<<1, 32, 0, stream>>>(a, sc, lam_bits, est_bits, status);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------- max wave speed --
-template <class T>
-__global__ void __launch_bounds__(256) max_speed_kernel(const T* __restrict__ U, long long ncell,
-                                                        long long c0, long long c1, int ndim,
-                                                        Phys<T> ph, unsigned long long* lam_bits,
-                                                        unsigned long long* floor_cnt) {
-  unsigned flags = 0;
-  double lam = 0.0;
-  for (long long c = c0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; c < c1;
-       c += (long long)gridDim.x * blockDim.x) {
-    T u[kNV];
+// Block maximum of a non-negative (or NaN) double per thread; thread 0 gets it.
+__device__ __forceinline__ double block_speed_max(double lam) {
 #pragma unroll
-    for (int k = 0; k < kNV; ++k) u[k] = U[k * ncell + c];
-    const double s = (double)cell_max_speed(u, ph, ndim, flags);
-    lam = nan_max(lam, s);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double other = __shfl_xor_sync(0xffffffffu, lam, o);
-    lam = nan_max(lam, other);
-  }
+  for (int o = 16; o > 0; o >>= 1) lam = nan_max(lam, __shfl_xor_sync(0xffffffffu, lam, o));
   __shared__ double w[8];
   if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = lam;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double m = w[0];
-    for (int i = 1; i < (int)(blockDim.x >> 5); ++i)
-      m = nan_max(m, w[i]);
-    unsigned long long bits = (unsigned long long)__double_as_longlong(m);
-    if (m != m) bits = 0x7ff8000000000000ull;
-    atomicMax(lam_bits, bits);
+  double m = w[0];
+  if (threadIdx.x == 0)
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = nan_max(m, w[i]);
+  return m;
+}
+
+// FP32 states: every cell's speed.
+__global__ void __launch_bounds__(256) max_speed_f32_kernel(const float* __restrict__ U,
+                                                            long long ncell, int ndim,
+                                                            Phys<float> ph,
+                                                            unsigned long long* lam_bits,
+                                                            unsigned long long* floor_cnt) {
+  unsigned flags = 0;
+  SpeedMax<float> smax(ph);
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    float u[kNV];
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) u[k] = U[k * ncell + c];
+    smax.update(u, true, ph, ndim, flags);
   }
+  const double m = block_speed_max(smax.value());
+  if (threadIdx.x == 0) SpeedMax<float>::publish(m, lam_bits, nullptr);
   if (flags & kFloorRho) atomicAdd(&floor_cnt[0], 1ull);
   if (flags & kFloorP) atomicAdd(&floor_cnt[1], 1ull);
 }
 
-template <class T>
-cudaError_t launch_max_speed(const Grid& g, const T* U, unsigned long long* lam_bits,
-                             unsigned long long* floor_cnt, cudaStream_t stream) {
-  cudaError_t e = cudaMemsetAsync(lam_bits, 0, sizeof(unsigned long long), stream);
-  if (e != cudaSuccess) return e;
-  return launch_max_speed_range<T>(g, U, 0, g.ncell, lam_bits, floor_cnt, stream);
+// FP64 pass 1 over cells [c0, c1): the maximum reliable FP32 estimate.
+__global__ void __launch_bounds__(256) speed_estimate_kernel(const double* __restrict__ U,
+                                                             long long ncell, long long c0,
+                                                             long long c1, int ndim,
+                                                             Phys<double> ph,
+                                                             unsigned int* est_bits) {
+  unsigned flags = 0;
+  SpeedMax<double> smax(ph);
+  for (long long c = c0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; c < c1;
+       c += (long long)gridDim.x * blockDim.x) {
+    double u[kNV];
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) u[k] = U[k * ncell + c];
+    smax.update(u, true, ph, ndim, flags);
+  }
+  const double m = block_speed_max(smax.value());
+  if (threadIdx.x == 0) SpeedMax<double>::publish(m, nullptr, est_bits);
+}
+
+// FP64 pass 2: the exact speed of every cell whose estimate reaches 0.999 of
+// the maximum reliable estimate or is not reliable (mhd_physics.cuh).  The
+// trip count is warp-uniform so that the FP64 evaluation can sit behind a
+// warp-uniform branch.
+__global__ void __launch_bounds__(256) speed_exact_kernel(const double* __restrict__ U,
+                                                          long long ncell, int ndim,
+                                                          Phys<double> ph,
+                                                          const unsigned int* est_bits,
+                                                          unsigned long long* lam_bits,
+                                                          unsigned long long* floor_cnt) {
+  unsigned flags = 0;
+  const SpeedEstimator estimate(ph);
+  const float thr = 0.999f * __uint_as_float(*est_bits);
+  double lam = 0.0;
+  const long long lane = threadIdx.x & 31;
+  for (long long w = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane); w < ncell;
+       w += (long long)gridDim.x * blockDim.x) {
+    const long long c = w + lane;
+    const bool valid = c < ncell;
+    double u[kNV];
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) u[k] = valid ? U[k * ncell + c] : 0.0;
+    bool ok = true;
+    const float e = estimate(u, ndim, ok);
+    const bool cand = valid && (!ok || e >= thr);
+    if (__any_sync(0xffffffffu, cand)) {
+      if (cand) lam = nan_max(lam, cell_max_speed(u, ph, ndim, flags));
+    }
+  }
+  const double m = block_speed_max(lam);
+  if (threadIdx.x == 0) SpeedMax<float>::publish(m, lam_bits, nullptr);
+  if (flags & kFloorRho) atomicAdd(&floor_cnt[0], 1ull);
+  if (flags & kFloorP) atomicAdd(&floor_cnt[1], 1ull);
+}
+
+static unsigned speed_blocks(const Grid& g, long long n) {
+  long long blocks = (n + 255) / 256;
+  const long long cap = (long long)g.nsm * 8;
+  if (blocks > cap) blocks = cap;
+  return (unsigned)(blocks < 1 ? 1 : blocks);
+}
+
+cudaError_t launch_speed_estimate(const Grid& g, const double* U, long long c0, long long c1,
+                                  unsigned int* est_bits, cudaStream_t stream) {
+  if (c0 < 0 || c1 > g.ncell || c0 >= c1) return cudaErrorInvalidValue;
+  speed_estimate_kernel<<<speed_blocks(g, c1 - c0), 256, 0, stream>>>(
+      U, g.ncell, c0, c1, g.ndim, make_phys<double>(g), est_bits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_speed_exact(const Grid& g, const double* U, const unsigned int* est_bits,
+                               unsigned long long* lam_bits, unsigned long long* floor_cnt,
+                               cudaStream_t stream) {
+  speed_exact_kernel<<<speed_blocks(g, g.ncell), 256, 0, stream>>>(
+      U, g.ncell, g.ndim, make_phys<double>(g), est_bits, lam_bits, floor_cnt);
+  return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t launch_max_speed_range(const Grid& g, const T* U, long long c0, long long c1,
-                                   unsigned long long* lam_bits, unsigned long long* floor_cnt,
-                                   cudaStream_t stream) {
-  if (c0 < 0 || c1 > g.ncell || c0 >= c1) return cudaErrorInvalidValue;
-  long long blocks = (c1 - c0 + 255) / 256;
-  const long long cap = (long long)g.nsm * 8;
-  if (blocks > cap) blocks = cap;
-  if (blocks < 1) blocks = 1;
-  max_speed_kernel<T><<<(unsigned)blocks, 256, 0, stream>>>(U, g.ncell, c0, c1, g.ndim,
-                                                            make_phys<T>(g), lam_bits, floor_cnt);
-  return cudaGetLastError();
+cudaError_t launch_max_speed(const Grid& g, const T* U, unsigned long long* lam_bits,
+                             unsigned int* est_bits, unsigned long long* floor_cnt,
+                             cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(lam_bits, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return e;
+  if constexpr (sizeof(T) == 8) {
+    if (!est_bits) return cudaErrorInvalidValue;
+    e = cudaMemsetAsync(est_bits, 0, sizeof(unsigned int), stream);
+    if (e == cudaSuccess) e = launch_speed_estimate(g, U, 0, g.ncell, est_bits, stream);
+    if (e == cudaSuccess) e = launch_speed_exact(g, U, est_bits, lam_bits, floor_cnt, stream);
+    return e;
+  } else {
+    max_speed_f32_kernel<<<speed_blocks(g, g.ncell), 256, 0, stream>>>(
+        U, g.ncell, g.ndim, make_phys<float>(g), lam_bits, floor_cnt);
+    return cudaGetLastError();
+  }
 }
 template cudaError_t launch_max_speed<double>(const Grid&, const double*, unsigned long long*,
-                                              unsigned long long*, cudaStream_t);
+                                              unsigned int*, unsigned long long*, cudaStream_t);
 template cudaError_t launch_max_speed<float>(const Grid&, const float*, unsigned long long*,
-                                             unsigned long long*, cudaStream_t);
-template cudaError_t launch_max_speed_range<double>(const Grid&, const double*, long long,
-                                                    long long, unsigned long long*,
-                                                    unsigned long long*, cudaStream_t);
-template cudaError_t launch_max_speed_range<float>(const Grid&, const float*, long long,
-                                                   long long, unsigned long long*,
-                                                   unsigned long long*, cudaStream_t);
+                                             unsigned int*, unsigned long long*, cudaStream_t);
 
 // ------------------------------------------------------ conservation sums --
 // Pass 1: CTA b sums the contiguous cell range [b*chunk, (b+1)*chunk) of the

@@ -18,7 +18,7 @@ struct Scalars {  // device block at the start of the scalar region
   unsigned long long lam_bits;
   unsigned long long floor_cnt[2];
   unsigned int status;
-  unsigned int pad;
+  unsigned int est_bits;  // FP64: max reliable FP32 speed estimate (FP32 bits)
   double sums[8];
   unsigned long long aux_bits;  // scratch max (face divergence)
 };

@@ -380,8 +380,8 @@ int mhd_ensemble_step(mhd_ensemble* e, int nsteps) {
     if (!e->ctx[b]->have_state) return efail(e, MHD_ERR_STATE, "box %d has no state", b);
     if (!e->lam_ok[b]) {
       ECK(e, mhd::launch_max_speed<float>(e->ctx[b]->grid, static_cast<const float*>(e->ctx[b]->Ua),
-                                          &e->d[b].lam_bits[e->cur[b]], &e->d[b].floor_cnt[0],
-                                          e->stream));
+                                          &e->d[b].lam_bits[e->cur[b]], nullptr,
+                                          &e->d[b].floor_cnt[0], e->stream));
       e->lam_ok[b] = true;
     }
   }

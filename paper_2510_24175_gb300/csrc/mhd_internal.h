@@ -40,7 +40,8 @@ cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T*
                          const StepScalars* sc, unsigned long long* lam_bits,
                          unsigned long long* floor_cnt, cudaStream_t stream,
                          double a_n = 0.5, double a_w = 0.5, const T* const* bw = nullptr,
-                         T* ctf = nullptr, int zlo = 0, int zhi = -1, int tz = 0);
+                         T* ctf = nullptr, int zlo = 0, int zhi = -1, int tz = 0,
+                         unsigned int* est_bits = nullptr);
 
 // Constrained-transport kernels (mhd_ct.cu); face / edge arrays are three
 // planes of ncell values, b_d on each cell's lower d-face.
@@ -75,17 +76,25 @@ struct PrepArgs {
   int active[3];
 };
 cudaError_t launch_prep(const PrepArgs& a, StepScalars* sc, unsigned long long* lam_bits,
-                        unsigned int* status, cudaStream_t stream);
+                        unsigned int* est_bits, unsigned int* status, cudaStream_t stream);
 
+// Maximum wave speed of a state into lam_bits (FP64 bits; both words cleared
+// first).  FP32: every cell evaluated.  FP64: the two passes of
+// mhd_physics.cuh (estimates into est_bits, then the exact evaluation of the
+// cells that can hold the maximum).
 template <class T>
 cudaError_t launch_max_speed(const Grid& g, const T* U, unsigned long long* lam_bits,
-                             unsigned long long* floor_cnt, cudaStream_t stream);
-// The same reduction over cells [c0, c1) only, accumulated into lam_bits
-// (not cleared first).
-template <class T>
-cudaError_t launch_max_speed_range(const Grid& g, const T* U, long long c0, long long c1,
-                                   unsigned long long* lam_bits, unsigned long long* floor_cnt,
-                                   cudaStream_t stream);
+                             unsigned int* est_bits, unsigned long long* floor_cnt,
+                             cudaStream_t stream);
+// FP64 pass 1 over cells [c0, c1): the maximum reliable estimate, accumulated
+// into est_bits (not cleared first).
+cudaError_t launch_speed_estimate(const Grid& g, const double* U, long long c0, long long c1,
+                                  unsigned int* est_bits, cudaStream_t stream);
+// FP64 pass 2 over all cells: the exact maximum of the cells whose estimate
+// reaches 0.999 of *est_bits or is not reliable, accumulated into lam_bits.
+cudaError_t launch_speed_exact(const Grid& g, const double* U, const unsigned int* est_bits,
+                               unsigned long long* lam_bits, unsigned long long* floor_cnt,
+                               cudaStream_t stream);
 
 template <class T>
 cudaError_t launch_sums(const Grid& g, const T* U, double* partials, int nblocks,

@@ -305,6 +305,128 @@ MHD_HD T cell_max_speed(const T u[kNV], const Phys<T>& ph, int ndim,
   return lam;
 }
 
+#ifdef __CUDACC__
+// ---------------------------------------------------------------------------
+// Maximum wave speed of a state (cell_max_speed over all cells): the
+// last-stage epilogue and the wave-speed kernels.  FP32 evaluates every cell.
+// FP64 works in two passes.  Pass 1 (the epilogue, or a kernel over a state)
+// takes an FP32 estimate of each cell's speed from FP32 images of its
+// conservative variables (integer-pipe truncation, error < 2^-23 each)
+// computed on the FP32 pipe, and the maximum M of the reliable estimates goes
+// to one word (FP32 bits, atomicMax).  Reliable means: every input is 0 or
+// within 2^-100 <= |x| < 2^100, rho and p are at least twice their floors (no
+// floor acts), the internal energy is at least 1/50 of E and each
+// direction's discriminant a^2 - 4 g c_an^2 at least 1e-4 a^2 (bounded
+// cancellation: the FP32 errors of E - kin - |B|^2/2 and of the discriminant,
+// a few 2^-24 of E and of a^2, are amplified at most 50-fold and, through the
+// square root, to at most ~3e-5 of c_f^2); the estimate's relative error is
+// then below 1e-4 (largest seen on 8 M random states pushed to the guard
+// edges: 3.3e-6).  Pass 2
+// (speed_exact_kernel) evaluates the FP64 speed of every cell whose estimate
+// reaches 0.999 M or is not reliable.  The cell holding the exact maximum
+// Lambda has an estimate >= Lambda (1 - 1e-4) when reliable, and
+// M <= Lambda (1 + 1e-4), so it is always evaluated: the result is the exact
+// FP64 maximum (floors and NaNs included, which are never screened out).
+// Pass 2's FP64 evaluation sits behind a warp-uniform branch, so warps
+// without a candidate issue no FP64 work for it.
+
+// FP32 image of a double on the integer pipe: sign, rebiased exponent, top 23
+// mantissa bits.  Clears ok unless x is 0 or 2^-100 <= |x| < 2^100.
+__device__ __forceinline__ float f32_image(double x, bool& ok) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const unsigned mag = hi & 0x7fffffffu;
+  const bool zero = (mag | lo) == 0u;
+  ok = ok && (zero || ((mag >> 20) - 923u) < 200u);
+  const unsigned fb = (hi & 0x80000000u) | (((mag - (896u << 20)) << 3) | (lo >> 29));
+  return zero ? 0.0f : __uint_as_float(fb);
+}
+
+// FP32 estimate of cell_max_speed for an FP64 conservative cell (see above).
+struct SpeedEstimator {
+  float gm1, gamma, rho2, p2;  // FP32 images of the physics constants
+  __device__ explicit SpeedEstimator(const Phys<double>& ph) {
+    bool ok = true;
+    gm1 = f32_image(ph.gm1, ok);
+    gamma = f32_image(ph.gamma, ok);
+    rho2 = 2.0f * f32_image(ph.rho_floor, ok);
+    p2 = 2.0f * f32_image(ph.p_floor, ok);
+    if (!ok) rho2 = __int_as_float(0x7f800000);  // never reliable
+  }
+  __device__ __forceinline__ float operator()(const double u[kNV], int ndim, bool& ok) const {
+    float f[kNV];
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) f[k] = f32_image(u[k], ok);
+    const float r = f[kRHO];
+    ok = ok && r >= rho2;
+    const float ri = __frcp_rn(r);
+    const float v[3] = {f[kVX] * ri, f[kVY] * ri, f[kVZ] * ri};
+    const float kin = 0.5f * (f[kVX] * v[0] + f[kVY] * v[1] + f[kVZ] * v[2]);
+    const float b2 = f[kBX] * f[kBX] + f[kBY] * f[kBY] + f[kBZ] * f[kBZ];
+    const float eint = f[kPRS] - kin - 0.5f * b2;
+    ok = ok && eint >= 0.02f * f[kPRS];
+    const float pr = gm1 * eint;
+    ok = ok && pr >= p2;
+    const float g = gamma * pr * ri;
+    const float a = b2 * ri + g;
+    float lam = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (d < ndim) {
+        const float bd = f[kBX + d];
+        const float disc = a * a - 4.0f * g * (bd * bd * ri);
+        ok = ok && disc >= 1e-4f * a * a;
+        lam = fmaxf(lam, fabsf(v[d]) + sqrtf(0.5f * (a + sqrtf(fmaxf(disc, 0.0f)))));
+      }
+    }
+    return lam;
+  }
+};
+
+// Per-thread accumulator of the epilogue and the wave-speed kernels: the
+// exact FP32 maximum, or (FP64) the maximum of the reliable estimates.
+template <class T>
+struct SpeedMax;
+
+template <>
+struct SpeedMax<float> {
+  float lam = 0.0f;
+  __device__ explicit SpeedMax(const Phys<float>&) {}
+  __device__ __forceinline__ void update(const float u[kNV], bool valid, const Phys<float>& ph,
+                                         int ndim, unsigned& flags) {
+    if (valid) lam = nan_max(lam, cell_max_speed(u, ph, ndim, flags));
+  }
+  __device__ __forceinline__ double value() const { return (double)lam; }
+  // one thread per CTA: the CTA's maximum m into the state's wave-speed word
+  __device__ __forceinline__ static void publish(double m, unsigned long long* lam_bits,
+                                                 unsigned int*) {
+    unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+    if (is_nan(m)) bits = 0x7ff8000000000000ull;
+    atomicMax(lam_bits, bits);
+  }
+};
+
+template <>
+struct SpeedMax<double> {
+  float est = 0.0f;
+  SpeedEstimator estimate;
+  __device__ explicit SpeedMax(const Phys<double>& ph) : estimate(ph) {}
+  __device__ __forceinline__ void update(const double u[kNV], bool valid, const Phys<double>&,
+                                         int ndim, unsigned&) {
+    bool ok = true;
+    const float e = estimate(u, ndim, ok);
+    if (valid && ok) est = fmaxf(est, e);
+  }
+  __device__ __forceinline__ double value() const { return (double)est; }
+  // the CTA's maximum estimate (a non-negative FP32 value) into the estimate
+  // word: non-negative floats order like their bit patterns
+  __device__ __forceinline__ static void publish(double m, unsigned long long*,
+                                                 unsigned int* est_bits) {
+    atomicMax(est_bits, __float_as_uint((float)m));
+  }
+};
+#endif
+
 // Limited slope (van Leer 1977): 0 when the one-sided differences disagree in
 // sign; minmod = smaller magnitude; MC = min(2|dm|, 2|dp|, |dm+dp|/2).
 template <class T>

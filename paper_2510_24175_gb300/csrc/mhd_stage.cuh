@@ -53,7 +53,8 @@ struct StageParams {
   T a_n, a_w;     // combining stages: out = a_n U^n + a_w (W + dt L(W))
   Phys<T> ph;
   const StepScalars* sc;
-  unsigned long long* lam_bits;   // stage 2: max wave speed as FP64 bits
+  unsigned long long* lam_bits;   // stage 2: max wave speed as FP64 bits (FP32 path)
+  unsigned int* est_bits;         // stage 2, FP64: max reliable FP32 speed estimate
   unsigned long long* floor_cnt;  // [2] floor activations
   // constrained transport (kernels instantiated with CT = true)
   const T* bw[3];  // the stage input's face field: b_d on each cell's lower d-face
@@ -328,7 +329,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
     __syncthreads();
   }
 
-  T lam = T(0);
+  SpeedMax<T> smax(ph);  // last stage: the new state's maximum wave speed
   for (int k = z0; k < z1; ++k) {
     // ---- A: loads ---------------------------------------------------------
     for (int it = tid; it < G::NLOAD; it += NT) {
@@ -462,9 +463,12 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
     // ---- D: right-hand side and RK combination (column owners) -------------
     if (owner) {
       const int gx = x0 + ocol, gy = y0 + orow;
-      if (gx < nx && gy < ny) {
+      const bool valid = gx < nx && gy < ny;
+      T unew[kNV];
+#pragma unroll
+      for (int q = 0; q < kNV; ++q) unew[q] = T(0);
+      if (valid) {
         const long long off = (long long)k * p.sz + (long long)gy * p.sy + gx;
-        T unew[kNV];
 #pragma unroll
         for (int q = 0; q < kNV; ++q) {
           const T* fx = Fx + q * G::FXN + orow * (TX + 1) + ocol;
@@ -493,18 +497,17 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
 #pragma unroll
           for (int q = 0; q < kNV; ++q) p.uout[q * p.sv + off] = unew[q];
         }
-        if constexpr (STAGE == 2 && !CT) {
-          const int ndim = 1 + (G::GY > 0) + (ZACT ? 1 : 0);
-          const T s = cell_max_speed(unew, ph, ndim, flags);
-          lam = nan_max(lam, s);
-        }
+      }
+      if constexpr (STAGE == 2 && !CT) {  // every lane of the (whole) owner warps
+        const int ndim = 1 + (G::GY > 0) + (ZACT ? 1 : 0);
+        smax.update(unew, valid, ph, ndim, flags);
       }
     }
   }
 
   if constexpr (STAGE == 2 && !CT) {
     // block max of the wave speed -> one FP64-bit atomicMax per CTA
-    double l = (double)lam;
+    double l = smax.value();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const double other = __shfl_xor_sync(0xffffffffu, l, o);
@@ -517,9 +520,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
       double m = wmax[0];
       for (int w = 1; w < NW; ++w)
         m = nan_max(m, wmax[w]);
-      unsigned long long bits = (unsigned long long)__double_as_longlong(m);
-      if (is_nan(m)) bits = 0x7ff8000000000000ull;
-      atomicMax(p.lam_bits, bits);
+      SpeedMax<T>::publish(m, p.lam_bits, p.est_bits);
     }
   }
   if (flags) {

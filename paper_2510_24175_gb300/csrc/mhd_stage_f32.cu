@@ -5,6 +5,7 @@ namespace mhd {
 template cudaError_t launch_stage<float>(const Grid&, int, const float*, const float*, float*,
                                          const StepScalars*, unsigned long long*,
                                          unsigned long long*, cudaStream_t, double, double,
-                                         const float* const*, float*, int, int, int);
+                                         const float* const*, float*, int, int, int,
+                                          unsigned int*);
 template void stage_shape<float>(const Grid&, size_t*, int*, int*);
 }  // namespace mhd

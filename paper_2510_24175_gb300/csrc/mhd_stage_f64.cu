@@ -5,6 +5,7 @@ namespace mhd {
 template cudaError_t launch_stage<double>(const Grid&, int, const double*, const double*, double*,
                                           const StepScalars*, unsigned long long*,
                                           unsigned long long*, cudaStream_t, double, double,
-                                          const double* const*, double*, int, int, int);
+                                          const double* const*, double*, int, int, int,
+                                          unsigned int*);
 template void stage_shape<double>(const Grid&, size_t*, int*, int*);
 }  // namespace mhd

@@ -82,7 +82,8 @@ template <class T>
 cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T* uout,
                          const StepScalars* sc, unsigned long long* lam_bits,
                          unsigned long long* floor_cnt, cudaStream_t stream, double a_n,
-                         double a_w, const T* const* bw, T* ctf, int zlo, int zhi, int tz) {
+                         double a_w, const T* const* bw, T* ctf, int zlo, int zhi, int tz,
+                         unsigned int* est_bits) {
   StageParams<T> p;
   p.a_n = T(a_n);
   p.a_w = T(a_w);
@@ -106,6 +107,10 @@ cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T*
   p.ph = make_phys<T>(g);
   p.sc = sc;
   p.lam_bits = lam_bits;
+  p.est_bits = est_bits;
+  // the FP64 last stage publishes the maximum speed estimate (speed_exact
+  // finishes the maximum); it needs the estimate word
+  if (sizeof(T) == 8 && stage == 2 && !ctf && !est_bits) return cudaErrorInvalidValue;
   p.floor_cnt = floor_cnt;
   for (int d = 0; d < 3; ++d) p.bw[d] = bw ? bw[d] : nullptr;
   p.ctf = ctf;

@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
     __syncthreads();
   }
 
-  T lam = T(0);
+  SpeedMax<T> smax(ph);  // last stage: the new state's maximum wave speed
   for (int k = z0; k < z1; ++k) {
     // ---- A: loads ---------------------------------------------------------
     for (int it = tid; it < G::NLOAD; it += NT) {
@@ -388,9 +388,12 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
     // ---- D: right-hand side and Runge-Kutta combination --------------------
     if (owner) {
       const int gx = x0 + ocol, gy = y0 + orow;
-      if (gx < nx && gy < ny) {
+      const bool valid = gx < nx && gy < ny;
+      T unew[kNV];
+#pragma unroll
+      for (int q = 0; q < kNV; ++q) unew[q] = T(0);
+      if (valid) {
         const long long off = (long long)k * p.sz + (long long)gy * p.sy + gx;
-        T unew[kNV];
 #pragma unroll
         for (int q = 0; q < kNV; ++q) {
           const T* fx = Fx + q * G::FXN + orow * (TX + 1) + ocol;
@@ -419,16 +422,16 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
 #pragma unroll
           for (int q = 0; q < kNV; ++q) p.uout[q * p.sv + off] = unew[q];
         }
-        if constexpr (STAGE == 2 && !CT) {
-          const int ndim = 1 + (G::GY > 0) + (ZACT ? 1 : 0);
-          lam = nan_max(lam, cell_max_speed(unew, ph, ndim, flags));
-        }
+      }
+      if constexpr (STAGE == 2 && !CT) {  // every lane of the (whole) owner warps
+        const int ndim = 1 + (G::GY > 0) + (ZACT ? 1 : 0);
+        smax.update(unew, valid, ph, ndim, flags);
       }
     }
   }
 
   if constexpr (STAGE == 2 && !CT) {
-    double l = (double)lam;
+    double l = smax.value();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) l = nan_max(l, __shfl_xor_sync(0xffffffffu, l, o));
     __syncthreads();
@@ -437,9 +440,7 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
     if (tid == 0) {
       double m = wmax[0];
       for (int w = 1; w < NW; ++w) m = nan_max(m, wmax[w]);
-      unsigned long long bits = (unsigned long long)__double_as_longlong(m);
-      if (m != m) bits = 0x7ff8000000000000ull;
-      atomicMax(p.lam_bits, bits);
+      SpeedMax<T>::publish(m, p.lam_bits, p.est_bits);
     }
   }
   if (flags) {
