@@ -9,10 +9,14 @@ Metric: zone-updates/s = interior cells x steps / time.  The state (1.2 GB
 per array) is far larger than L2 (129 MB), so no flush is needed between
 steps.
 
-Also reported on the same line: the FP32-bulk sweep (turbulent box 512^3),
-per-kernel CUDA-event times, roofline fractions against MEASURED_PEAKS.json,
-end-to-end throughput through the C ABI with pinned host buffers, SM clocks
-sampled during the timed region, and the CPU oracle timed on the host cores.
+Also reported on the same line: the FP32-bulk sweep (turbulent box 512^3)
+and FP64 on that grid and on the FP64 workload's grid (same-grid precision
+ratios), per-kernel CUDA-event times, roofline fractions against
+MEASURED_PEAKS.json, end-to-end throughput through the C ABI with pinned host
+buffers, the paper's WENO-Z + SSP-RK3 schemes (GLM and constrained
+transport), the adjoint/forward step-time ratio, the batched ensemble, the
+1-D Brio-Wu run to t = 0.1 as GPU wall time, SM clocks sampled during the
+timed region, and the CPU oracle timed on the host cores.
 
 --impl reference times the CPU FP64 oracle (there is no runnable reference
 code for this paper) on bounded samples of the same workload.
@@ -78,6 +82,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-brio", action="store_true", help="skip the Brio-Wu latency line")
     ap.add_argument("--no-paper-scheme", action="store_true",
                     help="skip the WENO-Z + SSP-RK3 throughput lines")
     return ap.parse_args()
@@ -420,6 +425,62 @@ def main():
         del ss
         torch.cuda.empty_cache()
 
+    # ---- FP64 on the FP32 sweep's grid (turbulent box 512^3) ---------------
+    fp64_512 = None
+    if not args.no_fp32:
+        pbt = inputs.turbulent_box(args.n32)
+        st = m.MHD(m.Config.from_problem(pbt, precision=m.MHD_FP64))
+        Vt = torch.from_numpy(pbt.prim()).cuda()
+        st.set_state(Vt, kind=m.MHD_PRIM)
+        del Vt
+        for _ in range(W):
+            st.step()
+        st.step_info()
+        Kt = max(3, min(K, 5))
+        mst, proft = timed_steps(st, torch, Kt, dist, world)
+        st.step_info()
+        fp64_512 = {"workload": f"turbulent_box_{args.n32}^3_fp64",
+                    "value": world * pbt.ncell * Kt / (mst * 1e-3), "unit": "zone-updates/s",
+                    "steps": Kt, "ms_per_step": mst / Kt}
+        launches += sum(c for c, _ in proft.values())
+        del st
+        torch.cuda.empty_cache()
+
+    # ---- Brio-Wu 1024 to t = 0.1 (latency-bound 1-D case): GPU wall time ----
+    brio = None
+    if not args.no_brio:
+        pbb = inputs.brio_wu(1024)
+        sb = m.MHD(m.Config.from_problem(pbb))
+        Vb = pbb.prim()
+        sb.set_state(torch.from_numpy(Vb).cuda(), kind=m.MHD_PRIM)
+        nb = 0
+        while sb.step_info()["t"] < pbb.t_end and nb < 100000:  # untimed: count the steps
+            sb.step()
+            nb += 1
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        times = {}
+        for mode in ("single", "graph", "graph"):  # the second graph run is timed
+            sb.set_state(torch.from_numpy(Vb).cuda(), kind=m.MHD_PRIM)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            if mode == "single":
+                for _ in range(nb):
+                    sb.step()
+            else:
+                sb.step_n(nb)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times[mode] = e0.elapsed_time(e1)
+        brio = {"workload": "brio_wu_1024_fp64_to_t_0.1", "steps": nb,
+                "t_reached": sb.step_info()["t"], "gpu_ms": times["graph"],
+                "gpu_ms_single_launches": times["single"],
+                "api": "mhd_step_n (the steps replayed from one captured CUDA graph)",
+                "note": "state set from the device; the oracle's time for the same run is in "
+                        "cpu_baseline"}
+        del sb
+        torch.cuda.empty_cache()
+
     # ---- the paper's own schemes, OT 256^3: WENO-Z + SSP-RK3 with GLM ------
     # ---- (its strong-scaling runs) or constrained transport (weak scaling) --
     paper_scheme = None
@@ -562,6 +623,16 @@ def main():
     cpu = None
     if not args.no_cpu and world == 1:
         cpu = cpu_oracle_sample()
+        if brio is not None:  # the oracle on the same Brio-Wu run, one process
+            import oracle as orc
+            pbb = inputs.brio_wu(1024)
+            g = orc.Grid(n=pbb.n, dx=pbb.dx, gamma=pbb.gamma, glm_alpha=pbb.glm_alpha,
+                         limiter=pbb.limiter, bc=pbb.bc, cfl=pbb.cfl)
+            U0 = orc.prim_to_cons(pbb.prim(), pbb.gamma)
+            t0 = time.perf_counter()
+            r = orc.run(U0, g, 100000, t_end=pbb.t_end)
+            cpu["brio_wu_1024_oracle_s"] = time.perf_counter() - t0
+            cpu["brio_wu_1024_oracle_t"] = r.t
 
     line = {
         "metric": "zone-updates/s", "value": value, "unit": "zone-updates/s",
@@ -578,6 +649,10 @@ def main():
         "fp32": fp32,
         "fp32_same_grid": fp32_same,
         "fp32_over_fp64_same_grid": (fp32_same["value"] / value) if fp32_same else None,
+        "fp64_turbulent_512": fp64_512,
+        "fp32_over_fp64_turbulent_512": (fp32["value"] / fp64_512["value"])
+        if (fp32 and fp64_512) else None,
+        "brio_wu": brio,
         "paper_scheme_wenoz_rk3": paper_scheme,
         "adjoint": adjoint,
         "ensemble": ensemble,

@@ -158,6 +158,15 @@ int mhd_dt(mhd_ctx* ctx, double* dt, double* ch);
  * synchronise: dt and c_h stay on the device (see mhd_step_info). */
 int mhd_step(mhd_ctx* ctx, double dt, double ch);
 
+/* nsteps steps with the CFL time step and c_h = lambda, as nsteps calls of
+ * mhd_step(ctx, 0, 0) (same results), launched as one CUDA graph: the steps'
+ * launches are captured on a private stream the first time a given nsteps
+ * is asked for (again when nsteps changes) and the graph is replayed on the
+ * context's stream, so a small grid pays one launch instead of four per
+ * step.  With profiling on (mhd_profile_enable) the steps are launched one
+ * by one.  Asynchronous. */
+int mhd_step_n(mhd_ctx* ctx, int nsteps);
+
 /* One step of a state that lives in host memory: U_in (host, float64,
  * conservative, [9][nz][ny][nx]) becomes the context's state, is advanced by
  * mhd_step(dt, ch), and the result is copied to U_out (host; may be U_in).

@@ -35,7 +35,7 @@ MHD_DIVB_GLM, MHD_DIVB_CT = 0, 1
 
 EXPORTED = ["mhd_config_default", "mhd_workspace_bytes", "mhd_create", "mhd_set_stream",
             "mhd_set_state", "mhd_get_state", "mhd_dt", "mhd_step", "mhd_step_host",
-            "mhd_step_info",
+            "mhd_step_n", "mhd_step_info",
             "mhd_counters", "mhd_conserved_sums", "mhd_flux_batch", "mhd_adjoint_step",
             "mhd_profile_enable", "mhd_profile_read", "mhd_conserved_sums_noalloc",
             "mhd_last_error", "mhd_destroy", "mhd_set_face_field", "mhd_get_face_field",
@@ -88,6 +88,7 @@ def lib():
         L.mhd_dt.argtypes = [vp, dp, dp]
         L.mhd_step.argtypes = [vp, d, d]
         L.mhd_step_host.argtypes = [vp, vp, vp, d, d]
+        L.mhd_step_n.argtypes = [vp, i]
         L.mhd_step_info.argtypes = [vp, dp]
         L.mhd_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
         L.mhd_conserved_sums.argtypes = [vp, dp]
@@ -192,6 +193,10 @@ def mhd_dt(ctx):
 
 def mhd_step(ctx, dt: float = 0.0, ch: float = 0.0):
     _check(lib().mhd_step(ctx, float(dt), float(ch)), ctx, "mhd_step")
+
+
+def mhd_step_n(ctx, nsteps: int):
+    _check(lib().mhd_step_n(ctx, int(nsteps)), ctx, "mhd_step_n")
 
 
 def mhd_step_host(ctx, U_in, U_out, dt: float = 0.0, ch: float = 0.0):
@@ -360,6 +365,10 @@ class MHD:
 
     def step(self, dt: float = 0.0, ch: float = 0.0):
         mhd_step(self.ctx, dt, ch)
+
+    def step_n(self, nsteps: int):
+        """nsteps CFL steps launched as one captured CUDA graph (mhd_step_n)."""
+        mhd_step_n(self.ctx, nsteps)
 
     def step_host(self, U_in, U_out, dt: float = 0.0, ch: float = 0.0):
         """One step of a host-resident state (mhd_step_host): U_in, U_out are

@@ -363,8 +363,22 @@ int mhd_create(const mhd_config* cfg, void* d_workspace, size_t bytes, void* str
     gh.n[2] = (gh.n[2] + 1) / 2;
     c->tz_half = choose_tz(gh, per_sm < 1 ? 1 : per_sm, ty);
   }
+  {
+    // kernel attributes now, so that no later launch (a captured one in
+    // particular) needs the driver call
+    const bool ct = cfg->divb == MHD_DIVB_CT;
+    const cudaError_t pe = c->esize == 8 ? mhd::prepare_stage_kernels<double>(c->grid, ct)
+                                         : mhd::prepare_stage_kernels<float>(c->grid, ct);
+    if (pe != cudaSuccess) {
+      delete c;
+      return MHD_ERR_CUDA;
+    }
+  }
   c->xfer_ready = false;
   c->xfer = nullptr;
+  c->cap = nullptr;
+  c->gexec = nullptr;
+  c->graph_steps = 0;
   c->have_state = false;
   c->lam_valid = false;
   snprintf(c->err, sizeof(c->err), "no error");
@@ -690,6 +704,51 @@ static int step_impl(mhd_ctx* c, double dt, double ch, const HostOut* ho) {
   return MHD_OK;
 }
 
+int mhd_step_n(mhd_ctx* c, int nsteps) {
+  if (!c) return MHD_ERR_INVALID;
+  if (nsteps < 0) return fail(c, MHD_ERR_INVALID, "mhd_step_n: nsteps = %d < 0", nsteps);
+  if (nsteps == 0) return MHD_OK;
+  if (!c->have_state) return fail(c, MHD_ERR_STATE, "mhd_step_n before mhd_set_state");
+  if (c->cfg.divb == MHD_DIVB_CT && !c->faces_set)
+    return fail(c, MHD_ERR_STATE, "constrained transport: mhd_set_face_field after mhd_set_state");
+  // the wave speed of the current state is reduced outside the graph: the
+  // captured steps take it from the previous step, as mhd_step does
+  int rc = ensure_lambda(c);
+  if (rc != MHD_OK) return rc;
+  if (c->prof_on) {  // per-launch timing needs the individual launches
+    for (int i = 0; i < nsteps; ++i) {
+      rc = step_impl(c, 0.0, 0.0, nullptr);
+      if (rc != MHD_OK) return rc;
+    }
+    return MHD_OK;
+  }
+  if (!c->gexec || c->graph_steps != nsteps) {
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+    if (!c->cap) CK(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    cudaStream_t keep = c->stream;
+    c->stream = c->cap;  // every launch of the captured steps goes to the capture stream
+    cudaError_t ce = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed);
+    if (ce == cudaSuccess) {
+      for (int i = 0; i < nsteps && rc == MHD_OK; ++i) rc = step_impl(c, 0.0, 0.0, nullptr);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(c->cap, &graph);
+      if (rc == MHD_OK && ee == cudaSuccess) ce = cudaGraphInstantiate(&c->gexec, graph, 0);
+      else if (ee != cudaSuccess) ce = ee;
+      if (graph) cudaGraphDestroy(graph);
+    }
+    c->stream = keep;
+    if (rc != MHD_OK) return rc;
+    CK(c, ce);
+    c->graph_steps = nsteps;
+  }
+  CK(c, cudaGraphLaunch(c->gexec, c->stream));
+  c->lam_valid = true;
+  return MHD_OK;
+}
+
 int mhd_step_host(mhd_ctx* c, const double* U_in, double* U_out, double dt, double ch) {
   if (!c) return MHD_ERR_INVALID;
   if (!U_in || !U_out) return fail(c, MHD_ERR_INVALID, "mhd_step_host: null buffer");
@@ -863,6 +922,8 @@ int mhd_destroy(mhd_ctx* c) {
     for (auto e : c->xev) cudaEventDestroy(e);
     cudaStreamDestroy(c->xfer);
   }
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
   return MHD_OK;
 }

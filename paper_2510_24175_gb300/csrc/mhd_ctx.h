@@ -60,6 +60,10 @@ struct mhd_ctx {
   cudaStream_t xfer;
   cudaEvent_t xev[12];
   int tz_half;
+  // mhd_step_n: a capture stream and the graph of graph_steps steps
+  cudaStream_t cap;
+  cudaGraphExec_t gexec;
+  int graph_steps;
   // CUDA-event timing (mhd_profile_enable)
   bool prof_on;
   struct Rec { cudaEvent_t a, b; int kind; };

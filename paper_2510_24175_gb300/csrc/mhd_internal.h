@@ -64,6 +64,11 @@ template <class T>
 cudaError_t launch_ct_divb(const Grid& g, const T* b, unsigned long long* out_bits,
                            cudaStream_t s);
 
+// Sets the shared-memory limit of every stage-kernel variant the grid
+// launches (constrained transport or not), outside any stream capture.
+template <class T>
+cudaError_t prepare_stage_kernels(const Grid& g, bool ct);
+
 // Shared-memory bytes and threads of the stage kernel for this grid.
 template <class T>
 void stage_shape(const Grid& g, size_t* smem, int* threads, int* ty);

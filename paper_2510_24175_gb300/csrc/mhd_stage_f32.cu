@@ -8,4 +8,5 @@ template cudaError_t launch_stage<float>(const Grid&, int, const float*, const f
                                          const float* const*, float*, int, int, int,
                                           unsigned int*);
 template void stage_shape<float>(const Grid&, size_t*, int*, int*);
+template cudaError_t prepare_stage_kernels<float>(const Grid&, bool);
 }  // namespace mhd

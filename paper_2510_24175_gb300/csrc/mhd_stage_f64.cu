@@ -8,4 +8,5 @@ template cudaError_t launch_stage<double>(const Grid&, int, const double*, const
                                           const double* const*, double*, int, int, int,
                                           unsigned int*);
 template void stage_shape<double>(const Grid&, size_t*, int*, int*);
+template cudaError_t prepare_stage_kernels<double>(const Grid&, bool);
 }  // namespace mhd

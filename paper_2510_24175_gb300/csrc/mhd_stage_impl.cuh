@@ -18,13 +18,28 @@ struct StageShape3D {
   static constexpr int NW = sizeof(T) == 8 ? 13 : 8;
 };
 
+// The dynamic shared-memory limit of a kernel is set once per device (a
+// driver call per launch costs more than a small grid's kernel).  One flag
+// word per kernel: the template argument is the kernel itself.
+template <auto KERN>
+static cudaError_t set_smem_once(size_t smem) {
+  static unsigned long long done = 0;  // bit d: set on device d (d < 64)
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(KERN, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) done |= bit;
+  return e;
+}
+
 template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT = false>
 static cudaError_t launch_one(const StageParams<T>& p, dim3 grid, cudaStream_t s) {
   using G = TileGeom<TY, ZACT>;
   const size_t smem = (size_t)G::WORDS * sizeof(T);
   auto kern = rk_stage_kernel<T, TY, NW, STAGE, ZACT, CT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = set_smem_once<rk_stage_kernel<T, TY, NW, STAGE, ZACT, CT>>(smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, NW * 32, smem, s>>>(p);
   return cudaGetLastError();
@@ -35,8 +50,7 @@ static cudaError_t launch_weno(const StageParams<T>& p, dim3 grid, cudaStream_t 
   using G = WenoGeom<TY, ZACT>;
   const size_t smem = (size_t)G::WORDS * sizeof(T);
   auto kern = rk_stage_weno_kernel<T, TY, NW, STAGE, ZACT, CT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = set_smem_once<rk_stage_weno_kernel<T, TY, NW, STAGE, ZACT, CT>>(smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, NW * 32, smem, s>>>(p);
   return cudaGetLastError();
@@ -76,6 +90,52 @@ void stage_shape(const Grid& g, size_t* smem, int* threads, int* ty) {
     *threads = 32;
     *ty = 1;
   }
+}
+
+// Sets the shared-memory limit of every stage-kernel variant a grid launches
+// (stages 1, 2, 3; constrained transport or not), so that no launch needs the
+// driver call later, e.g. while a stream is being captured.
+template <class T>
+cudaError_t prepare_stage_kernels(const Grid& g, bool ct) {
+  cudaError_t e = cudaSuccess;
+  // the three stages of one variant <TY, NW, 3-D, CT> with geometry G
+#define MHD_SET1(KERN, G, TY_, NW_, S_, Z_, CT_) \
+  if (e == cudaSuccess) e = set_smem_once<KERN<T, TY_, NW_, S_, Z_, CT_>>((size_t)G::WORDS * sizeof(T))
+#define MHD_SET3(KERN, G, TY_, NW_, Z_, CT_)   \
+  MHD_SET1(KERN, G, TY_, NW_, 1, Z_, CT_);     \
+  MHD_SET1(KERN, G, TY_, NW_, 2, Z_, CT_);     \
+  MHD_SET1(KERN, G, TY_, NW_, 3, Z_, CT_)
+  using S = StageShape3D<T>;
+  using W3 = WenoGeom<4, true>;
+  using W2 = WenoGeom<4, false>;
+  using W1 = WenoGeom<1, false>;
+  using P3 = TileGeom<S::TY, true>;
+  using P2 = TileGeom<8, false>;
+  using P1 = TileGeom<1, false>;
+  if (ct) {
+    if (g.limiter == kLimWenoz) {
+      MHD_SET3(rk_stage_weno_kernel, W3, 4, 8, true, true);
+    } else {
+      MHD_SET3(rk_stage_kernel, P3, S::TY, S::NW, true, true);
+    }
+  } else if (g.limiter == kLimWenoz) {
+    if (g.ndim == 3) {
+      MHD_SET3(rk_stage_weno_kernel, W3, 4, 8, true, false);
+    } else if (g.ndim == 2) {
+      MHD_SET3(rk_stage_weno_kernel, W2, 4, 8, false, false);
+    } else {
+      MHD_SET3(rk_stage_weno_kernel, W1, 1, 1, false, false);
+    }
+  } else if (g.ndim == 3) {
+    MHD_SET3(rk_stage_kernel, P3, S::TY, S::NW, true, false);
+  } else if (g.ndim == 2) {
+    MHD_SET3(rk_stage_kernel, P2, 8, 8, false, false);
+  } else {
+    MHD_SET3(rk_stage_kernel, P1, 1, 1, false, false);
+  }
+#undef MHD_SET3
+#undef MHD_SET1
+  return e;
 }
 
 template <class T>
