@@ -57,26 +57,39 @@ def gpu_run(pb: Problem, nsteps: int, precision=None, record=False):
     return U, hist, counters
 
 
-def sampled_one_step(U0: np.ndarray, pb: Problem, dt: float, ch: float, cells, radius=4):
-    """Oracle value after one RK2 step at the given (k, j, i) cells of a fully
-    periodic grid.  A cell's new value depends only on cells within `radius`
-    (= 2 stages x 2 ghost cells) along each axis, so the oracle advances a
+def sampled_one_step(U0: np.ndarray, pb: Problem, dt: float, ch: float, cells, radius=None,
+                     faces=None):
+    """Oracle value after one step at the given (k, j, i) cells of a fully
+    periodic grid, for the problem's reconstruction and Runge-Kutta order
+    (and constrained transport when `faces`, the face field, is given).  A
+    cell's new value depends only on cells within `radius` along each axis
+    (stages x ghost depth, plus two cells per stage for constrained
+    transport's edge fields and face means, plus one spare), so the oracle advances a
     (2 radius + 1)^3 box cut out around the cell (periodic wrap) with the
     global dt and c_h and reads its centre; the box's own boundary treatment
     cannot reach the centre."""
+    rk = getattr(pb, "rk_order", 2)
+    ghost = 3 if pb.limiter == orc.LIM_WENOZ else 2
+    if radius is None:
+        radius = rk * (ghost + (2 if faces is not None else 0)) + (1 if rk != 2 or faces is not None else 0)
     out = np.empty((9, len(cells)))
     w = 2 * radius + 1
     sub = Problem(pb.name, (w, w, w), xmin=(0, 0, 0),
                   xmax=(w * pb.dx[0], w * pb.dx[1], w * pb.dx[2]), gamma=pb.gamma,
                   limiter=pb.limiter, glm_alpha=pb.glm_alpha, rho_floor=pb.rho_floor,
-                  p_floor=pb.p_floor, bc=(1,) * 6)
+                  p_floor=pb.p_floor, bc=(1,) * 6 if faces is None else (0,) * 6,
+                  rk_order=rk)
     g = grid_of(sub)
     nz, ny, nx = U0.shape[1:]
     for m, (k, j, i) in enumerate(cells):
         kk = np.arange(k - radius, k + radius + 1) % nz
         jj = np.arange(j - radius, j + radius + 1) % ny
         ii = np.arange(i - radius, i + radius + 1) % nx
-        box = U0[:, kk][:, :, jj][:, :, :, ii]
-        r = orc.run(np.ascontiguousarray(box), g, 1, dts=[dt], chs=[ch])
+        box = np.ascontiguousarray(U0[:, kk][:, :, jj][:, :, :, ii])
+        if faces is None:
+            r = orc.run(box, g, 1, dts=[dt], chs=[ch])
+        else:
+            fbox = np.ascontiguousarray(faces[:, kk][:, :, jj][:, :, :, ii])
+            r = orc.ct_run(box, fbox, g, 1, dts=[dt], chs=[ch])
         out[:, m] = r.U[:, radius, radius, radius]
     return out

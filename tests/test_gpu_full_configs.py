@@ -5,6 +5,8 @@ configuration bench.py times (same contexts, same kernels):
   oracle (a cell's new value needs only a 9^3 neighbourhood), and the error of
   the 50-step FP32 state against the FP64 GPU path (which holds 1e-12 against
   the oracle at every size the oracle can run);
+* the paper's schemes, WENO-Z + SSP-RK3 with GLM or constrained transport,
+  Orszag-Tang 256^3 FP64: one step at sampled cells against the oracle;
 * batched ensemble of 64 seeded boxes (edges 32..128, FP32, 10 steps in one
   persistent graph launch): bitwise equal to per-box plain launches;
 * adjoint of 2-D Orszag-Tang 512^2, 200 RK2 steps, checkpoints every 20 steps:
@@ -64,6 +66,42 @@ def test_turbulent_512_fp32_50_steps_against_fp64_gpu():
     err = num / np.maximum(den, 0.1 * den[0])
     print("turbulent 512^3 x 50 steps, FP32 vs FP64 rel L1 per variable:", err)
     assert np.all(err <= 1e-5), err
+
+
+@pytest.mark.parametrize("ct", [False, True])
+def test_wenoz_rk3_256_one_step_sampled_against_oracle(ct):
+    """The paper's own schemes as bench.py times them (WENO-Z + SSP-RK3 with
+    GLM cleaning or constrained transport, Orszag-Tang 256^3, FP64): one step
+    on the GPU, the oracle's value at sampled cells (a periodic box around each
+    cell, large enough that its boundary cannot reach the centre)."""
+    import torch
+    import paper_2510_24175_gb300 as m
+    from parity_util import grid_of
+    pb = inputs.orszag_tang_3d(256)
+    pb.limiter, pb.rk_order = m.MHD_LIM_WENOZ, 3
+    if ct:
+        pb.divb = m.MHD_DIVB_CT
+    s = m.MHD(m.Config.from_problem(pb))
+    s.set_state(torch.from_numpy(pb.prim()).cuda(), kind=m.MHD_PRIM)
+    faces = None
+    if ct:
+        faces = pb.faces()
+        s.set_face_field(torch.from_numpy(faces).cuda())
+    U0 = s.get_state().cpu().numpy()
+    s.step()
+    info = s.step_info()
+    dt, _ = orc.cfl_dt(U0, grid_of(pb))
+    assert abs(info["dt"] - dt) <= 1e-13 * dt
+    U1 = s.get_state().cpu().numpy()
+    rng = np.random.default_rng(31 + ct)
+    cells = [tuple(int(v) for v in rng.integers(0, 256, 3)) for _ in range(4 if ct else 10)]
+    cells += [(0, 0, 0), (255, 255, 255), (0, 255, 128)]
+    ref = sampled_one_step(U0, pb, info["dt"], info["ch"], cells, faces=faces)
+    got = np.stack([U1[:, k, j, i] for (k, j, i) in cells], axis=1)
+    scale = np.abs(U0).reshape(9, -1).max(axis=1)[:, None]
+    scale = np.maximum(scale, scale[0])  # B_z and psi start at zero
+    err = np.max(np.abs(got - ref) / scale)
+    assert err < 1e-12, err
 
 
 def test_ensemble_64_boxes_bitwise_equal_to_plain_launches():
