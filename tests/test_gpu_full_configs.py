@@ -6,7 +6,8 @@ configuration bench.py times (same contexts, same kernels):
   the 50-step FP32 state against the FP64 GPU path (which holds 1e-12 against
   the oracle at every size the oracle can run);
 * the paper's schemes, WENO-Z + SSP-RK3 with GLM or constrained transport,
-  Orszag-Tang 256^3 FP64: one step at sampled cells against the oracle;
+  Orszag-Tang 256^3 FP64: one step at sampled cells against the oracle; their
+  FP32 lines: 8 steps against the FP64 GPU path;
 * batched ensemble of 64 seeded boxes (edges 32..128, FP32, 10 steps in one
   persistent graph launch): bitwise equal to per-box plain launches;
 * adjoint of 2-D Orszag-Tang 512^2, 200 RK2 steps, checkpoints every 20 steps:
@@ -102,6 +103,38 @@ def test_wenoz_rk3_256_one_step_sampled_against_oracle(ct):
     scale = np.maximum(scale, scale[0])  # B_z and psi start at zero
     err = np.max(np.abs(got - ref) / scale)
     assert err < 1e-12, err
+
+
+@pytest.mark.parametrize("ct", [False, True])
+def test_wenoz_rk3_256_fp32_against_fp64_gpu(ct):
+    """The FP32 lines of the paper's schemes (WENO-Z + SSP-RK3, GLM or
+    constrained transport, Orszag-Tang 256^3): 8 steps in FP32 against the
+    FP64 GPU path (pinned to the oracle at this size by the sampled test)."""
+    import torch
+    import paper_2510_24175_gb300 as m
+    pb = inputs.orszag_tang_3d(256)
+    pb.limiter, pb.rk_order = m.MHD_LIM_WENOZ, 3
+    if ct:
+        pb.divb = m.MHD_DIVB_CT
+    res = {}
+    for prec in (m.MHD_FP32, m.MHD_FP64):
+        s = m.MHD(m.Config.from_problem(pb, precision=prec))
+        s.set_state(torch.from_numpy(pb.prim()).cuda(), kind=m.MHD_PRIM)
+        if ct:
+            s.set_face_field(torch.from_numpy(pb.faces()).cuda())
+        for _ in range(8):
+            s.step()
+        res[prec] = (s.get_state().cpu().numpy(), s.step_info())
+        c = s.counters()
+        assert c["rho_floor"] == 0 and c["p_floor"] == 0
+        del s
+    (U32, i32), (U64, i64) = res[m.MHD_FP32], res[m.MHD_FP64]
+    assert abs(i32["t"] - i64["t"]) <= 1e-5 * i64["t"]
+    num = np.abs(U32 - U64).reshape(9, -1).sum(axis=1)
+    den = np.abs(U64).reshape(9, -1).sum(axis=1)
+    err = num / np.maximum(den, 0.1 * den[0])
+    print("WENO-Z + SSP-RK3", "CT" if ct else "GLM", "256^3 x 8 steps, FP32 vs FP64:", err)
+    assert np.all(err <= 1e-5), err
 
 
 def test_ensemble_64_boxes_bitwise_equal_to_plain_launches():
