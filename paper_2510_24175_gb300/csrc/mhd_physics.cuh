@@ -586,6 +586,33 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
     esR = ((SR - uR) * eR - ptR * uR + pts * SM + bx * (vb - vbsR)) * smiR;
   }
 
+  // Fan region: side a = L if (S_L > 0) or (S_R >= 0 and S_M >= 0), else R
+  // (sign tests on the integer pipe in FP64: gt0 / lt0 / ge0).  The side's
+  // outer and single-star values are picked here, before the double-star
+  // states, so that the other side's outer state is no longer live there.
+  const bool sup = gt0(SL) || lt0(SR);
+  const bool useL = gt0(SL) || (!lt0(SR) && ge0(SM));
+  const T r = useL ? rL : rR, u = useL ? uL : uR, v = useL ? vL : vR, w = useL ? wL : wR;
+  const T by = useL ? byL : byR, bz = useL ? bzL : bzR, e = useL ? eL : eR;
+  const T pt = useL ? ptL : ptR;
+  const T rs = useL ? rsL : rsR, vs = useL ? vsL : vsR, ws = useL ? wsL : wsR;
+  const T bys = useL ? bysL : bysR, bzs = useL ? bzsL : bzsR, es = useL ? esL : esR;
+  const T vbs = useL ? vbsL : vbsR;
+  // the flux terms of the outer and single-star states (the Alfven-fan
+  // terms are added below), so that the outer state dies here
+  const T c1 = sup ? T(0) : (useL ? SL : SR);
+  T f[7];
+  {
+    const T vb = u * bx + v * by + w * bz;
+    f[0] = r * u + c1 * (rs - r);
+    f[1] = r * u * u + pt - bx2 + c1 * (rs * SM - r * u);
+    f[2] = r * v * u - bx * by + c1 * (rs * vs - r * v);
+    f[3] = r * w * u - bx * bz + c1 * (rs * ws - r * w);
+    f[4] = by * u - bx * v + c1 * (bys - by);
+    f[5] = bz * u - bx * w + c1 * (bzs - bz);
+    f[6] = (e + pt) * u - bx * vb + c1 * (es - e);
+  }
+
   // Alfven waves (MK05 Eq. 51) and double-star states (Eqs. 59-63);
   // 1/sqrt(rho*) by rsqrt, sqrt(rho*) = rho* / sqrt(rho*)
   const T iqL = trsqrt(rsL), iqR = trsqrt(rsR);
@@ -601,33 +628,17 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
   const T bzss = (sqL * bzsR + sqR * bzsL + sqL * sqR * (wsR - wsL) * sg) * isum;
   const T vbss = SM * bx + vss * byss + wss * bzss;
 
-  // Fan region: side a = L if (S_L > 0) or (S_R >= 0 and S_M >= 0), else R.
   // F = F_a + c1 (U*_a - U_a) + c2 (U**_a - U*_a) with c1 = S_a unless the
   // interface is supersonic, c2 = S*_a inside the Alfven fan.
-  // (sign tests on the integer pipe in FP64: gt0 / lt0 / ge0)
-  const bool sup = gt0(SL) || lt0(SR);
-  const bool useL = gt0(SL) || (!lt0(SR) && ge0(SM));
   const bool inner = !sup && (useL ? !gt0(SLs) : !lt0(SRs));
-  const T r = useL ? rL : rR, u = useL ? uL : uR, v = useL ? vL : vR, w = useL ? wL : wR;
-  const T by = useL ? byL : byR, bz = useL ? bzL : bzR, e = useL ? eL : eR;
-  const T pt = useL ? ptL : ptR;
-  const T rs = useL ? rsL : rsR, vs = useL ? vsL : vsR, ws = useL ? wsL : wsR;
-  const T bys = useL ? bysL : bysR, bzs = useL ? bzsL : bzsR, es = useL ? esL : esR;
   const T sq = useL ? -sqL : sqR;
-  const T vbs = useL ? vbsL : vbsR;
   const T ess = es + sq * (vbs - vbss) * sg;
-  const T c1 = sup ? T(0) : (useL ? SL : SR);
   const T c2 = inner ? (useL ? SLs : SRs) : T(0);
-
-  const T vb = u * bx + v * by + w * bz;
-  T f[7];
-  f[0] = r * u + c1 * (rs - r);
-  f[1] = r * u * u + pt - bx2 + c1 * (rs * SM - r * u);
-  f[2] = r * v * u - bx * by + c1 * (rs * vs - r * v) + c2 * rs * (vss - vs);
-  f[3] = r * w * u - bx * bz + c1 * (rs * ws - r * w) + c2 * rs * (wss - ws);
-  f[4] = by * u - bx * v + c1 * (bys - by) + c2 * (byss - bys);
-  f[5] = bz * u - bx * w + c1 * (bzs - bz) + c2 * (bzss - bzs);
-  f[6] = (e + pt) * u - bx * vb + c1 * (es - e) + c2 * (ess - es);
+  f[2] = f[2] + c2 * rs * (vss - vs);
+  f[3] = f[3] + c2 * rs * (wss - ws);
+  f[4] = f[4] + c2 * (byss - bys);
+  f[5] = f[5] + c2 * (bzss - bzs);
+  f[6] = f[6] + c2 * (ess - es);
 
   F[kRHO] = f[0];
   F[kPRS] = f[6];
