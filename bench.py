@@ -46,12 +46,12 @@ sys.path.insert(0, ROOT)
 # smsp__inst_executed_pipe_fp64 x 32 / cells over the timed steps of this
 # bench's Orszag-Tang 256^3 run (profiles/).  They change whenever the kernel
 # does.
-FP64_INST_PER_CELL = {1: 1210.3, 2: 1264.8}
+FP64_INST_PER_CELL = {1: 1182.7, 2: 1204.0}
 # DRAM bytes per cell of the stage kernel's launches (ncu dram__bytes_read +
 # dram__bytes_write over the timed steps of this bench's 256^3 FP64 and 512^3
 # FP32 runs, profiles/); reported as the roofline's traffic per launch.  Set
 # to None whenever the kernel changes until they are captured again.
-TRAFFIC_BYTES_PER_CELL = {8: {1: 149.5, 2: 221.5}, 4: {1: 75.7, 2: 111.4}}
+TRAFFIC_BYTES_PER_CELL = {8: {1: 149.3, 2: 221.1}, 4: {1: 75.6, 2: 111.4}}
 # FP64 pipe peak: 2 lanes/clk/SM (a DFMA probe measured 1.9) x 152 SMs x
 # 2.07 GHz = 629 G lane-instructions/s (1.26 TFLOP/s counting an FMA as 2).
 FP64_PEAK_GINST = 2 * 152 * 2.07
@@ -63,7 +63,7 @@ FP32_WARP_INST_PER_CELL = {1: 82.91, 2: 88.71}
 ISSUE_PEAK_GINST = 4 * 152 * 2.07
 # FP64-pipe lane-instructions per cell of the FP64 WENO-Z stage kernel (ncu,
 # Orszag-Tang 128^3; first / middle / last SSP-RK3 stage).
-WENO_FP64_INST_PER_CELL = {"stage1": 3601.8, "stage_mid": 3619.8, "stage2": 3621.0}
+WENO_FP64_INST_PER_CELL = {"stage1": 3594.7, "stage_mid": 3612.7, "stage2": 3613.8}
 # Algorithmic HBM bytes per cell: stage 1 reads U^n and writes U1 (18 words),
 # stage 2 reads U1 and U^n and writes U^{n+1} (27 words).
 WORDS_STAGE = {1: 18, 2: 27}
@@ -299,7 +299,7 @@ def roofline_of(prof, ncell, esize, hbm_peak, peak_kind, fp64):
            "kernel": "rk_stage_kernel", "avg_launch_ms": avg_ms,
            "fp64_inst_per_cell": FP64_INST_PER_CELL,
            "peak_source": "2 FP64 lanes/clk/SM x 152 SMs x 2.07 GHz (GB300 nominal 1.25 "
-                          "TFLOP/s FP64); FP64 pipe is the bound (ncu: 84 % busy)"}
+                          "TFLOP/s FP64); FP64 pipe is the bound (ncu: 84-85 % busy)"}
     return hbm, alu
 
 
