@@ -33,10 +33,26 @@ struct FaceArgs {
   Phys<double> ph;
 };
 
+// Primitives of every cell of W (the face kernels' stencils read them instead
+// of converting each of their four cells again).
+__global__ void adj_prims_kernel(const double* __restrict__ W, double* __restrict__ V,
+                                 long long ncell, Phys<double> ph) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    double u[kNV], v[kNV];
+    unsigned flags = 0;
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) u[k] = W[k * ncell + c];
+    cons_to_prim(u, v, ph, flags);
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) V[k * ncell + c] = v[k];
+  }
+}
+
 // One thread per face of direction DIR; faces f = 0..n_d along d (face f
-// separates cells f-1 and f).
+// separates cells f-1 and f).  Wp: the primitives of the stage input.
 template <int DIR>
-__global__ void __launch_bounds__(128) adj_faces_kernel(const double* __restrict__ W,
+__global__ void __launch_bounds__(128) adj_faces_kernel(const double* __restrict__ Wp,
                                                         const double* __restrict__ x,
                                                         double* __restrict__ gV,
                                                         const FaceArgs a) {
@@ -60,12 +76,9 @@ __global__ void __launch_bounds__(128) adj_faces_kernel(const double* __restrict
       off[q] = (long long)cc[2] * a.sz + (long long)cc[1] * a.sy + cc[0];
     }
     double V[4][kNV];
-    unsigned flags = 0;
     for (int q = 0; q < 4; ++q) {
-      double u[kNV];
 #pragma unroll
-      for (int k = 0; k < kNV; ++k) u[k] = W[k * a.sv + off[q]];
-      cons_to_prim(u, V[q], a.ph, flags);
+      for (int k = 0; k < kNV; ++k) V[q][k] = Wp[k * a.sv + off[q]];
     }
     // slopes of cells f-1 (a) and f (b) with their derivatives
     double sa[kNV], sb[kNV], dma[kNV], dpa[kNV], dmb[kNV], dpb[kNV];
@@ -162,11 +175,16 @@ unsigned blocks_for(long long n, int threads, int nsm) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
-// gV = 0; gV += J_V^T-scatter of every face; out = b1 (+ b2) + dt (dV/dW)^T gV
-cudaError_t vjp_L(const Grid& g, const FaceArgs& fa0, const double* W, const double* x,
-                  double* gV, const double* b1, const double* b2, double* out, double dt,
-                  cudaStream_t s) {
+// Wp = prim(W); gV = 0; gV += J_V^T-scatter of every face;
+// out = b1 (+ b2) + dt (dV/dW)^T gV
+cudaError_t vjp_L(const Grid& g, const FaceArgs& fa0, const double* W, double* Wp,
+                  const double* x, double* gV, const double* b1, const double* b2, double* out,
+                  double dt, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(gV, 0, (size_t)9 * g.ncell * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  adj_prims_kernel<<<blocks_for(g.ncell, 256, g.nsm), 256, 0, s>>>(W, Wp, g.ncell,
+                                                                     make_phys<double>(g));
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   for (int d = 0; d < 3; ++d) {
     if (g.n[d] <= 1) continue;
@@ -174,9 +192,9 @@ cudaError_t vjp_L(const Grid& g, const FaceArgs& fa0, const double* W, const dou
     fa.inv_dx = 1.0 / g.dx[d];
     long long nf = g.ncell / g.n[d] * (g.n[d] + 1);
     const unsigned nb = blocks_for(nf, 128, g.nsm);
-    if (d == 0) adj_faces_kernel<0><<<nb, 128, 0, s>>>(W, x, gV, fa);
-    if (d == 1) adj_faces_kernel<1><<<nb, 128, 0, s>>>(W, x, gV, fa);
-    if (d == 2) adj_faces_kernel<2><<<nb, 128, 0, s>>>(W, x, gV, fa);
+    if (d == 0) adj_faces_kernel<0><<<nb, 128, 0, s>>>(Wp, x, gV, fa);
+    if (d == 1) adj_faces_kernel<1><<<nb, 128, 0, s>>>(Wp, x, gV, fa);
+    if (d == 2) adj_faces_kernel<2><<<nb, 128, 0, s>>>(Wp, x, gV, fa);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -187,11 +205,12 @@ cudaError_t vjp_L(const Grid& g, const FaceArgs& fa0, const double* W, const dou
 
 }  // namespace
 
-// Scratch: U1, h, a1, gV (9 ncell doubles each), the step scalars of the
-// stage-1 recomputation and its (unused) reduction words.
+// Scratch: U1, h, a1, gV and the primitives of a stage input (9 ncell
+// doubles each), the step scalars of the stage-1 recomputation and its
+// (unused) reduction words.
 size_t adjoint_scratch_bytes(const Grid& g) {
   const size_t state = a256((size_t)9 * g.ncell * sizeof(double));
-  return 4 * state + a256(sizeof(StepScalars)) + 256;
+  return 5 * state + a256(sizeof(StepScalars)) + 256;
 }
 
 int adjoint_step(const Grid& g, double dt, double ch, double glm_alpha, double dh_min,
@@ -207,9 +226,10 @@ int adjoint_step(const Grid& g, double dt, double ch, double glm_alpha, double d
   double* h = reinterpret_cast<double*>(p + state);
   double* a1 = reinterpret_cast<double*>(p + 2 * state);
   double* gV = reinterpret_cast<double*>(p + 3 * state);
-  StepScalars* sc = reinterpret_cast<StepScalars*>(p + 4 * state);
+  double* Vp = reinterpret_cast<double*>(p + 4 * state);
+  StepScalars* sc = reinterpret_cast<StepScalars*>(p + 5 * state);
   unsigned long long* words =
-      reinterpret_cast<unsigned long long*>(p + 4 * state + a256(sizeof(StepScalars)));
+      reinterpret_cast<unsigned long long*>(p + 5 * state + a256(sizeof(StepScalars)));
 
   StepScalars hs{};
   hs.dt = dt;
@@ -238,9 +258,9 @@ int adjoint_step(const Grid& g, double dt, double ch, double glm_alpha, double d
   fa.half_chi = 0.5 / ch;
   fa.ph = make_phys<double>(g);
   // a1 = h + dt J_L(U1)^T h
-  if (e == cudaSuccess) e = vjp_L(g, fa, U1, h, gV, h, nullptr, a1, dt, s);
+  if (e == cudaSuccess) e = vjp_L(g, fa, U1, Vp, h, gV, h, nullptr, a1, dt, s);
   // lam_n = h + a1 + dt J_L(U_n)^T a1
-  if (e == cudaSuccess) e = vjp_L(g, fa, U_n, a1, gV, h, a1, lam_n, dt, s);
+  if (e == cudaSuccess) e = vjp_L(g, fa, U_n, Vp, a1, gV, h, a1, lam_n, dt, s);
   if (e != cudaSuccess) {
     snprintf(err, errlen, "adjoint launch failed: %s", cudaGetErrorString(e));
     return -3;
