@@ -537,17 +537,25 @@ def main():
         dt_a, ch_a = info_a["dt"], info_a["ch"]
         Ka = max(K, 10)
         stream = torch.cuda.current_stream()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
         torch.cuda.synchronize()
         ev[0].record(stream)
         for _ in range(Ka):
             sa.step(dt_a, ch_a)
         ev[1].record(stream)
         Ua = sa.get_state()
+        U1a = torch.empty_like(Ua)
+        # the reverse pass's forward recompute when it keeps the first stage
+        ev[4].record(stream)
+        for _ in range(Ka):
+            sa.step(dt_a, ch_a)
+            sa.get_stage1(U1a)
+        ev[5].record(stream)
         lam = torch.randn_like(Ua)
         out = torch.empty_like(Ua)
         for _ in range(W):
             sa.adjoint_step(Ua, lam, out, dt_a, ch_a)
+            sa.adjoint_step_stage1(Ua, U1a, lam, out, dt_a, ch_a)
         torch.cuda.synchronize()
         ev[2].record(stream)
         for i in range(Ka):
@@ -556,14 +564,31 @@ def main():
             else:
                 sa.adjoint_step(Ua, out, lam, dt_a, ch_a)
         ev[3].record(stream)
+        ev[6].record(stream)
+        for i in range(Ka):
+            if i % 2 == 0:
+                sa.adjoint_step_stage1(Ua, U1a, lam, out, dt_a, ch_a)
+            else:
+                sa.adjoint_step_stage1(Ua, U1a, out, lam, dt_a, ch_a)
+        ev[7].record(stream)
         torch.cuda.synchronize()
         ms_f = ev[0].elapsed_time(ev[1]) / Ka
         ms_a = ev[2].elapsed_time(ev[3]) / Ka
+        ms_fk = ev[4].elapsed_time(ev[5]) / Ka
+        ms_ak = ev[6].elapsed_time(ev[7]) / Ka
         adjoint = {"workload": "orszag_tang_2d_512^2_fp64", "forward_ms_per_step": ms_f,
                    "adjoint_ms_per_step": ms_a,
-                   "adjoint_over_forward": (ms_a + ms_f) / ms_f,
-                   "note": "ratio = (adjoint step + its forward recompute) / forward step"}
-        launches += Ka * 3 + Ka * 7
+                   "adjoint_over_forward": (ms_ak + ms_fk) / ms_f,
+                   "forward_keep_stage1_ms_per_step": ms_fk,
+                   "adjoint_stage1_kept_ms_per_step": ms_ak,
+                   "adjoint_over_forward_recomputing_stage1": (ms_a + ms_f) / ms_f,
+                   "note": "ratio = (adjoint step + its forward recompute) / forward step; "
+                           "the recompute keeps each step's first RK stage (get_stage1) "
+                           "and the adjoint reuses it (adjoint_step_stage1), as MHDRollout "
+                           "does for all but a checkpoint segment's last step"}
+        # forward FP64 step: prep, two stages, exact speed pass; 2-D adjoint:
+        # init, stage-1 recompute, 2 x (primitives, 2 face sweeps, cells)
+        launches += 2 * Ka * 4 + Ka * 10 + Ka * 9
         del sa
         torch.cuda.empty_cache()
 

@@ -216,6 +216,25 @@ int mhd_flux_batch(const void* VL, const void* VR, void* F, long long nface, int
 int mhd_adjoint_step(mhd_ctx* ctx, const double* U_n, const double* lam_np1, double* lam_n,
                      double dt, double ch);
 
+/* The first Runge-Kutta stage U1 = U^n + dt L(U^n) of the context's last
+ * step (mhd_step, mhd_step_n or mhd_step_host), so that a checkpointed
+ * reverse pass can keep it beside U^n instead of recomputing it inside
+ * mhd_adjoint_step_stage1.  Valid after an FP64 RK2 step with GLM; any
+ * mhd_set_state / mhd_set_face_field clears it (MHD_ERR_STATE until the next
+ * step).  U1: float64 [9][nz][ny][nx], host (where = MHD_HOST; synchronises)
+ * or device (MHD_DEVICE; enqueued on the context's stream). */
+int mhd_get_stage1(mhd_ctx* ctx, double* U1, int where);
+
+/* mhd_adjoint_step with the step's first stage supplied: U1 is the state
+ * mhd_get_stage1 returned after stepping U_n with the same dt and c_h (device
+ * float64 [9][nz][ny][nx], not aliasing U_n or lam_n).  Same result, bit for
+ * bit, as mhd_adjoint_step(ctx, U_n, lam_np1, lam_n, dt, ch); saves the
+ * recomputation of the first stage (one of the forward step's two stage
+ * kernels).  A U1 that does not belong to U_n gives the adjoint about a
+ * different trajectory; nothing checks it. */
+int mhd_adjoint_step_stage1(mhd_ctx* ctx, const double* U_n, const double* U1,
+                            const double* lam_np1, double* lam_n, double dt, double ch);
+
 /* Per-kernel timing of the context's launches with CUDA events recorded on
  * the context's stream (off by default; the events are created on the host
  * when enabled).  Kernel classes: 0 = step prepare, 1 = first RK stage,

@@ -37,6 +37,7 @@ EXPORTED = ["mhd_config_default", "mhd_workspace_bytes", "mhd_create", "mhd_set_
             "mhd_set_state", "mhd_get_state", "mhd_dt", "mhd_step", "mhd_step_host",
             "mhd_step_n", "mhd_step_info",
             "mhd_counters", "mhd_conserved_sums", "mhd_flux_batch", "mhd_adjoint_step",
+            "mhd_adjoint_step_stage1", "mhd_get_stage1",
             "mhd_profile_enable", "mhd_profile_read", "mhd_conserved_sums_noalloc",
             "mhd_last_error", "mhd_destroy", "mhd_set_face_field", "mhd_get_face_field",
             "mhd_divb_max",
@@ -94,6 +95,8 @@ def lib():
         L.mhd_conserved_sums.argtypes = [vp, dp]
         L.mhd_flux_batch.argtypes = [vp, vp, vp, ctypes.c_longlong, i, d, d, i, vp]
         L.mhd_adjoint_step.argtypes = [vp, vp, vp, vp, d, d]
+        L.mhd_adjoint_step_stage1.argtypes = [vp, vp, vp, vp, vp, d, d]
+        L.mhd_get_stage1.argtypes = [vp, vp, i]
         L.mhd_profile_enable.argtypes = [vp, i]
         L.mhd_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), dp]
         L.mhd_conserved_sums_noalloc.argtypes = [cfgp, vp, dp, vp]
@@ -210,6 +213,15 @@ def mhd_step_host(ctx, U_in, U_out, dt: float = 0.0, ch: float = 0.0):
 def mhd_adjoint_step(ctx, U_n, lam_np1, lam_n, dt: float, ch: float):
     _check(lib().mhd_adjoint_step(ctx, _ptr(U_n), _ptr(lam_np1), _ptr(lam_n), float(dt),
                                   float(ch)), ctx, "mhd_adjoint_step")
+
+
+def mhd_adjoint_step_stage1(ctx, U_n, U1, lam_np1, lam_n, dt: float, ch: float):
+    _check(lib().mhd_adjoint_step_stage1(ctx, _ptr(U_n), _ptr(U1), _ptr(lam_np1), _ptr(lam_n),
+                                         float(dt), float(ch)), ctx, "mhd_adjoint_step_stage1")
+
+
+def mhd_get_stage1(ctx, U1, where: int):
+    _check(lib().mhd_get_stage1(ctx, _ptr(U1), int(where)), ctx, "mhd_get_stage1")
 
 
 def mhd_destroy(ctx):
@@ -406,6 +418,20 @@ class MHD:
 
     def adjoint_step(self, U_n, lam_np1, lam_n, dt: float, ch: float):
         mhd_adjoint_step(self.ctx, U_n, lam_np1, lam_n, dt, ch)
+
+    def get_stage1(self, out=None):
+        """The last step's first Runge-Kutta stage U1 (mhd_get_stage1) as a
+        float64 CUDA tensor (or into ``out``; a numpy ``out`` receives a host
+        copy)."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        mhd_get_stage1(self.ctx, out, MHD_HOST if isinstance(out, np.ndarray) else MHD_DEVICE)
+        return out
+
+    def adjoint_step_stage1(self, U_n, U1, lam_np1, lam_n, dt: float, ch: float):
+        """adjoint_step with the step's first stage U1 supplied (get_stage1)."""
+        mhd_adjoint_step_stage1(self.ctx, U_n, U1, lam_np1, lam_n, dt, ch)
 
     def run(self, nsteps: int, t_end: float = 0.0):
         """Advances up to nsteps CFL steps (stopping at t_end when the config

@@ -4,9 +4,12 @@ forward: advances the state nsteps CFL steps with mhd_step, keeping a copy of
 the state every k steps (checkpoints) and recording each step's dt and c_h.
 backward: for each k-step segment, last first, recomputes the segment's
 states from its checkpoint with the recorded dt and c_h (mhd_step with
-explicit dt, ch: bitwise the same states), then applies mhd_adjoint_step
-(the discrete adjoint of one step with dt and c_h frozen) from the last step
-of the segment to the first.  Every step of the method runs in the CUDA
+explicit dt, ch: bitwise the same states), keeping each recomputed step's
+first Runge-Kutta stage (mhd_get_stage1), then applies the discrete adjoint
+of one step with dt and c_h frozen from the last step of the segment to the
+first: mhd_adjoint_step_stage1 with the kept stage, and for the segment's
+last step, which is not recomputed, mhd_adjoint_step (which recomputes only
+that step's first stage).  Every step of the method runs in the CUDA
 library; torch holds the tensors.
 """
 from __future__ import annotations
@@ -48,14 +51,19 @@ class MHDRollout(torch.autograd.Function):
             n0 = s * k
             n1 = min(n0 + k, nsteps)
             solver.set_state(ctx.ckpts[s])
-            states = [ctx.ckpts[s]]
+            states, stage1 = [ctx.ckpts[s]], []
             for n in range(n0, n1 - 1):
                 solver.step(ctx.dts[n], ctx.chs[n])
+                stage1.append(solver.get_stage1())
                 states.append(solver.get_state())
             for i in reversed(range(n1 - n0)):
                 n = n0 + i
                 out = torch.empty_like(lam)
-                solver.adjoint_step(states[i], lam, out, ctx.dts[n], ctx.chs[n])
+                if i < len(stage1):
+                    solver.adjoint_step_stage1(states[i], stage1[i], lam, out, ctx.dts[n],
+                                               ctx.chs[n])
+                else:
+                    solver.adjoint_step(states[i], lam, out, ctx.dts[n], ctx.chs[n])
                 lam = out
         return lam, None, None, None
 

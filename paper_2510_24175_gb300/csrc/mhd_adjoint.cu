@@ -214,15 +214,16 @@ size_t adjoint_scratch_bytes(const Grid& g) {
 }
 
 int adjoint_step(const Grid& g, double dt, double ch, double glm_alpha, double dh_min,
-                 const double* U_n, const double* lam_np1, double* lam_n, void* scratch,
-                 size_t scratch_bytes, cudaStream_t s, char* err, size_t errlen) {
+                 const double* U_n, const double* U1_in, const double* lam_np1, double* lam_n,
+                 void* scratch, size_t scratch_bytes, cudaStream_t s, char* err,
+                 size_t errlen) {
   if (scratch_bytes < adjoint_scratch_bytes(g)) {
     snprintf(err, errlen, "adjoint scratch too small");
     return -2;
   }
   const size_t state = a256((size_t)9 * g.ncell * sizeof(double));
   char* p = static_cast<char*>(scratch);
-  double* U1 = reinterpret_cast<double*>(p);
+  double* U1s = reinterpret_cast<double*>(p);
   double* h = reinterpret_cast<double*>(p + state);
   double* a1 = reinterpret_cast<double*>(p + 2 * state);
   double* gV = reinterpret_cast<double*>(p + 3 * state);
@@ -238,8 +239,10 @@ int adjoint_step(const Grid& g, double dt, double ch, double glm_alpha, double d
   hs.damp = std::exp(-glm_alpha * ch * dt / dh_min);
   cudaError_t e = cudaMemcpyAsync(sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(words, 0, 256, s);
-  // forward stage 1 recomputed from U_n
-  if (e == cudaSuccess) e = launch_stage<double>(g, 1, U_n, nullptr, U1, sc, words, words + 1, s);
+  // forward stage 1: recomputed from U_n unless the caller kept it (U1_in)
+  const double* U1 = U1_in ? U1_in : U1s;
+  if (e == cudaSuccess && !U1_in)
+    e = launch_stage<double>(g, 1, U_n, nullptr, U1s, sc, words, words + 1, s);
   if (e == cudaSuccess)
     adj_init_kernel<<<blocks_for(g.ncell, 256, g.nsm), 256, 0, s>>>(lam_np1, h, g.ncell,
                                                                     hs.damp);

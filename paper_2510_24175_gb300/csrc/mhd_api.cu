@@ -145,8 +145,9 @@ static int validate(const mhd_config* c, char* msg, size_t len) {
 namespace mhd {
 size_t adjoint_scratch_bytes(const Grid& g);
 int adjoint_step(const Grid& g, double dt, double ch, double glm_alpha, double dh_min,
-                 const double* U_n, const double* lam_np1, double* lam_n, void* scratch,
-                 size_t scratch_bytes, cudaStream_t stream, char* err, size_t errlen);
+                 const double* U_n, const double* U1_in, const double* lam_np1, double* lam_n,
+                 void* scratch, size_t scratch_bytes, cudaStream_t stream, char* err,
+                 size_t errlen);
 }  // namespace mhd
 
 static void fill_grid(const mhd_config* c, mhd::Grid* g) {
@@ -379,6 +380,7 @@ int mhd_create(const mhd_config* cfg, void* d_workspace, size_t bytes, void* str
   c->cap = nullptr;
   c->gexec = nullptr;
   c->graph_steps = 0;
+  c->stage1_valid = false;
   c->have_state = false;
   c->lam_valid = false;
   snprintf(c->err, sizeof(c->err), "no error");
@@ -439,6 +441,7 @@ int mhd_set_state(mhd_ctx* c, const double* U, int where, int kind) {
   c->have_state = true;
   c->lam_valid = false;
   c->faces_set = false;
+  c->stage1_valid = false;
   return MHD_OK;
 }
 
@@ -449,6 +452,7 @@ int mhd_set_face_field(mhd_ctx* c, const double* b, int where) {
   if (!b || (where != MHD_HOST && where != MHD_DEVICE))
     return fail(c, MHD_ERR_INVALID, "mhd_set_face_field: bad argument");
   if (!c->have_state) return fail(c, MHD_ERR_STATE, "mhd_set_face_field before mhd_set_state");
+  c->stage1_valid = false;
   const long long n = 3 * c->grid.ncell;
   const cudaMemcpyKind mk = where == MHD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   if (c->esize == 8) {
@@ -701,6 +705,8 @@ static int step_impl(mhd_ctx* c, double dt, double ch, const HostOut* ho) {
     }
   }
   c->lam_valid = true;
+  // U_b now holds this step's first stage U1 (RK2; read by mhd_get_stage1)
+  c->stage1_valid = c->esize == 8 && c->cfg.rk_order != 3 && c->cfg.divb == MHD_DIVB_GLM;
   return MHD_OK;
 }
 
@@ -782,6 +788,7 @@ int mhd_step_host(mhd_ctx* c, const double* U_in, double* U_out, double dt, doub
   c->have_state = true;
   c->lam_valid = false;
   c->faces_set = false;
+  c->stage1_valid = false;
   const bool need_lam = !(dt > 0.0) || !(ch > 0.0);
   // eight input slabs; the wave-speed reduction follows each as it lands
   for (int k = 0; k < 8; ++k) {
@@ -870,16 +877,42 @@ int mhd_flux_batch(const void* VL, const void* VR, void* F, long long nface, int
   return e == cudaSuccess ? MHD_OK : MHD_ERR_CUDA;
 }
 
-int mhd_adjoint_step(mhd_ctx* c, const double* U_n, const double* lam_np1, double* lam_n,
-                     double dt, double ch) {
+static int adjoint_impl(mhd_ctx* c, const double* U_n, const double* U1, const double* lam_np1,
+                        double* lam_n, double dt, double ch) {
   if (!c) return MHD_ERR_INVALID;
   if (!(c->cfg.flags & MHD_FLAG_ADJOINT) || c->esize != 8)
     return fail(c, MHD_ERR_STATE, "context created without MHD_FLAG_ADJOINT / MHD_FP64");
   if (!U_n || !lam_np1 || !lam_n || lam_n == lam_np1 || !(dt > 0.0) || !(ch > 0.0) ||
-      !std::isfinite(dt) || !std::isfinite(ch))
+      !std::isfinite(dt) || !std::isfinite(ch) || (U1 && (U1 == lam_n || U1 == U_n)))
     return fail(c, MHD_ERR_INVALID, "mhd_adjoint_step: bad argument");
-  return mhd::adjoint_step(c->grid, dt, ch, c->cfg.glm_alpha, c->dh_min, U_n, lam_np1, lam_n,
-                           c->adj, c->adj_bytes, c->stream, c->err, sizeof(c->err));
+  return mhd::adjoint_step(c->grid, dt, ch, c->cfg.glm_alpha, c->dh_min, U_n, U1, lam_np1,
+                           lam_n, c->adj, c->adj_bytes, c->stream, c->err, sizeof(c->err));
+}
+
+int mhd_adjoint_step(mhd_ctx* c, const double* U_n, const double* lam_np1, double* lam_n,
+                     double dt, double ch) {
+  return adjoint_impl(c, U_n, nullptr, lam_np1, lam_n, dt, ch);
+}
+
+int mhd_adjoint_step_stage1(mhd_ctx* c, const double* U_n, const double* U1,
+                            const double* lam_np1, double* lam_n, double dt, double ch) {
+  if (c && !U1) return fail(c, MHD_ERR_INVALID, "mhd_adjoint_step_stage1: null U1");
+  return adjoint_impl(c, U_n, U1, lam_np1, lam_n, dt, ch);
+}
+
+int mhd_get_stage1(mhd_ctx* c, double* U1, int where) {
+  if (!c) return MHD_ERR_INVALID;
+  if (!U1 || (where != MHD_HOST && where != MHD_DEVICE))
+    return fail(c, MHD_ERR_INVALID, "mhd_get_stage1: bad argument");
+  if (!c->stage1_valid)
+    return fail(c, MHD_ERR_STATE,
+                "mhd_get_stage1: no FP64 RK2 GLM step since the state was last set");
+  const long long n = 9 * c->grid.ncell;
+  CK(c, cudaMemcpyAsync(U1, c->Ub, n * 8,
+                        where == MHD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                        c->stream));
+  if (where == MHD_HOST) CK(c, cudaStreamSynchronize(c->stream));
+  return MHD_OK;
 }
 
 int mhd_profile_enable(mhd_ctx* c, int enable) {

@@ -53,6 +53,7 @@ struct mhd_ctx {
   cudaStream_t stream;
   bool have_state;
   bool lam_valid;
+  bool stage1_valid;     // U_b holds the last step's first stage (mhd_get_stage1)
   double inv_dx_sum, dh_min;
   // mhd_step_host: a transfer stream and its events (made on first use), and
   // the z-chunk depth of the last stage's half launches
