@@ -212,7 +212,8 @@ int mhd_flux_batch(const void* VL, const void* VR, void* F, long long nface, int
  * U_n: the step's input state; lam_np1, lam_n: adjoints; all device float64
  * arrays [9][nz][ny][nx].  lam_n may not alias lam_np1.  Needs a context
  * created with MHD_FLAG_ADJOINT and MHD_FP64.  Does not change the context's
- * state. */
+ * state.  The slope derivatives are accumulated with FP64 atomics, so
+ * results vary run to run in the last few bits. */
 int mhd_adjoint_step(mhd_ctx* ctx, const double* U_n, const double* lam_np1, double* lam_n,
                      double dt, double ch);
 
@@ -227,10 +228,11 @@ int mhd_get_stage1(mhd_ctx* ctx, double* U1, int where);
 
 /* mhd_adjoint_step with the step's first stage supplied: U1 is the state
  * mhd_get_stage1 returned after stepping U_n with the same dt and c_h (device
- * float64 [9][nz][ny][nx], not aliasing U_n or lam_n).  Same result, bit for
- * bit, as mhd_adjoint_step(ctx, U_n, lam_np1, lam_n, dt, ch); saves the
- * recomputation of the first stage (one of the forward step's two stage
- * kernels).  A U1 that does not belong to U_n gives the adjoint about a
+ * float64 [9][nz][ny][nx], not aliasing U_n or lam_n).  Same result as
+ * mhd_adjoint_step(ctx, U_n, lam_np1, lam_n, dt, ch) up to the order of the
+ * FP64 atomic accumulation both use (which varies run to run by a few ulp);
+ * saves the recomputation of the first stage (one of the forward step's two
+ * stage kernels).  A U1 that does not belong to U_n gives the adjoint about a
  * different trajectory; nothing checks it. */
 int mhd_adjoint_step_stage1(mhd_ctx* ctx, const double* U_n, const double* U1,
                             const double* lam_np1, double* lam_n, double dt, double ch);

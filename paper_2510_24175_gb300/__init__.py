@@ -221,7 +221,8 @@ def mhd_adjoint_step_stage1(ctx, U_n, U1, lam_np1, lam_n, dt: float, ch: float):
 
 
 def mhd_get_stage1(ctx, U1, where: int):
-    _check(lib().mhd_get_stage1(ctx, _ptr(U1), int(where)), ctx, "mhd_get_stage1")
+    p = _ptr(U1) if where == MHD_DEVICE else U1.ctypes.data_as(ctypes.c_void_p)
+    _check(lib().mhd_get_stage1(ctx, p, int(where)), ctx, "mhd_get_stage1")
 
 
 def mhd_destroy(ctx):
@@ -426,7 +427,14 @@ class MHD:
         torch = _torch()
         if out is None:
             out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
-        mhd_get_stage1(self.ctx, out, MHD_HOST if isinstance(out, np.ndarray) else MHD_DEVICE)
+        if isinstance(out, np.ndarray):
+            assert out.dtype == np.float64 and out.flags["C_CONTIGUOUS"]
+            assert out.shape == self.shape
+            mhd_get_stage1(self.ctx, out, MHD_HOST)
+        else:
+            assert out.is_cuda and out.dtype == torch.float64 and out.is_contiguous()
+            assert tuple(out.shape) == self.shape
+            mhd_get_stage1(self.ctx, out, MHD_DEVICE)
         return out
 
     def adjoint_step_stage1(self, U_n, U1, lam_np1, lam_n, dt: float, ch: float):

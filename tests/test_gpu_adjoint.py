@@ -191,8 +191,10 @@ def test_adjoint_with_kept_stage1_equals_recomputed(pb):
     """mhd_get_stage1 after a step with explicit dt, c_h returns that step's
     first RK stage (the oracle's stage 1 within 1e-12 relative L1 per
     variable; host and device copies equal), and mhd_adjoint_step_stage1
-    with it gives mhd_adjoint_step's result bit for bit.  set_state clears
-    the kept stage; U1 aliasing U^n is rejected."""
+    with it gives mhd_adjoint_step's result up to the order of the adjoint's
+    FP64 atomic accumulation (run to run a few ulp: 1e-13 of the largest
+    component).  set_state clears the kept stage; U1 aliasing U^n is
+    rejected."""
     import torch
     import paper_2510_24175_gb300 as m
     g = grid_of(pb)
@@ -219,7 +221,8 @@ def test_adjoint_with_kept_stage1_equals_recomputed(pb):
     b = torch.empty_like(lam)
     s.adjoint_step(Ud, lam, a, dt, ch)
     s.adjoint_step_stage1(Ud, U1, lam, b, dt, ch)
-    np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+    ah, bh = a.cpu().numpy(), b.cpu().numpy()
+    np.testing.assert_allclose(bh, ah, rtol=1e-13, atol=1e-13 * float(np.abs(ah).max()))
     with pytest.raises(m.MHDError) as e:
         s.adjoint_step_stage1(Ud, Ud, lam, b, dt, ch)
     assert e.value.code == m.MHD_ERR_INVALID
@@ -233,11 +236,13 @@ def test_adjoint_with_kept_stage1_equals_recomputed(pb):
 def test_rollout_gradient_independent_of_checkpoint_interval(k):
     """The rollout's gradient does not depend on the checkpoint interval k
     (k = 1: every step recomputes its first stage inside the adjoint; larger
-    k: all but a segment's last step use the kept first stage): bit for bit
-    the gradient of k = 8 over 8 steps, which recomputes nothing but the
-    last step's first stage."""
+    k: all but a segment's last step use the kept first stage): the gradient
+    of k = 8 over 8 steps, which recomputes nothing but the last step's first
+    stage, up to the order of the adjoint's FP64 atomic accumulation (1e-11
+    of the largest component after 8 steps)."""
     pb = inputs.orszag_tang_2d(32, steps=8)
     dv = inputs.adjoint_perturbation(pb, seed=5)
     _, grad_k, _, _ = _rollout_grad(pb, dv, 8, k)
     _, grad_8, _, _ = _rollout_grad(pb, dv, 8, 8)
-    np.testing.assert_array_equal(grad_k, grad_8)
+    np.testing.assert_allclose(grad_k, grad_8, rtol=1e-11,
+                               atol=1e-11 * float(np.abs(grad_8).max()))
