@@ -3,8 +3,9 @@ ghost fill vs numpy padding, uniform-state preservation, exact conservation
 under periodic boundaries, translation / axis-permutation / reflection /
 point-inversion symmetry, closed-form boundary fluxes of the Brio-Wu tube,
 the decoupled linear (B_x, psi) subsystem against an independent upwind
-scheme, second-order convergence of linear waves to their closed forms, and
-the dual-number JVP against central finite differences.
+scheme, second-order convergence of linear waves to their closed forms, the
+dual-number JVP against central finite differences, and one RK2 step (both
+stages and the damping) rebuilt in numpy from the separately pinned pieces.
 """
 import math
 
@@ -284,3 +285,70 @@ def test_dual_jvp_matches_central_differences():
     dn = orc.run(U0 - eps * dU, g, 3, dts=r.dts, chs=r.chs).U
     fd = (up - dn) / (2 * eps)
     assert np.max(np.abs(fd - jvp)) <= 1e-6 * np.max(np.abs(jvp))
+
+
+# ------------------------------------------- one step from pinned pieces --
+def _rhs_from_pieces(W, g, ch):
+    """L(W) of Section 3.2's five steps, composed in numpy from the oracle's
+    separately pinned pieces: ghost fill (= numpy.pad), cons->prim, the
+    limited slope (hand values) with the flat fallback for a non-positive
+    face density or pressure, and the GLM + HLLD interface flux; the right-
+    hand side -(F_{i+1/2} - F_{i-1/2}) / dx_d summed over active d in x, y, z
+    order (the oracle's order, so the sums round alike)."""
+    Vp, _ = orc.cons_to_prim(orc.fill_ghosts(W, g), g)
+    gh = [g.ghost if n > 1 else 0 for n in g.n]
+    nx, ny, nz = g.n
+    L = np.zeros((9, nz, ny, nx))
+    for d in range(3):
+        n = g.n[d]
+        if n <= 1:
+            continue
+        ax = 3 - d  # array axes (var, z, y, x)
+
+        def cells(off):  # cells -1 .. n along d shifted by off; interior across
+            idx = [slice(None)] * 4
+            for a in range(3):
+                lo = gh[a] + (off - 1 if a == d else 0)
+                idx[3 - a] = slice(lo, lo + g.n[a] + (2 if a == d else 0))
+            return Vp[tuple(idx)]
+
+        v0, vm, vp = cells(0), cells(-1), cells(1)
+        sig = orc.limited_slope(v0 - vm, vp - v0, g.limiter)
+        plus, minus = v0 + 0.5 * sig, v0 - 0.5 * sig
+        bad = (plus[RHO] <= 0) | (minus[RHO] <= 0) | (plus[PRS] <= 0) | (minus[PRS] <= 0)
+        plus, minus = np.where(bad, v0, plus), np.where(bad, v0, minus)
+        # face f = 0..n between cells f-1 (its + value) and f (its - value)
+        VL = np.take(plus, np.arange(0, n + 1), axis=ax)
+        VR = np.take(minus, np.arange(1, n + 2), axis=ax)
+        F = orc.interface_flux(VL.reshape(9, -1), VR.reshape(9, -1), d, ch,
+                               g.gamma).reshape(VL.shape)
+        L -= (np.take(F, np.arange(1, n + 1), axis=ax) - np.take(F, np.arange(0, n), axis=ax)) \
+            / g.dx[d]
+    return L
+
+
+@pytest.mark.parametrize("pb", [
+    Problem("random_smooth", (7, 6, 5), seed=51, bc=(0, 0, 1, 1, 0, 0),
+            params={"psi_amp": 1.0}),
+    Problem("random_smooth", (9, 8, 1), seed=52, limiter=orc.LIM_MINMOD, bc=(1,) * 6),
+], ids=["3d_mc_mixed_bc", "2d_minmod_outflow"])
+def test_rk2_step_rebuilt_from_pinned_pieces(pb):
+    """U1 = U + dt L(U) (stage 1), U^{n+1} = U/2 + (U1 + dt L(U1))/2 (stage 2)
+    and psi times exp(-alpha c_h dt / dh_min) (the damping), with L rebuilt
+    from the pinned pieces, equal orc.stage and one orc.run step bit for bit
+    (same operations in the same order; the oracle is built without FMA
+    contraction)."""
+    g = grid_of(pb)
+    U = cons_of(pb)
+    dt, ch = orc.cfl_dt(U, g)
+    U1 = U + dt * _rhs_from_pieces(U, g, ch)
+    s1, cnt = orc.stage(U, g, dt, ch, 1)
+    assert cnt == (0, 0)
+    np.testing.assert_array_equal(s1, U1)
+    U2 = 0.5 * U + 0.5 * (U1 + dt * _rhs_from_pieces(U1, g, ch))
+    s2, _ = orc.stage(U1, g, dt, ch, 2, Un=U)
+    np.testing.assert_array_equal(s2, U2)
+    dh = min(g.dx[d] for d in range(3) if g.n[d] > 1)
+    U2[PSI] *= math.exp(-g.glm_alpha * ch * dt / dh)
+    r = orc.run(U, g, 1, dts=[dt], chs=[ch])
+    np.testing.assert_array_equal(r.U, U2)
