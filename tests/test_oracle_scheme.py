@@ -4,8 +4,9 @@ under periodic boundaries, translation / axis-permutation / reflection /
 point-inversion symmetry, closed-form boundary fluxes of the Brio-Wu tube,
 the decoupled linear (B_x, psi) subsystem against an independent upwind
 scheme, second-order convergence of linear waves to their closed forms, the
-dual-number JVP against central finite differences, and one RK2 step (both
-stages and the damping) rebuilt in numpy from the separately pinned pieces.
+dual-number JVP against central finite differences, and one RK2 (PLM) and
+one SSP-RK3 (WENO-Z) step, every stage and the damping, rebuilt in numpy
+from the separately pinned pieces.
 """
 import math
 
@@ -312,9 +313,14 @@ def _rhs_from_pieces(W, g, ch):
                 idx[3 - a] = slice(lo, lo + g.n[a] + (2 if a == d else 0))
             return Vp[tuple(idx)]
 
-        v0, vm, vp = cells(0), cells(-1), cells(1)
-        sig = orc.limited_slope(v0 - vm, vp - v0, g.limiter)
-        plus, minus = v0 + 0.5 * sig, v0 - 0.5 * sig
+        v0 = cells(0)
+        if g.limiter == orc.LIM_WENOZ:  # WENO-Z values at the cell's two faces
+            st = np.stack([cells(o) for o in (-2, -1, 0, 1, 2)]).reshape(5, -1)
+            plus = orc.wenoz_face(st).reshape(v0.shape)
+            minus = orc.wenoz_face(st[::-1]).reshape(v0.shape)
+        else:
+            sig = orc.limited_slope(v0 - cells(-1), cells(1) - v0, g.limiter)
+            plus, minus = v0 + 0.5 * sig, v0 - 0.5 * sig
         bad = (plus[RHO] <= 0) | (minus[RHO] <= 0) | (plus[PRS] <= 0) | (minus[PRS] <= 0)
         plus, minus = np.where(bad, v0, plus), np.where(bad, v0, minus)
         # face f = 0..n between cells f-1 (its + value) and f (its - value)
@@ -331,24 +337,34 @@ def _rhs_from_pieces(W, g, ch):
     Problem("random_smooth", (7, 6, 5), seed=51, bc=(0, 0, 1, 1, 0, 0),
             params={"psi_amp": 1.0}),
     Problem("random_smooth", (9, 8, 1), seed=52, limiter=orc.LIM_MINMOD, bc=(1,) * 6),
-], ids=["3d_mc_mixed_bc", "2d_minmod_outflow"])
-def test_rk2_step_rebuilt_from_pinned_pieces(pb):
-    """U1 = U + dt L(U) (stage 1), U^{n+1} = U/2 + (U1 + dt L(U1))/2 (stage 2)
-    and psi times exp(-alpha c_h dt / dh_min) (the damping), with L rebuilt
-    from the pinned pieces, equal orc.stage and one orc.run step bit for bit
-    (same operations in the same order; the oracle is built without FMA
+    Problem("random_smooth", (8, 7, 6), seed=53, limiter=orc.LIM_WENOZ, rk_order=3,
+            bc=(1, 1, 0, 0, 0, 0), params={"psi_amp": 1.0}),
+], ids=["3d_mc_mixed_bc", "2d_minmod_outflow", "3d_wenoz_rk3"])
+def test_step_rebuilt_from_pinned_pieces(pb):
+    """RK2: U1 = U + dt L(U), U^{n+1} = U/2 + (U1 + dt L(U1))/2; SSP-RK3 (Shu
+    & Osher): U1 as RK2, U2 = 3U/4 + (U1 + dt L(U1))/4, U^{n+1} = U/3 +
+    2(U2 + dt L(U2))/3; then psi times exp(-alpha c_h dt / dh_min) (the
+    damping).  With L rebuilt from the pinned pieces, each stage equals
+    orc.stage and the step equals one orc.run step, bit for bit (same
+    operations in the same order; the oracle is built without FMA
     contraction)."""
     g = grid_of(pb)
     U = cons_of(pb)
     dt, ch = orc.cfl_dt(U, g)
-    U1 = U + dt * _rhs_from_pieces(U, g, ch)
-    s1, cnt = orc.stage(U, g, dt, ch, 1)
-    assert cnt == (0, 0)
-    np.testing.assert_array_equal(s1, U1)
-    U2 = 0.5 * U + 0.5 * (U1 + dt * _rhs_from_pieces(U1, g, ch))
-    s2, _ = orc.stage(U1, g, dt, ch, 2, Un=U)
-    np.testing.assert_array_equal(s2, U2)
+    if g.rk_order == 3:
+        coeffs = [(0.0, 1.0), (0.75, 0.25), (1.0 / 3.0, 2.0 / 3.0)]
+    else:
+        coeffs = [(0.0, 1.0), (0.5, 0.5)]
+    W = U
+    for k, (a_n, a_w) in enumerate(coeffs):
+        s1 = W + dt * _rhs_from_pieces(W, g, ch)
+        nxt = s1 if k == 0 else a_n * U + a_w * s1
+        ref, cnt = orc.stage(W, g, dt, ch, k + 1, Un=None if k == 0 else U)
+        assert cnt == (0, 0)
+        np.testing.assert_array_equal(ref, nxt)
+        W = nxt
     dh = min(g.dx[d] for d in range(3) if g.n[d] > 1)
-    U2[PSI] *= math.exp(-g.glm_alpha * ch * dt / dh)
+    W = W.copy()
+    W[PSI] *= math.exp(-g.glm_alpha * ch * dt / dh)
     r = orc.run(U, g, 1, dts=[dt], chs=[ch])
-    np.testing.assert_array_equal(r.U, U2)
+    np.testing.assert_array_equal(r.U, W)
