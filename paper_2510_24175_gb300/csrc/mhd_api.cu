@@ -618,6 +618,7 @@ static int step_impl(mhd_ctx* c, double dt, double ch, const HostOut* ho) {
     int rc = ensure_lambda(c);
     if (rc != MHD_OK) return rc;
   }
+  c->stage1_valid = false;  // until this step has written its first stage
   mhd::PrepArgs a;
   a.dt_req = dt;
   a.ch_req = ch;
