@@ -605,6 +605,12 @@ static int copy_planes(mhd_ctx* c, double* dst, const double* src, int z0, int z
 
 static int step_impl(mhd_ctx* c, double dt, double ch, const HostOut* ho);
 
+// After an FP64 RK2 GLM step, U_b holds that step's first stage U1 (read by
+// mhd_get_stage1); RK3 and constrained transport use U_b otherwise.
+static bool keeps_stage1(const mhd_ctx* c) {
+  return c->esize == 8 && c->cfg.rk_order != 3 && c->cfg.divb == MHD_DIVB_GLM;
+}
+
 int mhd_step(mhd_ctx* c, double dt, double ch) { return step_impl(c, dt, ch, nullptr); }
 
 static int step_impl(mhd_ctx* c, double dt, double ch, const HostOut* ho) {
@@ -706,8 +712,7 @@ static int step_impl(mhd_ctx* c, double dt, double ch, const HostOut* ho) {
     }
   }
   c->lam_valid = true;
-  // U_b now holds this step's first stage U1 (RK2; read by mhd_get_stage1)
-  c->stage1_valid = c->esize == 8 && c->cfg.rk_order != 3 && c->cfg.divb == MHD_DIVB_GLM;
+  c->stage1_valid = keeps_stage1(c);
   return MHD_OK;
 }
 
@@ -753,6 +758,7 @@ int mhd_step_n(mhd_ctx* c, int nsteps) {
   }
   CK(c, cudaGraphLaunch(c->gexec, c->stream));
   c->lam_valid = true;
+  c->stage1_valid = keeps_stage1(c);  // also when the graph was replayed, not captured
   return MHD_OK;
 }
 

@@ -88,3 +88,27 @@ def test_graph_steps_with_profiling_and_argument_checks():
     with pytest.raises(m.MHDError) as e:
         a.step_n(-1)
     assert e.value.code == m.MHD_ERR_INVALID
+
+
+def test_stage1_after_graph_steps():
+    """mhd_get_stage1 after mhd_step_n returns the last step's first stage,
+    bitwise that of the same steps taken one by one, also when the captured
+    graph is replayed after a new set_state."""
+    import torch
+    m = _mhd()
+    pb = inputs.orszag_tang_3d(8).with_n((32, 16, 8))
+    a, b = _pair(pb)
+    V = torch.from_numpy(pb.prim()).cuda()
+    for rep in range(2):  # capture, then replay after set_state
+        if rep:
+            a.set_state(V, kind=m.MHD_PRIM)
+            b.set_state(V, kind=m.MHD_PRIM)
+            with pytest.raises(m.MHDError) as e:
+                a.get_stage1()
+            assert e.value.code == m.MHD_ERR_STATE
+        a.step_n(3)
+        for _ in range(3):
+            b.step()
+        _same(a, b)
+        np.testing.assert_array_equal(a.get_stage1().cpu().numpy(),
+                                      b.get_stage1().cpu().numpy())
