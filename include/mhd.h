@@ -24,7 +24,8 @@
  *   - All device work is enqueued on the context's CUDA stream and is
  *     asynchronous, except the calls documented as synchronising.
  *   - Return value: MHD_OK (0) or a negative MHD_ERR_* code; the context keeps
- *     a message for mhd_last_error().  Device-side faults of the numerics
+ *     a message for mhd_last_error() (calls without a context keep it per host
+ *     thread: mhd_last_error(NULL)).  Device-side faults of the numerics
  *     (non-finite state or time step) are recorded in a device status word and
  *     reported as MHD_ERR_NONFINITE by the next synchronising call.  No kernel
  *     traps.
@@ -298,7 +299,10 @@ int mhd_ensemble_autotune(mhd_ensemble* ens, int trial_steps);
 const char* mhd_ensemble_last_error(const mhd_ensemble* ens);
 int mhd_ensemble_destroy(mhd_ensemble* ens);
 
-/* Message of the last failing call on ctx (never NULL). */
+/* Message of the last failing call on ctx (never NULL).  ctx = NULL: the
+ * message of the calling host thread's last failing call that has no context
+ * (mhd_workspace_bytes, mhd_create, mhd_flux_batch, mhd_ensemble_create,
+ * mhd_ensemble_workspace_bytes, mhd_conserved_sums_noalloc). */
 const char* mhd_last_error(const mhd_ctx* ctx);
 
 /* Releases the context (not the workspace). */

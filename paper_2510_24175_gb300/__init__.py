@@ -122,7 +122,8 @@ def lib():
 
 def _check(rc: int, ctx=None, what: str = ""):
     if rc != MHD_OK:
-        msg = lib().mhd_last_error(ctx).decode() if ctx else what
+        # no context: the calling thread's last context-free message
+        msg = lib().mhd_last_error(ctx if ctx else None).decode()
         raise MHDError(rc, f"{what}: {msg}")
 
 

@@ -62,6 +62,18 @@ static int fail(mhd_ctx* c, int code, const char* fmt, ...) {
       return fail((ctx), MHD_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
   } while (0)
 
+namespace mhd {
+static thread_local char g_free_err[256] = "no error";
+
+int free_fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_free_err, sizeof(g_free_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+}  // namespace mhd
+
 static int validate(const mhd_config* c, char* msg, size_t len) {
   if (!c) {
     snprintf(msg, len, "null config");
@@ -255,7 +267,8 @@ int mhd_config_default(mhd_config* cfg) {
 int mhd_workspace_bytes(const mhd_config* cfg, size_t* bytes) {
   char msg[256];
   int rc = validate(cfg, msg, sizeof(msg));
-  if (rc != MHD_OK || !bytes) return MHD_ERR_INVALID;
+  if (rc != MHD_OK) return mhd::free_fail(rc, "invalid config: %s", msg);
+  if (!bytes) return mhd::free_fail(MHD_ERR_INVALID, "mhd_workspace_bytes: null bytes");
   mhd::Grid g;
   fill_grid(cfg, &g);
   const size_t es = cfg->precision == MHD_FP64 ? 8 : 4;
@@ -273,23 +286,19 @@ int mhd_workspace_bytes(const mhd_config* cfg, size_t* bytes) {
 
 int mhd_create(const mhd_config* cfg, void* d_workspace, size_t bytes, void* stream,
                mhd_ctx** out) {
-  if (!out) return MHD_ERR_INVALID;
+  if (!out) return mhd::free_fail(MHD_ERR_INVALID, "mhd_create: null out");
   *out = nullptr;
   char msg[256] = "";
   int rc = validate(cfg, msg, sizeof(msg));
-  if (rc != MHD_OK) {
-    fprintf(stderr, "mhd_create: %s\n", msg);
-    return rc;
-  }
+  if (rc != MHD_OK) return mhd::free_fail(rc, "mhd_create: invalid config: %s", msg);
   size_t need = 0;
   mhd_workspace_bytes(cfg, &need);
-  if (!d_workspace || bytes < need || ((uintptr_t)d_workspace & 255)) {
-    fprintf(stderr, "mhd_create: workspace %p of %zu bytes (need %zu, 256-byte aligned)\n",
-            d_workspace, bytes, need);
-    return MHD_ERR_NOMEM;
-  }
+  if (!d_workspace || bytes < need || ((uintptr_t)d_workspace & 255))
+    return mhd::free_fail(MHD_ERR_NOMEM,
+                          "mhd_create: workspace %p of %zu bytes (need %zu, 256-byte aligned)",
+                          d_workspace, bytes, need);
   mhd_ctx* c = new (std::nothrow) mhd_ctx();
-  if (!c) return MHD_ERR_NOMEM;
+  if (!c) return mhd::free_fail(MHD_ERR_NOMEM, "mhd_create: host allocation failed");
   c->cfg = *cfg;
   fill_grid(cfg, &c->grid);
   int dev = 0;
@@ -298,7 +307,7 @@ int mhd_create(const mhd_config* cfg, void* d_workspace, size_t bytes, void* str
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       nsm <= 0) {
     delete c;
-    return MHD_ERR_CUDA;
+    return mhd::free_fail(MHD_ERR_CUDA, "mhd_create: no usable CUDA device");
   }
   c->grid.nsm = nsm;
   c->esize = cfg->precision == MHD_FP64 ? 8 : 4;
@@ -372,7 +381,8 @@ int mhd_create(const mhd_config* cfg, void* d_workspace, size_t bytes, void* str
                                          : mhd::prepare_stage_kernels<float>(c->grid, ct);
     if (pe != cudaSuccess) {
       delete c;
-      return MHD_ERR_CUDA;
+      return mhd::free_fail(MHD_ERR_CUDA, "mhd_create: kernel attributes: %s",
+                            cudaGetErrorString(pe));
     }
   }
   c->xfer_ready = false;
@@ -387,7 +397,7 @@ int mhd_create(const mhd_config* cfg, void* d_workspace, size_t bytes, void* str
   cudaError_t e = cudaMemsetAsync(c->scal, 0, sizeof(Scalars), c->stream);
   if (e != cudaSuccess) {
     delete c;
-    return MHD_ERR_CUDA;
+    return mhd::free_fail(MHD_ERR_CUDA, "mhd_create: %s", cudaGetErrorString(e));
   }
   *out = c;
   return MHD_OK;
@@ -870,7 +880,7 @@ int mhd_flux_batch(const void* VL, const void* VR, void* F, long long nface, int
                    double gamma, int precision, void* stream) {
   if (!VL || !VR || !F || nface < 0 || dir < 0 || dir > 2 || !(ch > 0.0) || !(gamma > 1.0) ||
       (precision != MHD_FP64 && precision != MHD_FP32))
-    return MHD_ERR_INVALID;
+    return mhd::free_fail(MHD_ERR_INVALID, "mhd_flux_batch: bad argument");
   if (nface == 0) return MHD_OK;
   cudaError_t e;
   if (precision == MHD_FP64)
@@ -881,7 +891,9 @@ int mhd_flux_batch(const void* VL, const void* VR, void* F, long long nface, int
     e = mhd::launch_flux_batch<float>(static_cast<const float*>(VL),
                                       static_cast<const float*>(VR), static_cast<float*>(F),
                                       nface, dir, ch, gamma, static_cast<cudaStream_t>(stream));
-  return e == cudaSuccess ? MHD_OK : MHD_ERR_CUDA;
+  if (e != cudaSuccess)
+    return mhd::free_fail(MHD_ERR_CUDA, "mhd_flux_batch: %s", cudaGetErrorString(e));
+  return MHD_OK;
 }
 
 static int adjoint_impl(mhd_ctx* c, const double* U_n, const double* U1, const double* lam_np1,
@@ -948,7 +960,7 @@ int mhd_profile_read(mhd_ctx* c, long long counts[6], double ms[6]) {
   return MHD_OK;
 }
 
-const char* mhd_last_error(const mhd_ctx* c) { return c ? c->err : "null context"; }
+const char* mhd_last_error(const mhd_ctx* c) { return c ? c->err : mhd::g_free_err; }
 
 int mhd_destroy(mhd_ctx* c) {
   if (!c) return MHD_ERR_INVALID;

@@ -167,15 +167,24 @@ static int efail(mhd_ensemble* e, int code, const char* fmt, ...) {
       return efail((e), MHD_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
   } while (0)
 
+// Each box: a valid 3-D MHD_FP32 config with RK2, PLM and GLM, no adjoint.
+// A failure leaves its reason for mhd_last_error(NULL).
 static int ens_validate(const mhd_config* cfgs, int nbox) {
-  if (!cfgs || nbox < 1) return MHD_ERR_INVALID;
+  if (!cfgs || nbox < 1)
+    return mhd::free_fail(MHD_ERR_INVALID, "ensemble: no boxes (nbox = %d)", nbox);
   for (int b = 0; b < nbox; ++b) {
     size_t bytes;
-    if (mhd_workspace_bytes(&cfgs[b], &bytes) != MHD_OK) return MHD_ERR_INVALID;
+    if (mhd_workspace_bytes(&cfgs[b], &bytes) != MHD_OK) {
+      char why[256];  // the message is rewritten below: copy it out first
+      snprintf(why, sizeof(why), "%s", mhd_last_error(nullptr));
+      return mhd::free_fail(MHD_ERR_INVALID, "ensemble box %d: %s", b, why);
+    }
     if (cfgs[b].precision != MHD_FP32 || cfgs[b].n[1] < 2 || cfgs[b].n[2] < 2 ||
         (cfgs[b].flags & MHD_FLAG_ADJOINT) || cfgs[b].rk_order != 2 ||
         cfgs[b].limiter == MHD_LIM_WENOZ || cfgs[b].divb != MHD_DIVB_GLM)
-      return MHD_ERR_INVALID;
+      return mhd::free_fail(MHD_ERR_INVALID,
+                            "ensemble box %d: needs a 3-D MHD_FP32 RK2 PLM GLM config "
+                            "without MHD_FLAG_ADJOINT", b);
   }
   return MHD_OK;
 }
@@ -241,7 +250,8 @@ static cudaError_t ens_launch(mhd_ensemble* e, int nsteps, cudaStream_t s) {
 extern "C" {
 
 int mhd_ensemble_workspace_bytes(const mhd_config* cfgs, int nbox, size_t* bytes) {
-  if (!bytes || ens_validate(cfgs, nbox) != MHD_OK) return MHD_ERR_INVALID;
+  if (!bytes) return mhd::free_fail(MHD_ERR_INVALID, "mhd_ensemble_workspace_bytes: null bytes");
+  if (ens_validate(cfgs, nbox) != MHD_OK) return MHD_ERR_INVALID;
   size_t total = 0;
   for (int b = 0; b < nbox; ++b) {
     size_t s = 0;
@@ -255,17 +265,17 @@ int mhd_ensemble_workspace_bytes(const mhd_config* cfgs, int nbox, size_t* bytes
 
 int mhd_ensemble_create(const mhd_config* cfgs, int nbox, void* d_workspace, size_t bytes,
                         void* stream, mhd_ensemble** out) {
-  if (!out) return MHD_ERR_INVALID;
+  if (!out) return mhd::free_fail(MHD_ERR_INVALID, "mhd_ensemble_create: null out");
   *out = nullptr;
-  if (ens_validate(cfgs, nbox) != MHD_OK) {
-    fprintf(stderr, "mhd_ensemble_create: boxes must be valid 3-D MHD_FP32 configs\n");
-    return MHD_ERR_INVALID;
-  }
+  if (ens_validate(cfgs, nbox) != MHD_OK) return MHD_ERR_INVALID;
   size_t need = 0;
   mhd_ensemble_workspace_bytes(cfgs, nbox, &need);
-  if (!d_workspace || bytes < need || ((uintptr_t)d_workspace & 255)) return MHD_ERR_NOMEM;
+  if (!d_workspace || bytes < need || ((uintptr_t)d_workspace & 255))
+    return mhd::free_fail(MHD_ERR_NOMEM,
+                          "mhd_ensemble_create: workspace %p of %zu bytes (need %zu, "
+                          "256-byte aligned)", d_workspace, bytes, need);
   mhd_ensemble* e = new (std::nothrow) mhd_ensemble();
-  if (!e) return MHD_ERR_NOMEM;
+  if (!e) return mhd::free_fail(MHD_ERR_NOMEM, "mhd_ensemble_create: host allocation failed");
   e->nbox = nbox;
   e->stream = static_cast<cudaStream_t>(stream);
   e->gexec = nullptr;
@@ -274,7 +284,7 @@ int mhd_ensemble_create(const mhd_config* cfgs, int nbox, void* d_workspace, siz
   e->cap = nullptr;
   if (cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking) != cudaSuccess) {
     delete e;
-    return MHD_ERR_CUDA;
+    return mhd::free_fail(MHD_ERR_CUDA, "mhd_ensemble_create: stream creation failed");
   }
   snprintf(e->err, sizeof(e->err), "no error");
   char* p = static_cast<char*>(d_workspace);
@@ -340,7 +350,8 @@ int mhd_ensemble_create(const mhd_config* cfgs, int nbox, void* d_workspace, siz
     for (auto* x : e->ctx) mhd_destroy(x);
     cudaStreamDestroy(e->cap);
     delete e;
-    return MHD_ERR_CUDA;
+    return mhd::free_fail(MHD_ERR_CUDA, "mhd_ensemble_create: kernel set-up failed (%s)",
+                          cudaGetErrorString(ce));
   }
   e->grid_ctas = per_sm * nsm;
   *out = e;

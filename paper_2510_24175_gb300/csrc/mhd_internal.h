@@ -11,6 +11,11 @@
 
 namespace mhd {
 
+// Message of a failing call that has no context (configuration checks,
+// mhd_create, mhd_flux_batch, mhd_ensemble_create, the no-alloc sums): kept
+// per host thread, returned by mhd_last_error(NULL).  Returns code.
+int free_fail(int code, const char* fmt, ...);
+
 // Geometry + physics of one context, shared by all launchers.
 struct Grid {
   int n[3];

@@ -32,15 +32,16 @@ double* g_scratch_addr[kMaxDevices] = {};
 // device (host code cannot use the symbol itself as a device pointer).
 int scratch_address(double** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MHD_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return mhd::free_fail(MHD_ERR_CUDA, "mhd_conserved_sums_noalloc: no usable device");
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_sums_scratch);
     if (e != cudaSuccess || !p) {
-      fprintf(stderr, "mhd_conserved_sums_noalloc: cudaGetSymbolAddress failed: %s\n",
-              cudaGetErrorString(e));
-      return MHD_ERR_CUDA;
+      return mhd::free_fail(MHD_ERR_CUDA,
+                            "mhd_conserved_sums_noalloc: cudaGetSymbolAddress failed: %s",
+                            cudaGetErrorString(e));
     }
     g_scratch_addr[dev] = static_cast<double*>(p);
   }
@@ -52,10 +53,10 @@ int scratch_address(double** out) {
 
 extern "C" int mhd_conserved_sums_noalloc(const mhd_config* cfg, const void* U, double out[8],
                                           void* stream) {
-  if (!cfg || !U || !out) return MHD_ERR_INVALID;
-  if (cfg->precision != MHD_FP64 && cfg->precision != MHD_FP32) return MHD_ERR_INVALID;
+  if (!cfg || !U || !out)
+    return mhd::free_fail(MHD_ERR_INVALID, "mhd_conserved_sums_noalloc: null argument");
   size_t unused = 0;
-  if (mhd_workspace_bytes(cfg, &unused) != MHD_OK) return MHD_ERR_INVALID;  // validates cfg
+  if (mhd_workspace_bytes(cfg, &unused) != MHD_OK) return MHD_ERR_INVALID;  // its message
   mhd::Grid g{};
   long long ncell = 1;
   for (int d = 0; d < 3; ++d) {
@@ -66,11 +67,10 @@ extern "C" int mhd_conserved_sums_noalloc(const mhd_config* cfg, const void* U, 
   g.ncell = ncell;
   const long long nparts = (ncell + kCellsPerPartial - 1) / kCellsPerPartial;
   if (nparts > kMaxPartials) {
-    fprintf(stderr,
-            "mhd_conserved_sums_noalloc: %lld cells exceed the fixed scratch (at most %lld "
-            "cells); use mhd_conserved_sums with a workspace\n",
-            ncell, (long long)kMaxPartials * kCellsPerPartial);
-    return MHD_ERR_NOMEM;
+    return mhd::free_fail(MHD_ERR_NOMEM,
+                          "mhd_conserved_sums_noalloc: %lld cells exceed the fixed scratch (at "
+                          "most %lld cells); use mhd_conserved_sums with a workspace",
+                          ncell, (long long)kMaxPartials * kCellsPerPartial);
   }
   double* scratch = nullptr;
   int rc = scratch_address(&scratch);
@@ -86,10 +86,10 @@ extern "C" int mhd_conserved_sums_noalloc(const mhd_config* cfg, const void* U, 
   else
     e = mhd::launch_sums<float>(g, static_cast<const float*>(U), scratch, (int)nparts, results,
                                 s);
-  if (e != cudaSuccess) return MHD_ERR_CUDA;
-  if (cudaMemcpyAsync(out, results, 8 * sizeof(double), cudaMemcpyDeviceToHost, s) !=
-      cudaSuccess)
-    return MHD_ERR_CUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, results, 8 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess)
+    return mhd::free_fail(MHD_ERR_CUDA, "mhd_conserved_sums_noalloc: %s", cudaGetErrorString(e));
   return MHD_OK;
 }

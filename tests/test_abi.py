@@ -77,3 +77,47 @@ def test_flux_batch_rejects_bad_arguments(built_lib):
     import paper_2510_24175_gb300 as m
     L = m.lib()
     assert L.mhd_flux_batch(None, None, None, 10, 0, 1.0, 5 / 3, 0, None) == m.MHD_ERR_INVALID
+
+
+def test_context_free_failures_leave_a_message(built_lib):
+    """Calls without a context (configuration checks, flux batch, ensemble
+    sizing) leave the reason of a failure for mhd_last_error(NULL), per host
+    thread; the binding puts it into the raised error."""
+    import ctypes
+    import threading
+    import paper_2510_24175_gb300 as m
+    L = m.lib()
+    cfg = m.mhd_config_default()
+    cfg.n[0], cfg.n[1], cfg.n[2] = 8, 1, 8
+    with pytest.raises(m.MHDError) as e:
+        m.mhd_workspace_bytes(cfg)
+    assert "ny = 1 needs nz = 1" in str(e.value)
+    cfg = m.mhd_config_default()
+    cfg.n[0] = 8
+    cfg.cfl = 1.5
+    with pytest.raises(m.MHDError) as e:
+        m.mhd_workspace_bytes(cfg)
+    assert "cfl" in str(e.value)
+    assert L.mhd_flux_batch(None, None, None, 10, 0, 1.0, 5 / 3, 0, None) == m.MHD_ERR_INVALID
+    assert L.mhd_last_error(None) == b"mhd_flux_batch: bad argument"
+    # ensemble: box 1 is FP64, which the batched kernel does not take
+    boxes = (m.mhd_config * 2)()
+    for b in range(2):
+        boxes[b] = m.mhd_config_default()
+        boxes[b].n[0] = boxes[b].n[1] = boxes[b].n[2] = 16
+        boxes[b].precision = m.MHD_FP32
+    boxes[1].precision = m.MHD_FP64
+    nb = ctypes.c_size_t(0)
+    assert L.mhd_ensemble_workspace_bytes(boxes, 2, ctypes.byref(nb)) == m.MHD_ERR_INVALID
+    assert L.mhd_last_error(None).startswith(b"ensemble box 1:")
+    boxes[1].precision = m.MHD_FP32
+    boxes[1].n[0] = 1
+    assert L.mhd_ensemble_workspace_bytes(boxes, 2, ctypes.byref(nb)) == m.MHD_ERR_INVALID
+    assert L.mhd_last_error(None) == b"ensemble box 1: invalid config: x must be active (nx >= 2)"
+    # another thread keeps its own message
+    seen = []
+    t = threading.Thread(target=lambda: seen.append(L.mhd_last_error(None)))
+    t.start()
+    t.join()
+    assert seen == [b"no error"]
+    assert L.mhd_last_error(None) == b"ensemble box 1: invalid config: x must be active (nx >= 2)"
