@@ -121,3 +121,44 @@ def test_context_free_failures_leave_a_message(built_lib):
     t.join()
     assert seen == [b"no error"]
     assert L.mhd_last_error(None) == b"ensemble box 1: invalid config: x must be active (nx >= 2)"
+
+
+def _paper_configs():
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_benchmark_configs.txt")
+    rows = []
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            name, grid, rec, rk, divb, prec, _ = [f.strip() for f in line.split("|")]
+            rows.append((name, tuple(int(x) for x in grid.split()), rec, rk, divb, prec))
+    return rows
+
+
+def test_paper_benchmark_configs_are_accepted(built_lib):
+    """The paper's stated gPLUTO benchmark configurations (Section 4.2;
+    tests/golden/paper_benchmark_configs.txt) are valid configurations of the
+    library, and its memory statement holds for this layout: divergence
+    cleaning needs less device memory than constrained transport, which let
+    the strong-scaling runs take a slightly larger grid (832^2 x 416 with GLM
+    needs no more than 704^2 x 352 with CT).  The per-node grids of both fit
+    one GB300 (284,208 MiB)."""
+    import paper_2510_24175_gb300 as m
+    m.lib()
+    rows = _paper_configs()
+    assert len(rows) == 4
+    need = {}
+    for name, n, rec, rk, divb, prec in rows:
+        cfg = m.mhd_config_default()
+        cfg.n[0], cfg.n[1], cfg.n[2] = n
+        cfg.limiter = {"WENOZ": m.MHD_LIM_WENOZ}[rec]
+        cfg.rk_order = {"RK3": 3}[rk]
+        cfg.divb = {"CT": m.MHD_DIVB_CT, "GLM": m.MHD_DIVB_GLM}[divb]
+        cfg.precision = {"FP64": m.MHD_FP64}[prec]
+        need[name] = m.mhd_workspace_bytes(cfg)
+        cfg.divb = m.MHD_DIVB_GLM if cfg.divb == m.MHD_DIVB_CT else m.MHD_DIVB_CT
+        other = m.mhd_workspace_bytes(cfg)
+        glm, ct = (need[name], other) if divb == "GLM" else (other, need[name])
+        assert glm < ct, name
+    assert need["strong_scaling_group1_base"] <= need["orszag_tang_weak_scaling_per_node"]
+    gb300 = 284208 * 2 ** 20
+    assert need["orszag_tang_weak_scaling_per_node"] < gb300
+    assert need["strong_scaling_group1_base"] < gb300
