@@ -149,7 +149,9 @@ int mhd_divb_max(mhd_ctx* ctx, double* out);
  * dt = cfl / (c_h sum_d 1/dx_d)).  Synchronises.  Either pointer may be NULL. */
 int mhd_dt(mhd_ctx* ctx, double* dt, double* ch);
 
-/* One Runge-Kutta step.  RK2:  U1 = U + dt L(U);  U' = (U + U1 + dt L(U1))/2.
+/* One Runge-Kutta step (Section 3.2: every stage runs the five steps listed
+ * at the top of this file to form L; SSP-RK3 is the integrator of the
+ * paper's runs, Section 4.2).  RK2:  U1 = U + dt L(U);  U' = (U + U1 + dt L(U1))/2.
  * SSP-RK3 (rk_order 3):  U1 = U + dt L(U);  U2 = 3/4 U + 1/4 (U1 + dt L(U1));
  * U' = 1/3 U + 2/3 (U2 + dt L(U2)).  GLM: then psi' *= exp(-glm_alpha c_h dt /
  * dh_min).  CT: the face field takes the same stages (its L is -curl E), and
@@ -208,7 +210,9 @@ int mhd_flux_batch(const void* VL, const void* VR, void* F, long long nface, int
                    double ch, double gamma, int precision, void* stream);
 
 /* Discrete adjoint of one RK2 step (reverse-mode derivative of mhd_step with
- * dt and c_h frozen):  lam_n = (dU^{n+1}/dU^n)^T lam_np1.  Needs RK2 and a
+ * dt and c_h frozen):  lam_n = (dU^{n+1}/dU^n)^T lam_np1.  The paper has no
+ * adjoint; this differentiates the step of Section 3.2 as mhd_step computes
+ * it.  Needs RK2 and a
  * PLM limiter (MHD_LIM_FLAT / MINMOD / MC).
  * U_n: the step's input state; lam_np1, lam_n: adjoints; all device float64
  * arrays [9][nz][ny][nx].  lam_n may not alias lam_np1.  Needs a context
