@@ -192,10 +192,23 @@ int mhd_step_host(mhd_ctx* ctx, const double* U_in, double* U_out, double dt, do
  * MHD_ERR_NONFINITE if the device flagged a non-finite dt or state. */
 int mhd_step_info(mhd_ctx* ctx, double out[4]);
 
-/* Floor activations since set_state: counters[0] = rho floor hits,
- * counters[1] = p floor hits; counters[2] = device status bits.
- * Synchronises. */
-int mhd_counters(mhd_ctx* ctx, long long counters[3]);
+/* mhd_step_info without the synchronisation: enqueues a copy of (t, dt,
+ * c_h, steps) of the last step into d_out, 4 doubles of device memory, on the
+ * context's stream (e.g. to record a rollout's time steps without a host
+ * round trip per step). */
+int mhd_step_record(mhd_ctx* ctx, double* d_out);
+
+/* Counters since set_state (synchronises), each counted once per Runge-Kutta
+ * stage for every cell whose conversion of that stage's input (step 2 of
+ * the stage, Section 3.2) took the branch; conversions inside the wave-speed
+ * reduction are not counted:
+ *   counters[0]: density floor (rho < rho_floor: rho = rho_floor);
+ *   counters[1]: pressure floor (p < p_floor: p = p_floor);
+ *   counters[2]: device status bits (non-zero: a non-finite dt or c_h);
+ *   counters[3]: MHD_FP32 only: cells whose FP32 pressure fell below p_floor
+ *                or below 1e-3 (gamma-1) E and was recomputed in FP64 (the
+ *                floor decision then taken in FP64). */
+int mhd_counters(mhd_ctx* ctx, long long counters[4]);
 
 /* Conservation sums: sum over cells of (rho, mx, my, mz, E, Bx, By, Bz) times
  * the cell volume, accumulated in FP64 in a fixed order (deterministic).
@@ -253,21 +266,22 @@ int mhd_profile_enable(mhd_ctx* ctx, int enable);
 int mhd_profile_read(mhd_ctx* ctx, long long counts[6], double ms[6]);
 
 /* Conservation sums for callers that can't allocate device memory: a host
- * application whose GPU memory is owned by another allocator, a code that
- * forbids allocations once its time loop runs, or a hook running while the
- * caller captures a stream (cudaMalloc is not allowed there in the default
- * capture mode).  The paper has no counterpart; this is a library service.
+ * application whose GPU memory is owned by another allocator, or a code that
+ * forbids allocations once its time loop runs.  The paper has no
+ * counterpart; this is a library service.
  * Same result as mhd_conserved_sums() (up to the summation order) for a state
  * U held by the caller in device memory: float64 (cfg->precision = MHD_FP64)
  * or float32 (MHD_FP32), conservative, [9][nz][ny][nx]; out: 8 host doubles.
  * Needs no context and no workspace and allocates nothing: the scratch is a
  * fixed 1 MiB device array inside the library (16384 partial sums), which
  * every GPU that loads the library holds until the process exits.  Grids of
- * more than 16384 * 32768 cells are rejected with MHD_ERR_NOMEM.  The first
- * call on each device looks up that array's device address; make that first
- * call before any stream capture.  All calls share the one array: calls that
- * overlap on the GPU (other streams, other host threads) race.  Enqueues on
- * stream and synchronises it. */
+ * more than 16384 * 32768 cells are rejected with MHD_ERR_NOMEM.  Each call
+ * looks up that array's device address on the current device (nothing is
+ * cached, so a cudaDeviceReset between calls is harmless).  All calls share
+ * the one array: calls that overlap on the GPU (other streams, other host
+ * threads) race.  Enqueues on stream and synchronises it; a stream that is
+ * being captured is refused with MHD_ERR_INVALID before anything is
+ * enqueued. */
 int mhd_conserved_sums_noalloc(const mhd_config* cfg, const void* U, double out[8],
                                void* stream);
 

@@ -428,6 +428,17 @@ struct Field {
   const S& at(int v, int i, int j, int k) const { return a[idx(v, i, j, k)]; }
 };
 
+// Cell c of f is an interior cell (not a ghost).  Reading (the paper does not
+// discuss floors): floor activations are counted once per stage for each
+// interior cell, from its conversion of the stage input; the ghost copies'
+// conversions and those of the time-step reduction are not counted.
+template <class S>
+bool interior(const Field<S>& f, const int c[3]) {
+  for (int d = 0; d < 3; ++d)
+    if (c[d] < 0 || c[d] >= f.n[d]) return false;
+  return true;
+}
+
 // Step 1 of the stage (Section 3.2, "boundary exchange/calculation"): fill the
 // ghost zones.  Periodic: ghost(i) = U(i mod N).  Outflow (zero gradient):
 // ghost = nearest interior cell.  Dimension by dimension, each pass covering
@@ -540,7 +551,7 @@ void rk_stage(const Params& P, Field<S>& W, const Field<S>* Un, double dt, doubl
         for (c[0] = -W.g[0]; c[0] < W.n[0] + W.g[0]; ++c[0]) {
           S u[NV], v[NV];
           for (int k = 0; k < NV; ++k) u[k] = W.at(k, c[0], c[1], c[2]);
-          cons_to_prim(u, v, P, cnt);
+          cons_to_prim(u, v, P, interior(W, c) ? cnt : nullptr);
           for (int k = 0; k < NV; ++k) V.at(k, c[0], c[1], c[2]) = v[k];
         }
   }
@@ -806,7 +817,7 @@ void ct_stage(const Params& P, Field<double>& W, const Faces& bw, const Field<do
         for (c[0] = -W.g[0]; c[0] < W.n[0] + W.g[0]; ++c[0]) {
           double u[NV], v[NV];
           for (int k = 0; k < NV; ++k) u[k] = W.at(k, c[0], c[1], c[2]);
-          cons_to_prim(u, v, P, cnt);
+          cons_to_prim(u, v, P, interior(W, c) ? cnt : nullptr);
           for (int k = 0; k < NV; ++k) V.at(k, c[0], c[1], c[2]) = v[k];
         }
   }
@@ -1162,7 +1173,7 @@ double orc_run(const orc_params* p, double* U, int nsteps, double cfl, double t0
       dt = dts[s];
       ch = chs[s];
     } else {
-      ch = max_speed(P, f, &cnt);
+      ch = max_speed(P, f, (Counters*)nullptr);
       dt = cfl / (ch * inv_sum);
       if (t_end > 0.0 && t + dt > t_end) dt = t_end - t;
       if (dts) {
@@ -1237,7 +1248,7 @@ double orc_ct_run(const orc_params* p, double* U, double* b, int nsteps, double 
       dt = dts[s];
       ch = chs[s];
     } else {
-      ch = max_speed(P, f, &cnt);
+      ch = max_speed(P, f, (Counters*)nullptr);
       dt = cfl / (ch * inv_sum);
       if (t_end > 0.0 && t + dt > t_end) dt = t_end - t;
       if (dts) {

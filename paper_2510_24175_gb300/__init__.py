@@ -35,7 +35,7 @@ MHD_DIVB_GLM, MHD_DIVB_CT = 0, 1
 
 EXPORTED = ["mhd_config_default", "mhd_workspace_bytes", "mhd_create", "mhd_set_stream",
             "mhd_set_state", "mhd_get_state", "mhd_dt", "mhd_step", "mhd_step_host",
-            "mhd_step_n", "mhd_step_info",
+            "mhd_step_n", "mhd_step_info", "mhd_step_record",
             "mhd_counters", "mhd_conserved_sums", "mhd_flux_batch", "mhd_adjoint_step",
             "mhd_adjoint_step_stage1", "mhd_get_stage1",
             "mhd_profile_enable", "mhd_profile_read", "mhd_conserved_sums_noalloc",
@@ -91,6 +91,7 @@ def lib():
         L.mhd_step_host.argtypes = [vp, vp, vp, d, d]
         L.mhd_step_n.argtypes = [vp, i]
         L.mhd_step_info.argtypes = [vp, dp]
+        L.mhd_step_record.argtypes = [vp, vp]
         L.mhd_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
         L.mhd_conserved_sums.argtypes = [vp, dp]
         L.mhd_flux_batch.argtypes = [vp, vp, vp, ctypes.c_longlong, i, d, d, i, vp]
@@ -199,6 +200,12 @@ def mhd_step(ctx, dt: float = 0.0, ch: float = 0.0):
     _check(lib().mhd_step(ctx, float(dt), float(ch)), ctx, "mhd_step")
 
 
+def mhd_step_record(ctx, out):
+    """(t, dt, c_h, steps) of the last step into ``out`` (4 float64 values of
+    a CUDA tensor), enqueued without synchronising."""
+    _check(lib().mhd_step_record(ctx, _ptr(out)), ctx, "mhd_step_record")
+
+
 def mhd_step_n(ctx, nsteps: int):
     _check(lib().mhd_step_n(ctx, int(nsteps)), ctx, "mhd_step_n")
 
@@ -233,7 +240,14 @@ def mhd_destroy(ctx):
 def mhd_conserved_sums_noalloc(cfg: mhd_config, U) -> np.ndarray:
     """Conservation sums of a caller-held CUDA state tensor (float64 or
     float32 to match cfg.precision) without a context or workspace; the
-    library's fixed internal scratch is used and nothing is allocated."""
+    library's fixed internal scratch is used and nothing is allocated.  The
+    current stream must not be capturing (the call synchronises it)."""
+    torch = _torch()
+    want = torch.float64 if cfg.precision == MHD_FP64 else torch.float32
+    ncell = int(cfg.n[0]) * int(cfg.n[1]) * int(cfg.n[2])
+    assert U.is_cuda and U.is_contiguous(), "U must be a contiguous CUDA tensor"
+    assert U.dtype == want, f"U is {U.dtype}, the config's precision needs {want}"
+    assert U.numel() >= 9 * ncell, f"U holds {U.numel()} values, the grid needs {9 * ncell}"
     out = (ctypes.c_double * 8)()
     _check(lib().mhd_conserved_sums_noalloc(ctypes.byref(cfg), _ptr(U), out, _stream_ptr()),
            what="mhd_conserved_sums_noalloc")
@@ -397,10 +411,21 @@ class MHD:
         _check(lib().mhd_step_info(self.ctx, out), self.ctx, "mhd_step_info")
         return {"t": out[0], "dt": out[1], "ch": out[2], "steps": int(out[3])}
 
+    def step_record(self, out):
+        """Enqueues (t, dt, c_h, steps) of the last step into ``out``, a
+        float64 CUDA tensor of 4 contiguous values (no synchronisation)."""
+        torch = _torch()
+        assert out.is_cuda and out.dtype == torch.float64 and out.is_contiguous()
+        assert out.numel() >= 4
+        mhd_step_record(self.ctx, out)
+
     def counters(self):
-        out = (ctypes.c_longlong * 3)()
+        """Per-stage, per-cell counts of the floor branches of cons->prim
+        (mhd_counters): rho floor, p floor, and (FP32) the pressure
+        recomputed in FP64; plus the device status bits."""
+        out = (ctypes.c_longlong * 4)()
         _check(lib().mhd_counters(self.ctx, out), self.ctx, "mhd_counters")
-        return {"rho_floor": out[0], "p_floor": out[1], "status": out[2]}
+        return {"rho_floor": out[0], "p_floor": out[1], "status": out[2], "p_f64": out[3]}
 
     def conserved_sums(self) -> np.ndarray:
         out = (ctypes.c_double * 8)()

@@ -1,7 +1,9 @@
 """Differentiable RK2 rollouts: a torch.autograd.Function over the C ABI.
 
 forward: advances the state nsteps CFL steps with mhd_step, keeping a copy of
-the state every k steps (checkpoints) and recording each step's dt and c_h.
+the state every k steps (checkpoints) and recording each step's dt and c_h on
+the device (mhd_step_record: no host round trip per step; the record is read
+once, when the forward pass ends).
 backward: for each k-step segment, last first, recomputes the segment's
 states from its checkpoint with the recorded dt and c_h (mhd_step with
 explicit dt, ch: bitwise the same states), keeping each recomputed step's
@@ -29,15 +31,18 @@ class MHDRollout(torch.autograd.Function):
     def forward(ctx, U0, solver: MHD, nsteps: int, k: int):
         assert solver.config.flags & MHD_FLAG_ADJOINT, "solver needs MHD_FLAG_ADJOINT"
         solver.set_state(U0.detach().contiguous())
-        ckpts, dts, chs = [], [], []
+        ckpts = []
+        rec = torch.empty((max(nsteps, 1), 4), dtype=torch.float64, device=U0.device)
         for n in range(nsteps):
             if n % k == 0:
                 ckpts.append(solver.get_state())
             solver.step()
-            info = solver.step_info()
-            dts.append(info["dt"])
-            chs.append(info["ch"])
+            solver.step_record(rec[n])
         UN = solver.get_state()
+        solver.step_info()  # one synchronisation: raises if the device flagged a fault
+        rec = rec.cpu().numpy()
+        dts = [float(x) for x in rec[:nsteps, 1]]
+        chs = [float(x) for x in rec[:nsteps, 2]]
         ctx.solver, ctx.nsteps, ctx.k = solver, nsteps, k
         ctx.ckpts, ctx.dts, ctx.chs = ckpts, dts, chs
         return UN
@@ -72,17 +77,3 @@ def rollout_solver(problem) -> MHD:
     """An adjoint-capable FP64 solver for a Problem."""
     return MHD(Config.from_problem(problem, precision=0, flags=MHD_FLAG_ADJOINT))
 
-
-def kinetic_energy(U: torch.Tensor, cell_volume: float) -> torch.Tensor:
-    """J = sum over cells of |m|^2 / (2 rho) times the cell volume."""
-    return 0.5 * ((U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0]).sum() * cell_volume
-
-
-def prim_to_cons_torch(V: torch.Tensor, gamma: float) -> torch.Tensor:
-    """Differentiable primitive -> conservative map for parameterising
-    initial conditions in user code (e.g. a velocity perturbation)."""
-    rho = V[0]
-    v2 = V[1] ** 2 + V[2] ** 2 + V[3] ** 2
-    b2 = V[4] ** 2 + V[5] ** 2 + V[6] ** 2
-    E = V[7] / (gamma - 1.0) + 0.5 * rho * v2 + 0.5 * b2
-    return torch.stack([rho, rho * V[1], rho * V[2], rho * V[3], V[4], V[5], V[6], E, V[8]])

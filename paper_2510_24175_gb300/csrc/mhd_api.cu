@@ -235,7 +235,7 @@ static int ct_stage(mhd_ctx* c, int kind, int cls, void* win, void* un, void* ou
   CK(c, mhd::launch_ct_faces<T>(c->grid, kind == 1, edge, fw, fn, fo, &c->scal->sc, an, aw,
                                 c->stream));
   CK(c, mhd::launch_ct_cells<T>(c->grid, kind == 2, fo, static_cast<T*>(out),
-                                &c->scal->lam_bits, c->scal->floor_cnt, c->stream));
+                                &c->scal->lam_bits, c->stream));
   return MHD_OK;
 }
 
@@ -567,12 +567,10 @@ static int ensure_lambda(mhd_ctx* c) {
   ProfScope ps(c, 3);
   if (c->esize == 8)
     CK(c, mhd::launch_max_speed<double>(c->grid, static_cast<const double*>(c->Ua),
-                                        &c->scal->lam_bits, &c->scal->est_bits,
-                                        c->scal->floor_cnt, c->stream));
+                                        &c->scal->lam_bits, &c->scal->est_bits, c->stream));
   else
     CK(c, mhd::launch_max_speed<float>(c->grid, static_cast<const float*>(c->Ua),
-                                       &c->scal->lam_bits, nullptr, c->scal->floor_cnt,
-                                       c->stream));
+                                       &c->scal->lam_bits, nullptr, c->stream));
   c->lam_valid = true;
   return MHD_OK;
 }
@@ -694,8 +692,7 @@ static int step_impl(mhd_ctx* c, double dt, double ch, const HostOut* ho) {
       }
       ProfScope ps(c, 3);
       CK(c, mhd::launch_speed_exact(c->grid, static_cast<const double*>(q.out),
-                                    &c->scal->est_bits, &c->scal->lam_bits, c->scal->floor_cnt,
-                                    c->stream));
+                                    &c->scal->est_bits, &c->scal->lam_bits, c->stream));
       continue;
     }
     if (c->esize == 8) {
@@ -710,8 +707,7 @@ static int step_impl(mhd_ctx* c, double dt, double ch, const HostOut* ho) {
       if (i == nst - 1) {  // the exact maximum speed of the new state (pass 2)
         ProfScope ps(c, 3);
         CK(c, mhd::launch_speed_exact(c->grid, static_cast<const double*>(q.out),
-                                      &c->scal->est_bits, &c->scal->lam_bits,
-                                      c->scal->floor_cnt, c->stream));
+                                      &c->scal->est_bits, &c->scal->lam_bits, c->stream));
       }
     } else {
       ProfScope ps(c, q.cls);
@@ -823,7 +819,7 @@ int mhd_step_host(mhd_ctx* c, const double* U_in, double* U_out, double dt, doub
   if (need_lam) {  // pass 2 once the whole state is on the device
     ProfScope ps(c, 3);
     CK(c, mhd::launch_speed_exact(c->grid, A, &c->scal->est_bits, &c->scal->lam_bits,
-                                  c->scal->floor_cnt, c->stream));
+                                  c->stream));
   }
   c->lam_valid = need_lam;
   HostOut ho{U_out, nz / 2};
@@ -850,7 +846,13 @@ int mhd_step_info(mhd_ctx* c, double out[4]) {
   return MHD_OK;
 }
 
-int mhd_counters(mhd_ctx* c, long long counters[3]) {
+int mhd_step_record(mhd_ctx* c, double* d_out) {
+  if (!c || !d_out) return MHD_ERR_INVALID;
+  CK(c, mhd::launch_step_record(&c->scal->sc, d_out, c->stream));
+  return MHD_OK;
+}
+
+int mhd_counters(mhd_ctx* c, long long counters[4]) {
   if (!c || !counters) return MHD_ERR_INVALID;
   Scalars h;
   CK(c, cudaMemcpyAsync(&h, c->scal, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
@@ -858,6 +860,7 @@ int mhd_counters(mhd_ctx* c, long long counters[3]) {
   counters[0] = (long long)h.floor_cnt[0];
   counters[1] = (long long)h.floor_cnt[1];
   counters[2] = (long long)h.status;
+  counters[3] = (long long)h.floor_cnt[2];
   return MHD_OK;
 }
 

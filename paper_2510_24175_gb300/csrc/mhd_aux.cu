@@ -61,6 +61,20 @@ cudaError_t launch_prep(const PrepArgs& a, StepScalars* sc, unsigned long long* 
   return cudaGetLastError();
 }
 
+// (t, dt, c_h, steps) of the last step into a caller's device array.
+__global__ void step_record_kernel(const StepScalars* sc, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  out[0] = sc->t;
+  out[1] = sc->dt;
+  out[2] = sc->ch;
+  out[3] = sc->steps;
+}
+
+cudaError_t launch_step_record(const StepScalars* sc, double* out, cudaStream_t stream) {
+  step_record_kernel<<<1, 32, 0, stream>>>(sc, out);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------- max wave speed --
 // Block maximum of a non-negative (or NaN) double per thread; thread 0 gets it.
 __device__ __forceinline__ double block_speed_max(double lam) {
@@ -79,9 +93,8 @@ __device__ __forceinline__ double block_speed_max(double lam) {
 __global__ void __launch_bounds__(256) max_speed_f32_kernel(const float* __restrict__ U,
                                                             long long ncell, int ndim,
                                                             Phys<float> ph,
-                                                            unsigned long long* lam_bits,
-                                                            unsigned long long* floor_cnt) {
-  unsigned flags = 0;
+                                                            unsigned long long* lam_bits) {
+  unsigned flags = 0;  // not counted: floors are counted per stage input
   SpeedMax<float> smax(ph);
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x) {
@@ -92,8 +105,6 @@ __global__ void __launch_bounds__(256) max_speed_f32_kernel(const float* __restr
   }
   const double m = block_speed_max(smax.value());
   if (threadIdx.x == 0) SpeedMax<float>::publish(m, lam_bits, nullptr);
-  if (flags & kFloorRho) atomicAdd(&floor_cnt[0], 1ull);
-  if (flags & kFloorP) atomicAdd(&floor_cnt[1], 1ull);
 }
 
 // FP64 pass 1 over cells [c0, c1): the maximum reliable FP32 estimate.
@@ -123,9 +134,8 @@ __global__ void __launch_bounds__(256) speed_exact_kernel(const double* __restri
                                                           long long ncell, int ndim,
                                                           Phys<double> ph,
                                                           const unsigned int* est_bits,
-                                                          unsigned long long* lam_bits,
-                                                          unsigned long long* floor_cnt) {
-  unsigned flags = 0;
+                                                          unsigned long long* lam_bits) {
+  unsigned flags = 0;  // not counted: floors are counted per stage input
   const SpeedEstimator estimate(ph);
   const float thr = 0.999f * __uint_as_float(*est_bits);
   double lam = 0.0;
@@ -146,8 +156,6 @@ __global__ void __launch_bounds__(256) speed_exact_kernel(const double* __restri
   }
   const double m = block_speed_max(lam);
   if (threadIdx.x == 0) SpeedMax<float>::publish(m, lam_bits, nullptr);
-  if (flags & kFloorRho) atomicAdd(&floor_cnt[0], 1ull);
-  if (flags & kFloorP) atomicAdd(&floor_cnt[1], 1ull);
 }
 
 static unsigned speed_blocks(const Grid& g, long long n) {
@@ -166,35 +174,33 @@ cudaError_t launch_speed_estimate(const Grid& g, const double* U, long long c0, 
 }
 
 cudaError_t launch_speed_exact(const Grid& g, const double* U, const unsigned int* est_bits,
-                               unsigned long long* lam_bits, unsigned long long* floor_cnt,
-                               cudaStream_t stream) {
+                               unsigned long long* lam_bits, cudaStream_t stream) {
   speed_exact_kernel<<<speed_blocks(g, g.ncell), 256, 0, stream>>>(
-      U, g.ncell, g.ndim, make_phys<double>(g), est_bits, lam_bits, floor_cnt);
+      U, g.ncell, g.ndim, make_phys<double>(g), est_bits, lam_bits);
   return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t launch_max_speed(const Grid& g, const T* U, unsigned long long* lam_bits,
-                             unsigned int* est_bits, unsigned long long* floor_cnt,
-                             cudaStream_t stream) {
+                             unsigned int* est_bits, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(lam_bits, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
   if constexpr (sizeof(T) == 8) {
     if (!est_bits) return cudaErrorInvalidValue;
     e = cudaMemsetAsync(est_bits, 0, sizeof(unsigned int), stream);
     if (e == cudaSuccess) e = launch_speed_estimate(g, U, 0, g.ncell, est_bits, stream);
-    if (e == cudaSuccess) e = launch_speed_exact(g, U, est_bits, lam_bits, floor_cnt, stream);
+    if (e == cudaSuccess) e = launch_speed_exact(g, U, est_bits, lam_bits, stream);
     return e;
   } else {
     max_speed_f32_kernel<<<speed_blocks(g, g.ncell), 256, 0, stream>>>(
-        U, g.ncell, g.ndim, make_phys<float>(g), lam_bits, floor_cnt);
+        U, g.ncell, g.ndim, make_phys<float>(g), lam_bits);
     return cudaGetLastError();
   }
 }
 template cudaError_t launch_max_speed<double>(const Grid&, const double*, unsigned long long*,
-                                              unsigned int*, unsigned long long*, cudaStream_t);
+                                              unsigned int*, cudaStream_t);
 template cudaError_t launch_max_speed<float>(const Grid&, const float*, unsigned long long*,
-                                             unsigned int*, unsigned long long*, cudaStream_t);
+                                             unsigned int*, cudaStream_t);
 
 // ------------------------------------------------------ conservation sums --
 // Pass 1: CTA b sums the contiguous cell range [b*chunk, (b+1)*chunk) of the

@@ -129,14 +129,13 @@ __global__ void __launch_bounds__(kCtThreads) ct_face_kernel(
 }
 
 // Cell-centred B of U = mean of the cell's two faces; LAST: also the max
-// wave speed of the new state (NaN-sticky; one FP64-bit atomicMax per CTA)
-// and the floor counters.
+// wave speed of the new state (NaN-sticky; one FP64-bit atomicMax per CTA).
+// Floors are counted by the stage kernels (per stage input), not here.
 template <class T, bool LAST>
 __global__ void __launch_bounds__(kCtThreads) ct_cell_kernel(const T* __restrict__ b, T* U,
                                                                int nx, int ny, int nz,
                                                                long long nc, Phys<T> ph,
-                                                               unsigned long long* lam_bits,
-                                                               unsigned long long* floor_cnt) {
+                                                               unsigned long long* lam_bits) {
   __shared__ double wmax[kCtThreads / 32];
   T lam = T(0);
   unsigned flags = 0;
@@ -173,8 +172,6 @@ __global__ void __launch_bounds__(kCtThreads) ct_cell_kernel(const T* __restrict
       if (m != m) bits = 0x7ff8000000000000ull;
       atomicMax(lam_bits, bits);
     }
-    if (flags & kFloorRho) atomicAdd(&floor_cnt[0], 1ull);
-    if (flags & kFloorP) atomicAdd(&floor_cnt[1], 1ull);
   }
 }
 
@@ -264,15 +261,14 @@ cudaError_t launch_ct_faces(const Grid& g, bool first, const T* edge, const T* b
 
 template <class T>
 cudaError_t launch_ct_cells(const Grid& g, bool last, const T* b, T* U,
-                            unsigned long long* lam_bits, unsigned long long* floor_cnt,
-                            cudaStream_t s) {
+                            unsigned long long* lam_bits, cudaStream_t s) {
   const Phys<T> ph = make_phys<T>(g);
   if (last)
     ct_cell_kernel<T, true><<<ct_blocks(g), kCtThreads, 0, s>>>(
-        b, U, g.n[0], g.n[1], g.n[2], g.ncell, ph, lam_bits, floor_cnt);
+        b, U, g.n[0], g.n[1], g.n[2], g.ncell, ph, lam_bits);
   else
     ct_cell_kernel<T, false><<<ct_blocks(g), kCtThreads, 0, s>>>(
-        b, U, g.n[0], g.n[1], g.n[2], g.ncell, ph, lam_bits, floor_cnt);
+        b, U, g.n[0], g.n[1], g.n[2], g.ncell, ph, lam_bits);
   return cudaGetLastError();
 }
 
@@ -298,8 +294,7 @@ cudaError_t launch_ct_divb(const Grid& g, const T* b, unsigned long long* out_bi
                                           T*, const StepScalars*, double, double,            \
                                           cudaStream_t);                                     \
   template cudaError_t launch_ct_cells<T>(const Grid&, bool, const T*, T*,                   \
-                                          unsigned long long*, unsigned long long*,          \
-                                          cudaStream_t);                                     \
+                                          unsigned long long*, cudaStream_t);                \
   template cudaError_t launch_ct_set_cells<T>(const Grid&, const T*, T*, cudaStream_t);      \
   template cudaError_t launch_ct_divb<T>(const Grid&, const T*, unsigned long long*,         \
                                          cudaStream_t);

@@ -16,7 +16,7 @@ constexpr int kSumBlocks = 1024;
 struct Scalars {  // device block at the start of the scalar region
   StepScalars sc;
   unsigned long long lam_bits;
-  unsigned long long floor_cnt[2];
+  unsigned long long floor_cnt[3];  // rho floor, p floor, FP32 p recomputed in FP64
   unsigned int status;
   unsigned int est_bits;  // FP64: max reliable FP32 speed estimate (FP32 bits)
   double sums[8];

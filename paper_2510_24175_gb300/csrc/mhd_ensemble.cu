@@ -40,7 +40,7 @@ struct EnsBox {
   float* Ub;
   StepScalars sc;
   unsigned long long lam_bits[2];
-  unsigned long long floor_cnt[2];
+  unsigned long long floor_cnt[3];
   unsigned int status;
   int cur;               // lam_bits slot holding the current state's wave speed
   double cfl, inv_dx_sum, t_end, glm_alpha, dh_min;
@@ -366,7 +366,7 @@ int mhd_ensemble_set_state(mhd_ensemble* e, int box, const double* U, int where,
   EnsBox r = e->h[box];
   memset(&r.sc, 0, sizeof(r.sc));
   r.lam_bits[0] = r.lam_bits[1] = 0ull;
-  r.floor_cnt[0] = r.floor_cnt[1] = 0ull;
+  r.floor_cnt[0] = r.floor_cnt[1] = r.floor_cnt[2] = 0ull;
   r.status = 0;
   r.cur = 0;
   e->h[box] = r;
@@ -391,8 +391,7 @@ int mhd_ensemble_step(mhd_ensemble* e, int nsteps) {
     if (!e->ctx[b]->have_state) return efail(e, MHD_ERR_STATE, "box %d has no state", b);
     if (!e->lam_ok[b]) {
       ECK(e, mhd::launch_max_speed<float>(e->ctx[b]->grid, static_cast<const float*>(e->ctx[b]->Ua),
-                                          &e->d[b].lam_bits[e->cur[b]], nullptr,
-                                          &e->d[b].floor_cnt[0], e->stream));
+                                          &e->d[b].lam_bits[e->cur[b]], nullptr, e->stream));
       e->lam_ok[b] = true;
     }
   }

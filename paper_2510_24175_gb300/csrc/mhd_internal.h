@@ -60,8 +60,7 @@ cudaError_t launch_ct_faces(const Grid& g, bool first, const T* edge, const T* b
 // U's cell-centred B := face means; last: also the max wave speed into lam_bits.
 template <class T>
 cudaError_t launch_ct_cells(const Grid& g, bool last, const T* b, T* U,
-                            unsigned long long* lam_bits, unsigned long long* floor_cnt,
-                            cudaStream_t s);
+                            unsigned long long* lam_bits, cudaStream_t s);
 // U's cell-centred B := face means with the pressure kept (after a new face field).
 template <class T>
 cudaError_t launch_ct_set_cells(const Grid& g, const T* b, T* U, cudaStream_t s);
@@ -87,6 +86,8 @@ struct PrepArgs {
 };
 cudaError_t launch_prep(const PrepArgs& a, StepScalars* sc, unsigned long long* lam_bits,
                         unsigned int* est_bits, unsigned int* status, cudaStream_t stream);
+// out[0..3] = (t, dt, c_h, steps) of the last step (device array).
+cudaError_t launch_step_record(const StepScalars* sc, double* out, cudaStream_t stream);
 
 // Maximum wave speed of a state into lam_bits (FP64 bits; both words cleared
 // first).  FP32: every cell evaluated.  FP64: the two passes of
@@ -94,8 +95,7 @@ cudaError_t launch_prep(const PrepArgs& a, StepScalars* sc, unsigned long long* 
 // cells that can hold the maximum).
 template <class T>
 cudaError_t launch_max_speed(const Grid& g, const T* U, unsigned long long* lam_bits,
-                             unsigned int* est_bits, unsigned long long* floor_cnt,
-                             cudaStream_t stream);
+                             unsigned int* est_bits, cudaStream_t stream);
 // FP64 pass 1 over cells [c0, c1): the maximum reliable estimate, accumulated
 // into est_bits (not cleared first).
 cudaError_t launch_speed_estimate(const Grid& g, const double* U, long long c0, long long c1,
@@ -103,8 +103,7 @@ cudaError_t launch_speed_estimate(const Grid& g, const double* U, long long c0, 
 // FP64 pass 2 over all cells: the exact maximum of the cells whose estimate
 // reaches 0.999 of *est_bits or is not reliable, accumulated into lam_bits.
 cudaError_t launch_speed_exact(const Grid& g, const double* U, const unsigned int* est_bits,
-                               unsigned long long* lam_bits, unsigned long long* floor_cnt,
-                               cudaStream_t stream);
+                               unsigned long long* lam_bits, cudaStream_t stream);
 
 template <class T>
 cudaError_t launch_sums(const Grid& g, const T* U, double* partials, int nblocks,

@@ -28,7 +28,10 @@ enum { kRHO = 0, kVX = 1, kVY = 2, kVZ = 3, kBX = 4, kBY = 5, kBZ = 6, kPRS = 7,
        kNV = 9 };
 enum { kLimFlat = 0, kLimMinmod = 1, kLimMC = 2, kLimWenoz = 3 };
 enum { kBcPeriodic = 0, kBcOutflow = 1 };
-enum { kFloorRho = 1u, kFloorP = 2u };
+// cons->prim flags: density floor, pressure floor, and (FP32 only) the
+// pressure recomputed in FP64 because the FP32 value fell in the
+// cancellation-dominated range
+enum { kFloorRho = 1u, kFloorP = 2u, kPressF64 = 4u };
 
 template <class T>
 struct Phys {
@@ -200,6 +203,7 @@ MHD_HD double pressure_floor(double p, const double u[kNV], double rho,
 MHD_HD float pressure_floor(float p, const float u[kNV], float rho,
                                                 const Phys<float>& ph, unsigned& flags) {
   if (p < ph.p_floor || p < 1e-3f * ph.gm1 * u[kPRS]) {
+    flags |= kPressF64;
     double r = rho;
     double m2 = (double)u[kVX] * u[kVX] + (double)u[kVY] * u[kVY] + (double)u[kVZ] * u[kVZ];
     double b2 = (double)u[kBX] * u[kBX] + (double)u[kBY] * u[kBY] + (double)u[kBZ] * u[kBZ];

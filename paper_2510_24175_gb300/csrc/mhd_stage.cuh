@@ -55,7 +55,7 @@ struct StageParams {
   const StepScalars* sc;
   unsigned long long* lam_bits;   // stage 2: max wave speed as FP64 bits (FP32 path)
   unsigned int* est_bits;         // stage 2, FP64: max reliable FP32 speed estimate
-  unsigned long long* floor_cnt;  // [2] floor activations
+  unsigned long long* floor_cnt;  // [3] floor activations (see count_floors)
   // constrained transport (kernels instantiated with CT = true)
   const T* bw[3];  // the stage input's face field: b_d on each cell's lower d-face
   T* ctf;          // kCtPlanes planes of ncell values (layout below)
@@ -232,13 +232,24 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
   const bool frozen = !(sc.dt != 0.0);
   const int lim = p.limiter;
   const Phys<T> ph = p.ph;
-  unsigned flags = 0;
+  unsigned flags = 0;  // of the wave-speed conversions (not counted)
 
   auto slot = [](int zz) { return ZACT ? ((zz % 3) + 3) % 3 : 0; };
   auto ring_plane = [&](int zz) { return ring + slot(zz) * (kNV * G::NINT); };
 
-  // cons -> prim of cell (r, c) of plane zz into dst (variables dst_stride apart)
-  auto load_cell = [&](int zz, int r, int c, T* dst, int dst_stride) {
+  // Floor activations are counted once per stage for each cell the tile
+  // updates, from that cell's own conversion of the stage input; halo copies
+  // converted by neighbouring tiles are not counted, so the counts do not
+  // depend on the decomposition.  Rare: one atomic per flagged cell.
+  auto count_floors = [&](unsigned fl, int zz, int r, int c) {
+    if (zz < z0 || zz >= z1 || x0 + c >= nx || (G::GY && y0 + r >= ny)) return;
+    if (fl & kFloorRho) atomicAdd(&p.floor_cnt[0], 1ull);
+    if (fl & kFloorP) atomicAdd(&p.floor_cnt[1], 1ull);
+    if (fl & kPressF64) atomicAdd(&p.floor_cnt[2], 1ull);
+  };
+  // cons -> prim of cell (r, c) of plane zz into dst (variables dst_stride
+  // apart); own: an interior item of the tile (counted if the tile updates it)
+  auto load_cell = [&](int zz, int r, int c, T* dst, int dst_stride, bool own) {
     const int gz = ZACT ? remap(zz, nz, p.bc_lo[2], p.bc_hi[2]) : 0;
     const int gx = remap(x0 + c, nx, p.bc_lo[0], p.bc_hi[0]);
     const int gy = G::GY ? remap(y0 + r, ny, p.bc_lo[1], p.bc_hi[1]) : 0;
@@ -246,7 +257,9 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
     T u[kNV], v[kNV];
 #pragma unroll
     for (int k = 0; k < kNV; ++k) u[k] = p.win[k * p.sv + off];
-    cons_to_prim(u, v, ph, flags);
+    unsigned fl = 0;
+    cons_to_prim(u, v, ph, fl);
+    if (fl && own) count_floors(fl, zz, r, c);
 #pragma unroll
     for (int k = 0; k < kNV; ++k) dst[k * dst_stride] = v[k];
   };
@@ -254,17 +267,17 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
   auto load_item = [&](int it, int zi, int zh) {
     if (it < G::NINT) {
       const int r = it / TX, c = it - (it / TX) * TX;
-      load_cell(zi, r, c, ring_plane(zi) + it, G::NINT);
+      load_cell(zi, r, c, ring_plane(zi) + it, G::NINT, true);
     } else if (it < G::NINT + G::NXH) {
       const int j = it - G::NINT;
       const int r = j >> 2, q = j & 3;
       const int c = q < 2 ? q - 2 : TX + q - 2;
-      load_cell(zh, r, c, xh + j, G::NXH);
+      load_cell(zh, r, c, xh + j, G::NXH, false);
     } else {
       const int j = it - G::NINT - G::NXH;
       const int hr = j / TX, c = j - (j / TX) * TX;
       const int r = hr < 2 ? hr - 2 : TY + hr - 2;
-      load_cell(zh, r, c, yh + j, G::NYH);
+      load_cell(zh, r, c, yh + j, G::NYH, false);
     }
   };
   // primitives of cell (r, c) of the current plane (interior in ring slot,
@@ -522,10 +535,6 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
         m = nan_max(m, wmax[w]);
       SpeedMax<T>::publish(m, p.lam_bits, p.est_bits);
     }
-  }
-  if (flags) {
-    if (flags & kFloorRho) atomicAdd(&p.floor_cnt[0], 1ull);
-    if (flags & kFloorP) atomicAdd(&p.floor_cnt[1], 1ull);
   }
   __syncthreads();  // the CTA may start another tile on the same shared memory
 }

@@ -169,12 +169,20 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
   const T damp = T(sc.damp);
   const bool frozen = !(sc.dt != 0.0);
   const Phys<T> ph = p.ph;
-  unsigned flags = 0;
+  unsigned flags = 0;  // of the wave-speed conversions (not counted)
 
   auto slot = [](int zz) { return ZACT ? ((zz % 5) + 5) % 5 : 0; };
   auto ring_plane = [&](int zz) { return ring + slot(zz) * (kNV * G::NINT); };
 
-  auto load_cell = [&](int zz, int r, int c, T* dst, int dst_stride) {
+  // floor activations: once per stage for each cell the tile updates, from
+  // its own conversion (as in the PLM stage kernel)
+  auto count_floors = [&](unsigned fl, int zz, int r, int c) {
+    if (zz < z0 || zz >= z1 || x0 + c >= nx || (G::GY && y0 + r >= ny)) return;
+    if (fl & kFloorRho) atomicAdd(&p.floor_cnt[0], 1ull);
+    if (fl & kFloorP) atomicAdd(&p.floor_cnt[1], 1ull);
+    if (fl & kPressF64) atomicAdd(&p.floor_cnt[2], 1ull);
+  };
+  auto load_cell = [&](int zz, int r, int c, T* dst, int dst_stride, bool own) {
     const int gz = ZACT ? remap3(zz, nz, p.bc_lo[2], p.bc_hi[2]) : 0;
     const int gx = remap3(x0 + c, nx, p.bc_lo[0], p.bc_hi[0]);
     const int gy = G::GY ? remap3(y0 + r, ny, p.bc_lo[1], p.bc_hi[1]) : 0;
@@ -182,24 +190,26 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
     T u[kNV], v[kNV];
 #pragma unroll
     for (int k = 0; k < kNV; ++k) u[k] = p.win[k * p.sv + off];
-    cons_to_prim(u, v, ph, flags);
+    unsigned fl = 0;
+    cons_to_prim(u, v, ph, fl);
+    if (fl && own) count_floors(fl, zz, r, c);
 #pragma unroll
     for (int k = 0; k < kNV; ++k) dst[k * dst_stride] = v[k];
   };
   auto load_item = [&](int it, int zi, int zh) {
     if (it < G::NINT) {
       const int r = it / TX, c = it - (it / TX) * TX;
-      load_cell(zi, r, c, ring_plane(zi) + it, G::NINT);
+      load_cell(zi, r, c, ring_plane(zi) + it, G::NINT, true);
     } else if (it < G::NINT + G::NXH) {
       const int j = it - G::NINT;
       const int r = j / 6, q = j - (j / 6) * 6;
       const int c = q < 3 ? q - 3 : TX + q - 3;
-      load_cell(zh, r, c, xh + j, G::NXH);
+      load_cell(zh, r, c, xh + j, G::NXH, false);
     } else {
       const int j = it - G::NINT - G::NXH;
       const int hr = j / TX, c = j - (j / TX) * TX;
       const int r = hr < 3 ? hr - 3 : TY + hr - 3;
-      load_cell(zh, r, c, yh + j, G::NYH);
+      load_cell(zh, r, c, yh + j, G::NYH, false);
     }
   };
   auto cell_ptr = [&](const T* cur, int r, int c, int* st) -> const T* {
@@ -442,10 +452,6 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
       for (int w = 1; w < NW; ++w) m = nan_max(m, wmax[w]);
       SpeedMax<T>::publish(m, p.lam_bits, p.est_bits);
     }
-  }
-  if (flags) {
-    if (flags & kFloorRho) atomicAdd(&p.floor_cnt[0], 1ull);
-    if (flags & kFloorP) atomicAdd(&p.floor_cnt[1], 1ull);
   }
 }
 

@@ -226,6 +226,61 @@ def _random_smooth(pb: Problem) -> np.ndarray:
     return V
 
 
+def _floor_defects(pb: Problem) -> np.ndarray:
+    """The smooth random state with seeded defect cells that drive the floor
+    branches of cons->prim: ``n_rho`` near-vacuum cells (rho = rho_defect,
+    v = 0), ``n_p`` cells with a negative pressure (p = p_defect < 0: their
+    total energy is below the kinetic plus magnetic energy), and ``n_cold``
+    cold, strongly magnetised, fast cells (p = p_cold, |B| ~ b_cold,
+    |v| ~ 1), whose internal energy is a tiny fraction of the total.  Defect
+    cells are distinct and at least two cells apart along every axis.
+    ``p_base`` scales the background pressure (a cold flow when small)."""
+    V = _random_smooth(pb)
+    q = pb.params
+    V[PRS] *= q.get("p_base", 1.0)
+    rng = np.random.default_rng(pb.seed + 1000)
+    nx, ny, nz = pb.n
+    counts = (q.get("n_rho", 0), q.get("n_p", 0), q.get("n_cold", 0))
+    picked = []
+    while len(picked) < sum(counts):
+        c = (int(rng.integers(nz)), int(rng.integers(ny)), int(rng.integers(nx)))
+        if all(max(abs(c[0] - o[0]), abs(c[1] - o[1]), abs(c[2] - o[2])) > 2 for o in picked):
+            picked.append(c)
+    kinds = [0] * counts[0] + [1] * counts[1] + [2] * counts[2]
+    for (k, j, i), kind in zip(picked, kinds):
+        if kind == 0:
+            V[RHO, k, j, i] = q.get("rho_defect", 1e-5)
+            V[VX:VZ + 1, k, j, i] = 0.0
+        elif kind == 1:
+            V[PRS, k, j, i] = q.get("p_defect", -0.5)
+        else:
+            V[PRS, k, j, i] = q.get("p_cold", 1e-5)
+            b = rng.normal(size=3)
+            V[BX:BZ + 1, k, j, i] = q.get("b_cold", 2.0) * b / np.linalg.norm(b)
+            v = rng.normal(size=3)
+            V[VX:VZ + 1, k, j, i] = v / np.linalg.norm(v)
+    return V
+
+
+def _cold_flow(pb: Problem) -> np.ndarray:
+    """A cold, strongly magnetised, highly supersonic uniform flow with small
+    seeded smooth perturbations: rho = 1, v = (1, 0.5, 0.2), B = (0.5, 0.3,
+    0.1), each with a relative perturbation of rms ``amp`` (default 1e-5), and
+    p = p0 (default 1e-4) times (1 + 0.1 tanh f): the internal energy is
+    about 2e-4 of the total in every cell."""
+    rng = np.random.default_rng(pb.seed)
+    q = pb.params
+    amp = q.get("amp", 1e-5)
+    f, _ = _gaussian_field(pb.n, rng, 1, 4, -2.0, 8)
+    f /= np.maximum(np.sqrt(np.mean(f * f, axis=(1, 2, 3), keepdims=True)), 1e-300)
+    V = _empty(pb)
+    base = (1.0, 1.0, 0.5, 0.2, 0.5, 0.3, 0.1)
+    for k in range(7):
+        V[k] = base[k] * (1.0 + amp * f[k])
+    V[PRS] = q.get("p0", 1e-4) * (1.0 + 0.1 * np.tanh(f[7]))
+    return V
+
+
 # ------------------------------------------- staggered (face) magnetic fields --
 def _cell_mean(b: np.ndarray) -> np.ndarray:
     """Cell-centred field = mean of each cell's two faces (periodic)."""
@@ -453,6 +508,8 @@ _GENERATORS = {
     "linear_wave": _linear_wave,
     "uniform": _uniform,
     "random_smooth": _random_smooth,
+    "floor_defects": _floor_defects,
+    "cold_flow": _cold_flow,
     "ct_random": _ct_random,
     "shock_pair": _shock_pair,
     "field_loop": _field_loop,

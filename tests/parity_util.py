@@ -93,3 +93,58 @@ def sampled_one_step(U0: np.ndarray, pb: Problem, dt: float, ch: float, cells, r
             r = orc.ct_run(box, fbox, g, 1, dts=[dt], chs=[ch])
         out[:, m] = r.U[:, radius, radius, radius]
     return out
+
+
+def floor_decisions(W: np.ndarray, pb: Problem):
+    """The decisions the conversion of a stage input W takes at each interior
+    cell, from the plain formulas in FP64: (rho floored, p floored, FP32
+    pressure recomputed in FP64), and the smallest relative distance of any
+    of them from its threshold.  Density first; the pressure uses the
+    floored density.  The FP32 path recomputes p in FP64 when p < p_floor or
+    p < 1e-3 (gamma - 1) E, and floors it when the FP64 value is below
+    p_floor.  A decision farther than about 1e-3 from its threshold is taken
+    alike by the FP64 oracle and by either GPU precision."""
+    rho = W[RHO]
+    rho_f = rho < pb.rho_floor
+    r = np.where(rho_f, pb.rho_floor, rho)
+    kin = 0.5 * (W[VX] ** 2 + W[VY] ** 2 + W[VZ] ** 2) / r
+    mag = 0.5 * (W[BX] ** 2 + W[BY] ** 2 + W[BZ] ** 2)
+    p = (pb.gamma - 1.0) * (W[PRS] - kin - mag)
+    p_f = p < pb.p_floor
+    cold = p < 1e-3 * (pb.gamma - 1.0) * W[PRS]
+    branch = p_f | cold
+
+    def margin(a, t):
+        t = np.broadcast_to(np.asarray(t, dtype=np.float64), a.shape)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            m = np.where(t > 0, np.abs(a / t - 1.0), np.inf)
+        return np.where(np.isfinite(m), m, np.inf)
+
+    m = min(float(margin(rho, pb.rho_floor).min()), float(margin(p, pb.p_floor).min()),
+            float(margin(p, 1e-3 * (pb.gamma - 1.0) * W[PRS]).min()))
+    return (int(rho_f.sum()), int(p_f.sum()), int(branch.sum())), m
+
+
+def oracle_floor_run(pb: Problem, nsteps: int):
+    """Oracle run of nsteps CFL steps with the decision counts of every
+    stage input (floor_decisions of U^n and of the first stage U1, and of
+    U2 with SSP-RK3): returns (RunResult, counts (rho, p, branch), margin)."""
+    g = grid_of(pb)
+    U0 = orc.prim_to_cons(pb.prim(), pb.gamma)
+    U = U0
+    tot = np.zeros(3, dtype=np.int64)
+    margin = np.inf
+    for _ in range(nsteps):
+        dt, ch = orc.cfl_dt(U, g)
+        inputs = [U]
+        U1, _ = orc.stage(U, g, dt, ch, 1)
+        inputs.append(U1)
+        if g.rk_order == 3:
+            U2, _ = orc.stage(U1, g, dt, ch, 2, Un=U)
+            inputs.append(U2)
+        for W in inputs:
+            c, m = floor_decisions(W, pb)
+            tot += c
+            margin = min(margin, m)
+        U = orc.run(U, g, 1).U
+    return orc.run(U0, g, nsteps), tuple(int(x) for x in tot), margin

@@ -93,11 +93,28 @@ def test_step_adjoint_full_jacobian(pb):
         assert err.max() < 1e-11, err.max()
 
 
+def kinetic_energy(U, cell_volume: float):
+    """The test's objective J = sum over cells of |m|^2 / (2 rho) times the
+    cell volume (user-side code: differentiated by torch, not the library)."""
+    return 0.5 * ((U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0]).sum() * cell_volume
+
+
+def prim_to_cons_torch(V, gamma: float):
+    """The test's parameterisation of the initial state: primitive ->
+    conservative in torch, so that the gradient reaches the velocity
+    perturbation (user-side code, not the library's conversion)."""
+    import torch
+    rho = V[0]
+    v2 = V[1] ** 2 + V[2] ** 2 + V[3] ** 2
+    b2 = V[4] ** 2 + V[5] ** 2 + V[6] ** 2
+    E = V[7] / (gamma - 1.0) + 0.5 * rho * v2 + 0.5 * b2
+    return torch.stack([rho, rho * V[1], rho * V[2], rho * V[3], V[4], V[5], V[6], E, V[8]])
+
 def _rollout_grad(pb, dv, nsteps, k):
     """Gradient of J = kinetic energy at t_N w.r.t. the velocity perturbation
     dv (2, nz, ny, nx) through MHDRollout; returns (J, grad, dts, chs, U0)."""
     import torch
-    from paper_2510_24175_gb300.adjoint import MHDRollout, kinetic_energy, prim_to_cons_torch
+    from paper_2510_24175_gb300.adjoint import MHDRollout
     s = _solver(pb)
     V0 = torch.from_numpy(pb.prim()).cuda()
     p = torch.from_numpy(dv).cuda().requires_grad_(True)

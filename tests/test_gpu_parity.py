@@ -109,7 +109,7 @@ def test_brio_wu_short_times(t_end):
     assert len(hist) == int(np.count_nonzero(ref.dts))
     err = rel_l1(U, ref.U)
     assert np.all(err <= TOL64), err
-    assert cnt == {"rho_floor": 0, "p_floor": 0, "status": 0}
+    assert cnt == {"rho_floor": 0, "p_floor": 0, "status": 0, "p_f64": 0}
 
 
 def test_brio_wu_to_t_end_within_conditioning():
@@ -136,7 +136,7 @@ def test_brio_wu_to_t_end_within_conditioning():
         assert abs(s1[q] - s0[q]) < 1e-12, q
     assert s1[1] - s0[1] == pytest.approx(0.9 * 0.1, rel=1e-10)
     assert s1[2] - s0[2] == pytest.approx(-1.5 * 0.1, rel=1e-10)
-    assert cnt == {"rho_floor": 0, "p_floor": 0, "status": 0}
+    assert cnt == {"rho_floor": 0, "p_floor": 0, "status": 0, "p_f64": 0}
 
 
 def test_tiny_grids():
@@ -225,7 +225,7 @@ def test_orszag_tang_256_twenty_steps_properties():
     scale = U.abs().amax(dim=(1, 2, 3), keepdim=True)
     scale = torch.maximum(scale, 1e-3 * scale[RHO])  # B_z and psi are near zero
     assert float(((U - sym * inv).abs() / scale).max()) < 1e-11
-    assert s.counters() == {"rho_floor": 0, "p_floor": 0, "status": 0}
+    assert s.counters() == {"rho_floor": 0, "p_floor": 0, "status": 0, "p_f64": 0}
 
 
 def test_fp32_turbulent_box_50_steps_error_vs_oracle():
@@ -242,7 +242,7 @@ def test_fp32_turbulent_box_50_steps_error_vs_oracle():
     err = rel_l1(U, ref.U, floor=0.1)
     print("fp32 turbulent 64^3 x 50 steps rel L1:", err)
     assert np.all(err <= 2e-6), err
-    assert cnt == {"rho_floor": 0, "p_floor": 0, "status": 0}
+    assert cnt == {"rho_floor": 0, "p_floor": 0, "status": 0, "p_f64": 0}
 
 
 # ------------------------------------------------------------------ SSP-RK3 --

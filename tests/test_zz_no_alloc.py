@@ -52,3 +52,33 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
     rc = m.lib().mhd_conserved_sums_noalloc(ctypes.byref(cfg), ctypes.c_void_p(dummy.data_ptr()),
                                             out, None)
     assert rc == m.MHD_ERR_NOMEM
+
+
+def test_noalloc_refuses_a_capturing_stream_and_leaves_the_capture_intact():
+    """The call ends with a host copy and a stream synchronisation, which a
+    capturing stream does not accept: it must refuse such a stream before it
+    enqueues anything, so the caller's capture can still be completed."""
+    import torch
+    import paper_2510_24175_gb300 as m
+    pb = Problem("random_smooth", (40, 20, 12), seed=5)
+    U = torch.from_numpy(orc.prim_to_cons(pb.prim(), pb.gamma)).cuda()
+    c = m.Config.from_problem(pb).c()
+    y = torch.zeros(8, dtype=torch.float64, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            out = (ctypes.c_double * 8)()
+            rc = m.lib().mhd_conserved_sums_noalloc(
+                ctypes.byref(c), ctypes.c_void_p(U.data_ptr()), out,
+                ctypes.c_void_p(s.cuda_stream))
+            y.add_(1.0)
+    assert rc == m.MHD_ERR_INVALID
+    assert b"capturing" in m.lib().mhd_last_error(None)
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(y.sum()) == 8.0
+    # and the entry point still works afterwards on an ordinary stream
+    got = m.mhd_conserved_sums_noalloc(m.Config.from_problem(pb).c(), U)
+    assert np.isfinite(got).all()
