@@ -125,7 +125,7 @@ def _rollout_grad(pb, dv, nsteps, k):
     vol = pb.dx[0] * pb.dx[1]
     J = kinetic_energy(UN, vol)
     J.backward()
-    return float(J), p.grad.cpu().numpy(), U0.detach().cpu().numpy(), s
+    return float(J.detach()), p.grad.cpu().numpy(), U0.detach().cpu().numpy(), s
 
 
 def _J_frozen(pb, dv, dts, chs):

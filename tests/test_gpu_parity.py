@@ -203,22 +203,39 @@ def test_orszag_tang_256_one_step_sampled():
     assert np.max(np.abs(got - ref) / scale) < 1e-13
 
 
-def test_orszag_tang_256_twenty_steps_properties():
-    """20 steps of the benchmark workload: point symmetry of the OT vortex
-    and conservation hold at full size."""
+def test_orszag_tang_256_twenty_steps_against_the_oracle():
+    """The benchmark workload in full (3-D Orszag-Tang 256^3, FP64, 20 CFL
+    steps; the paper's 3-D test, Section 4.2) against the oracle: before
+    every step the GPU's dt and c_h (from its FP32-screened FP64 wave-speed
+    reduction) equal the oracle's CFL rule applied to the GPU's own state,
+    and after 20 steps the state equals the oracle's own 20-step run
+    (slab-parallel on the host cores, bitwise the single-process oracle) to
+    1e-12 relative L1.  Point symmetry of the vortex and conservation hold as
+    well."""
     import paper_2510_24175_gb300 as m
+    from oracle.slab import SlabRunner
     torch = _torch()
     pb = inputs.orszag_tang_3d(256)
+    g = grid_of(pb)
+    U0 = orc.prim_to_cons(pb.prim(), pb.gamma)
     s = m.MHD(m.Config.from_problem(pb))
     s.set_state(torch.from_numpy(pb.prim()).cuda(), kind=m.MHD_PRIM)
     s0 = s.conserved_sums()
-    for _ in range(20):
-        s.step()
-    s.step_info()
+    with SlabRunner(g) as runner:
+        for n in range(20):
+            dt_o, ch_o = runner.cfl_dt(s.get_state().cpu().numpy())
+            s.step()
+            info = s.step_info()
+            assert abs(info["dt"] - dt_o) <= 1e-13 * dt_o, (n, info, dt_o)
+            assert abs(info["ch"] - ch_o) <= 1e-13 * ch_o, (n, info, ch_o)
+        ref = runner.run(U0, 20)
     s1 = s.conserved_sums()
     # rho, m, E, B: conserved to round-off (B_x etc. sum to ~0 by symmetry)
     assert np.all(np.abs(s1 - s0) <= 1e-12 * (np.abs(s0).max() + 1.0))
     U = s.get_state()
+    err = rel_l1(U.cpu().numpy(), ref.U)
+    assert float(err.max()) <= TOL64, err
+    assert abs(info["t"] - ref.t) <= 1e-13 * ref.t
     inv = torch.flip(U, dims=(1, 2, 3))
     sym = torch.tensor([1, -1, -1, -1, -1, -1, -1, 1, 1.0], device=U.device,
                        dtype=U.dtype).view(9, 1, 1, 1)
