@@ -37,6 +37,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -150,63 +152,47 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------- CPU oracle --
-# CPU oracle workers (spawned processes; each owns one 48^3 Orszag-Tang box)
-_CPU = {}
-
-
-def _cpu_init(n: int):
+def _cpu_problem(n: int):
     import oracle as orc
     from paper_2510_24175_gb300 import inputs
     pb = inputs.orszag_tang_3d(n)
-    _CPU["g"] = orc.Grid(n=pb.n, dx=pb.dx, gamma=pb.gamma, glm_alpha=pb.glm_alpha,
-                         limiter=pb.limiter, bc=pb.bc, cfl=pb.cfl)
-    _CPU["U"] = orc.prim_to_cons(pb.prim(), pb.gamma)
-    _CPU["orc"] = orc
+    g = orc.Grid(n=pb.n, dx=pb.dx, gamma=pb.gamma, glm_alpha=pb.glm_alpha, limiter=pb.limiter,
+                 bc=pb.bc, cfl=pb.cfl)
+    return pb, g, orc.prim_to_cons(pb.prim(), pb.gamma)
 
 
-def _cpu_timed(target_s: float):
-    """Repeats one RK2 step of the worker's box for ~target_s; (reps, seconds)."""
-    orc, g, U = _CPU["orc"], _CPU["g"], _CPU["U"]
-    reps, t = 0, 0.0
-    while t < target_s:
-        t0 = time.perf_counter()
-        orc.run(U, g, 1)
-        t += time.perf_counter() - t0
-        reps += 1
-    return reps, t
-
-
-def _cpu_step(_):
-    """One RK2 step of the worker's box (its state advances)."""
-    _CPU["U"] = _CPU["orc"].run(_CPU["U"], _CPU["g"], 1).U
-    return 0
-
-
-def _cpu_pool(nproc: int, n: int):
-    import multiprocessing as mp
-    return mp.get_context("spawn").Pool(nproc, initializer=_cpu_init, initargs=(n,))
-
-
-def cpu_oracle_sample(target_s: float = 12.0, n: int = 48):
-    """Times the CPU FP64 oracle as it stands on one RK2 step of the 3-D
-    Orszag-Tang problem at 48^3, repeated for ~target_s: once in one process
-    (one thread), and as one independent process per host core at once
-    (the oracle is single-threaded; the all-core value is the sum of the
-    processes' rates)."""
-    from paper_2510_24175_gb300 import inputs
-    ncell = inputs.orszag_tang_3d(n).ncell
-    _cpu_init(n)
-    reps1, t1 = _cpu_timed(target_s)
-    single = ncell * reps1 / t1
+def cpu_oracle_sample(n: int = 256, slab: int = 32):
+    """Times the CPU FP64 oracle as it stands on the bench workload itself
+    (3-D Orszag-Tang n^3, one RK2 step with its CFL wave-speed reduction):
+    on all host cores through the slab-parallel runner (one process per
+    core, each stepping a z slab with its ghost planes exchanged through
+    shared memory; bitwise the single-process oracle), and on one core for a
+    z slab of `slab` planes of the same grid (the same per-zone arithmetic)."""
+    import oracle as orc
+    from oracle.slab import SlabRunner
+    pb, g, U0 = _cpu_problem(n)
     ncores = os.cpu_count() or 1
-    with _cpu_pool(ncores, n) as pool:
-        res = pool.map(_cpu_timed, [target_s] * ncores, chunksize=1)
-    allc = sum(ncell * r / t for r, t in res)
-    return {"value": allc, "unit": "zone-updates/s", "cores": ncores, "kind": "oracle",
-            "sample": f"one RK2 step of 3-D Orszag-Tang at {n}^3 (FP64, MC, HLLD+GLM) repeated "
-                      f"for ~{target_s:.0f} s in each of {ncores} concurrent single-threaded "
-                      f"processes ({sum(r for r, _ in res)} steps); single process: "
-                      f"{reps1} steps in {t1:.1f} s",
+    with SlabRunner(g, nproc=ncores) as r:
+        t0 = time.perf_counter()
+        r.run(U0, 1)
+        el = time.perf_counter() - t0
+        nproc = r.nproc
+    allc = pb.ncell / el
+    # one core: one step of an n x n x slab periodic box with the same cells
+    sub = orc.Grid(n=(n, n, slab), dx=g.dx, gamma=g.gamma, glm_alpha=g.glm_alpha,
+                   limiter=g.limiter, bc=g.bc, cfl=g.cfl)
+    Us = np.ascontiguousarray(U0[:, :slab])
+    t0 = time.perf_counter()
+    orc.run(Us, sub, 1)
+    t1 = time.perf_counter() - t0
+    single = n * n * slab / t1
+    return {"value": allc, "unit": "zone-updates/s", "cores": nproc, "kind": "oracle",
+            "sample": f"one RK2 step (with its CFL wave-speed reduction) of the 3-D "
+                      f"Orszag-Tang {n}^3 workload itself on {nproc} host cores: {nproc} "
+                      f"single-threaded oracle processes, one z slab each, ghost planes "
+                      f"exchanged through shared memory ({el:.1f} s); single_thread_value: "
+                      f"one RK2 step of an {n} x {n} x {slab} periodic box of the same cells "
+                      f"(its first {slab} planes) in one process ({t1:.1f} s)",
             "single_thread_value": single, "host_cores": ncores}
 
 
@@ -221,32 +207,36 @@ def workload_config(n: int, world: int, t_reached=None) -> dict:
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on the bench workload
+    itself (3-D Orszag-Tang n^3 FP64, MC, HLLD + GLM, RK2), every bench step
+    one full step on all host cores through the slab-parallel runner."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from paper_2510_24175_gb300 import inputs
-    n = 48
-    ncell = inputs.orszag_tang_3d(n).ncell
+    from oracle.slab import SlabRunner
+    n = args.n
+    pb, g, U0 = _cpu_problem(n)
     ncores = os.cpu_count() or 1
-    with _cpu_pool(ncores, n) as pool:
-        for _ in range(args.warmup):
-            pool.map(_cpu_step, range(ncores), chunksize=1)
+    with SlabRunner(g, nproc=ncores) as r:
+        r.run(U0, max(args.warmup, 0))
+        U = r.A.copy()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            pool.map(_cpu_step, range(ncores), chunksize=1)
+        res = r.run(U, args.steps)
         el = time.perf_counter() - t0
-    val = ncores * ncell * args.steps / el
-    sample = (f"each bench step: one RK2 step of the same Orszag-Tang problem on a {n}^3 "
-              f"periodic box (the same per-zone arithmetic as the 256^3 workload) in each of "
-              f"{ncores} concurrent single-threaded CPU oracle processes")
+        nproc = r.nproc
+    val = pb.ncell * args.steps / el
+    sample = (f"each bench step: one full RK2 step (with its CFL wave-speed reduction) of the "
+              f"{n}^3 Orszag-Tang workload on {nproc} host cores ({nproc} single-threaded "
+              f"oracle processes, one z slab each, ghost planes exchanged through shared "
+              f"memory; bitwise the single-process oracle); t reached {res.t:.6e}")
     print(json.dumps({
         "impl": "reference", "metric": "zone-updates/s", "value": val,
         "unit": "zone-updates/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (closed-form Orszag-Tang initial condition)",
-        "config": workload_config(args.n, 1),
-        "cpu_baseline": {"value": val, "unit": "zone-updates/s", "cores": ncores,
+        "config": {**workload_config(n, 1), "parallelism": f"{nproc} host processes (z slabs)"},
+        "cpu_baseline": {"value": val, "unit": "zone-updates/s", "cores": nproc,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "zone-updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}))

@@ -9,8 +9,8 @@ the FP32 path recomputes the pressure in FP64 (p < 1e-3 (gamma-1) E).  Every
 floor and branch decision is checked, on the oracle's own stage inputs, to be
 far from its threshold (> 0.1 %), so both sides take each one alike and the
 counters must be equal exactly.  FP64 states match the oracle to 1e-12
-relative L1; FP32 states to the bounds stated below (measured errors are
-quoted in the design notes)."""
+relative L1; FP32 states to the bounds stated below, about 3x the errors
+measured on GB300 (quoted beside each bound)."""
 import numpy as np
 import pytest
 
@@ -68,7 +68,8 @@ def test_fp32_floors_and_fp64_pressure_branch_match_the_oracle(bc):
     _dt_chain_matches(hist, ref, 1e-5)
     assert cnt == {"rho_floor": n_rho, "p_floor": n_p, "status": 0, "p_f64": n_branch}
     err = rel_l1(U, ref.U, floor=0.1)
-    assert float(err.max()) <= 2e-5, err
+    print(f"floor defects FP32 {bc}: counts {cnt}, rel L1 max {err.max():.3e}")
+    assert float(err.max()) <= 5e-6, err  # measured 1.5e-6 (periodic), 5.9e-7 (outflow)
 
 
 def test_fp32_isolated_cold_cells_take_the_fp64_pressure_branch():
@@ -78,7 +79,8 @@ def test_fp32_isolated_cold_cells_take_the_fp64_pressure_branch():
     U, hist, cnt = gpu_run(pb, NSTEPS, precision=1, record=True)
     assert cnt == {"rho_floor": 0, "p_floor": 0, "status": 0, "p_f64": n_branch}
     err = rel_l1(U, ref.U, floor=0.1)
-    assert float(err.max()) <= 2e-5, err
+    print(f"cold cells FP32: counts {cnt}, rel L1 max {err.max():.3e}")
+    assert float(err.max()) <= 5e-7, err  # measured 1.2e-7
     U64, _, cnt64 = gpu_run(pb, NSTEPS, precision=0)
     assert cnt64 == {"rho_floor": 0, "p_floor": 0, "status": 0, "p_f64": 0}
     assert float(rel_l1(U64, ref.U).max()) <= TOL64
@@ -103,11 +105,13 @@ def test_fp32_cold_flow_every_cell_takes_the_fp64_pressure_branch():
     assert cnt == {"rho_floor": 0, "p_floor": 0, "status": 0, "p_f64": n_branch}
     U = s.get_state().cpu().numpy()
     err = rel_l1(U, ref.U, floor=0.1)
-    assert float(err.max()) <= 1e-6, err
+    assert float(err.max()) <= 1e-6, err  # measured 5e-8 .. 2.2e-7 per variable
     V = s.get_state(kind=m.MHD_PRIM).cpu().numpy()
     Vref, _ = orc.cons_to_prim(ref.U, orc.Grid(n=pb.n, gamma=pb.gamma))
     p_err = np.abs(V[7] - Vref[7]).sum() / np.abs(Vref[7]).sum()
-    assert p_err <= 2e-2, p_err
+    print(f"cold flow FP32: counts {cnt}, rel L1 per variable {np.array2string(err, precision=2)}, "
+          f"pressure rel L1 {p_err:.3e}")
+    assert p_err <= 2e-3, p_err  # measured 4.8e-4: E stored in FP32, p ~ 2e-4 E
 
 
 def test_fp64_cold_flow_matches_the_oracle():
