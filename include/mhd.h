@@ -53,7 +53,12 @@ enum {
  * WENO-Z (Borges et al. 2008; the reconstruction of the paper's runs,
  * Section 4.2; needs active dimensions of at least 3 cells). */
 enum { MHD_LIM_FLAT = 0, MHD_LIM_MINMOD = 1, MHD_LIM_MC = 2, MHD_LIM_WENOZ = 3 };
-enum { MHD_BC_PERIODIC = 0, MHD_BC_OUTFLOW = 1 };
+/* Boundary conditions of a side.  MHD_BC_HALO: the side is a subdomain
+ * boundary of a decomposed grid -- its ghost cells are supplied by the caller
+ * before every stage (mhd_step_stage), the paper's boundary exchange between
+ * processes (Section 3.2); needs three active GLM dimensions (not the
+ * adjoint), and may face MHD_BC_OUTFLOW or MHD_BC_HALO on the other side. */
+enum { MHD_BC_PERIODIC = 0, MHD_BC_OUTFLOW = 1, MHD_BC_HALO = 2 };
 /* MHD_FP64: all arithmetic in FP64.  MHD_FP32: FP32 state and stage
  * arithmetic; FP64 for the time-step reduction result and dt, the
  * conservation sums, and the pressure-floor branch of cons->prim. */
@@ -158,7 +163,9 @@ int mhd_dt(mhd_ctx* ctx, double* dt, double* ch);
  * c_h only enters the (unused) psi flux.  dt > 0 and ch > 0 are used as
  * given; dt <= 0 uses the CFL rule on the device (clamped to t_end when
  * t_end > 0); ch <= 0 uses c_h = lambda of the current state.  Does not
- * synchronise: dt and c_h stay on the device (see mhd_step_info). */
+ * synchronise: dt and c_h stay on the device (see mhd_step_info).  Contexts
+ * with halo faces step with the staged calls (mhd_step_begin) instead:
+ * MHD_ERR_STATE here. */
 int mhd_step(mhd_ctx* ctx, double dt, double ch);
 
 /* nsteps steps with the CFL time step and c_h = lambda, as nsteps calls of
@@ -284,6 +291,64 @@ int mhd_profile_read(mhd_ctx* ctx, long long counts[6], double ms[6]);
  * enqueued. */
 int mhd_conserved_sums_noalloc(const mhd_config* cfg, const void* U, double out[8],
                                void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Staged steps and halo faces: a grid decomposed into blocks, one context
+ * per block (in one process or one per GPU), advanced together.  Section 3.2:
+ * the boundary exchange is the only communication between processes; the
+ * method also needs the global maximum wave speed for the common dt and c_h.
+ * Per step, for every block:
+ *   lam = 0 (device 64-bit word); mhd_lambda_max_into(ctx, lam) for every
+ *   block (then an allreduce(MAX) of lam across processes);
+ *   mhd_step_begin(ctx, 0, 0, lam);
+ *   per stage (2 for RK2, 3 for SSP-RK3): fill every halo face's buffer of
+ *   every block (mhd_halo_pack of the neighbour across the face, into the
+ *   buffer directly or through a send/receive), then mhd_step_stage(ctx,
+ *   halo buffers) for every block.
+ * Each block's cells then evolve bitwise as in the undecomposed grid.
+ * Halo buffer of face f (f = 2 d + side: 0 x-, 1 x+, 2 y-, 3 y+, 4 z-, 5 z+):
+ * mhd_halo_bytes() bytes of device memory owned by the caller, holding the
+ * block's ghost cells on that side in the context's precision with the
+ * grid's SoA layout restricted to the ghost slab: [9][nz][ny][g] for x faces,
+ * [9][nz][g][nx] for y faces, [9][g][ny][nx] for z faces, g = 2 (PLM) or 3
+ * (WENO-Z); layer l holds ghost index l - g (low side) or n_d + l (high
+ * side).  The stage kernels read only face ghosts (no edge or corner cells).
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of the halo buffer of face f (see above). */
+int mhd_halo_bytes(const mhd_ctx* ctx, int face, size_t* bytes);
+
+/* Packs the g interior layers of this block next to face f, taken from the
+ * input of the next stage (U^n outside a staged step, then each stage's
+ * output), into d_dst (device) with the layout of the halo buffer of the
+ * opposite face of the block across f (whose extents in the two tangential
+ * dimensions must equal this block's).  Enqueued on the context's stream. */
+int mhd_halo_pack(mhd_ctx* ctx, int face, void* d_dst);
+
+/* Raises *d_bits (device, 64-bit; zero it before the first block) to this
+ * block's maximum wave speed lambda (reduced on the device first if the
+ * state is new): the FP64 bit pattern, which orders like the value for the
+ * non-negative speeds, so an integer maximum over blocks (atomic here, an
+ * allreduce(MAX) of int64 or uint64 across processes) is the exact global
+ * maximum.  A NaN speed is written as the canonical quiet NaN, which
+ * dominates.  Not inside a staged step.  Enqueued on the context's stream. */
+int mhd_lambda_max_into(mhd_ctx* ctx, void* d_bits);
+
+/* Opens a step of a GLM context (with or without halo faces): dt and c_h as
+ * in mhd_step (dt <= 0 or ch <= 0: the CFL rule), lambda taken from
+ * d_lambda_bits (device word filled by mhd_lambda_max_into: the maximum over
+ * all blocks) or, when NULL, from this context's own state.  Enqueues the
+ * step-prepare kernel.  The step's stages follow with mhd_step_stage. */
+int mhd_step_begin(mhd_ctx* ctx, double dt, double ch, const void* d_lambda_bits);
+
+/* Runs the next stage of the open step, reading the ghost cells of every
+ * MHD_BC_HALO side from d_halo[f] (device buffers of mhd_halo_bytes; entries
+ * of other sides are ignored, d_halo may be NULL without halo faces).  The
+ * last stage also applies the GLM damping and reduces this block's new
+ * maximum wave speed, and closes the step.  Enqueued on the context's
+ * stream; the buffers must hold the ghosts of this stage's input when the
+ * stage runs (stream order). */
+int mhd_step_stage(mhd_ctx* ctx, const void* const d_halo[6]);
 
 /* ---------------------------------------------------------------------------
  * Batched ensemble: independent 3-D boxes (each with its own grid, domain,

@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmhd_gb300.so")
 MHD_OK, MHD_ERR_INVALID, MHD_ERR_NOMEM, MHD_ERR_CUDA = 0, -1, -2, -3
 MHD_ERR_NONFINITE, MHD_ERR_TIMEOUT, MHD_ERR_STATE = -4, -5, -6
 MHD_LIM_FLAT, MHD_LIM_MINMOD, MHD_LIM_MC, MHD_LIM_WENOZ = 0, 1, 2, 3
-MHD_BC_PERIODIC, MHD_BC_OUTFLOW = 0, 1
+MHD_BC_PERIODIC, MHD_BC_OUTFLOW, MHD_BC_HALO = 0, 1, 2
 MHD_FP64, MHD_FP32 = 0, 1
 MHD_HOST, MHD_DEVICE = 0, 1
 MHD_CONS, MHD_PRIM = 0, 1
@@ -40,7 +40,8 @@ EXPORTED = ["mhd_config_default", "mhd_workspace_bytes", "mhd_create", "mhd_set_
             "mhd_adjoint_step_stage1", "mhd_get_stage1",
             "mhd_profile_enable", "mhd_profile_read", "mhd_conserved_sums_noalloc",
             "mhd_last_error", "mhd_destroy", "mhd_set_face_field", "mhd_get_face_field",
-            "mhd_divb_max",
+            "mhd_divb_max", "mhd_halo_bytes", "mhd_halo_pack", "mhd_lambda_max_into",
+            "mhd_step_begin", "mhd_step_stage",
             "mhd_ensemble_workspace_bytes", "mhd_ensemble_create", "mhd_ensemble_set_state",
             "mhd_ensemble_get_state", "mhd_ensemble_step", "mhd_ensemble_info",
             "mhd_ensemble_autotune", "mhd_ensemble_last_error", "mhd_ensemble_destroy"]
@@ -114,6 +115,11 @@ def lib():
         L.mhd_ensemble_last_error.restype = ctypes.c_char_p
         L.mhd_ensemble_destroy.argtypes = [vp]
         L.mhd_destroy.argtypes = [vp]
+        L.mhd_halo_bytes.argtypes = [vp, i, ctypes.POINTER(ctypes.c_size_t)]
+        L.mhd_halo_pack.argtypes = [vp, i, vp]
+        L.mhd_lambda_max_into.argtypes = [vp, vp]
+        L.mhd_step_begin.argtypes = [vp, d, d, vp]
+        L.mhd_step_stage.argtypes = [vp, ctypes.POINTER(vp)]
         for name in EXPORTED:
             if not name.endswith("last_error"):
                 getattr(L, name).restype = ctypes.c_int
@@ -204,6 +210,37 @@ def mhd_step_record(ctx, out):
     """(t, dt, c_h, steps) of the last step into ``out`` (4 float64 values of
     a CUDA tensor), enqueued without synchronising."""
     _check(lib().mhd_step_record(ctx, _ptr(out)), ctx, "mhd_step_record")
+
+
+def mhd_halo_bytes(ctx, face: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().mhd_halo_bytes(ctx, int(face), ctypes.byref(b)), ctx, "mhd_halo_bytes")
+    return b.value
+
+
+def mhd_halo_pack(ctx, face: int, dst):
+    """The g boundary layers next to ``face`` of the next stage's input into
+    ``dst`` (a CUDA tensor of mhd_halo_bytes bytes)."""
+    _check(lib().mhd_halo_pack(ctx, int(face), _ptr(dst)), ctx, "mhd_halo_pack")
+
+
+def mhd_lambda_max_into(ctx, bits):
+    """Raises ``bits`` (a one-element int64 CUDA tensor) to the context's
+    maximum wave speed, as FP64 bits."""
+    _check(lib().mhd_lambda_max_into(ctx, _ptr(bits)), ctx, "mhd_lambda_max_into")
+
+
+def mhd_step_begin(ctx, dt: float = 0.0, ch: float = 0.0, lam_bits=None):
+    p = _ptr(lam_bits) if lam_bits is not None else None
+    _check(lib().mhd_step_begin(ctx, float(dt), float(ch), p), ctx, "mhd_step_begin")
+
+
+def mhd_step_stage(ctx, halo=None):
+    """halo: six CUDA tensors or None (faces without halo buffers)."""
+    arr = None
+    if halo is not None:
+        arr = (ctypes.c_void_p * 6)(*[(t.data_ptr() if t is not None else None) for t in halo])
+    _check(lib().mhd_step_stage(ctx, arr), ctx, "mhd_step_stage")
 
 
 def mhd_step_n(ctx, nsteps: int):
@@ -418,6 +455,46 @@ class MHD:
         assert out.is_cuda and out.dtype == torch.float64 and out.is_contiguous()
         assert out.numel() >= 4
         mhd_step_record(self.ctx, out)
+
+    # -- staged steps and halo faces (see paper_2510_24175_gb300.decomp) --
+    def halo_bytes(self, face: int) -> int:
+        return mhd_halo_bytes(self.ctx, face)
+
+    def halo_buffer(self, face: int):
+        """A CUDA tensor sized for face ``face``'s halo buffer, in the
+        context's precision."""
+        torch = _torch()
+        dt = torch.float64 if self.config.precision == MHD_FP64 else torch.float32
+        es = 8 if dt == torch.float64 else 4
+        return torch.empty(self.halo_bytes(face) // es, dtype=dt, device="cuda")
+
+    def halo_pack(self, face: int, dst):
+        torch = _torch()
+        want = torch.float64 if self.config.precision == MHD_FP64 else torch.float32
+        assert dst.is_cuda and dst.is_contiguous() and dst.dtype == want
+        assert dst.numel() * dst.element_size() >= self.halo_bytes(face)
+        mhd_halo_pack(self.ctx, face, dst)
+
+    def lambda_max_into(self, bits):
+        torch = _torch()
+        assert bits.is_cuda and bits.dtype == torch.int64 and bits.numel() >= 1
+        mhd_lambda_max_into(self.ctx, bits)
+
+    def step_begin(self, dt: float = 0.0, ch: float = 0.0, lam_bits=None):
+        if lam_bits is not None:
+            torch = _torch()
+            assert lam_bits.is_cuda and lam_bits.dtype == torch.int64
+        mhd_step_begin(self.ctx, dt, ch, lam_bits)
+
+    def step_stage(self, halo=None):
+        if halo is not None:
+            torch = _torch()
+            want = torch.float64 if self.config.precision == MHD_FP64 else torch.float32
+            for f, t in enumerate(halo):
+                if t is not None:
+                    assert t.is_cuda and t.is_contiguous() and t.dtype == want
+                    assert t.numel() * t.element_size() >= self.halo_bytes(f)
+        mhd_step_stage(self.ctx, halo)
 
     def counters(self):
         """Per-stage, per-cell counts of the floor branches of cons->prim

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmhd_gb300.so")
 SOURCES = ["mhd_api.cu", "mhd_aux.cu", "mhd_stage_f64.cu", "mhd_stage_f32.cu",
-           "mhd_adjoint.cu", "mhd_noalloc.cu", "mhd_ensemble.cu", "mhd_ct.cu"]
+           "mhd_stage_halo_f64.cu", "mhd_stage_halo_f32.cu", "mhd_adjoint.cu", "mhd_noalloc.cu",
+           "mhd_ensemble.cu", "mhd_ct.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

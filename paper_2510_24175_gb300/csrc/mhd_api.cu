@@ -116,12 +116,25 @@ static int validate(const mhd_config* c, char* msg, size_t len) {
         snprintf(msg, len, "WENO-Z needs active dimensions of at least 3 cells");
         return MHD_ERR_INVALID;
       }
+  bool halo = false;
   for (int d = 0; d < 3; ++d) {
     const int lo = c->bc[2 * d], hi = c->bc[2 * d + 1];
-    if ((lo != MHD_BC_PERIODIC && lo != MHD_BC_OUTFLOW) ||
-        (hi != MHD_BC_PERIODIC && hi != MHD_BC_OUTFLOW) ||
-        ((lo == MHD_BC_PERIODIC) != (hi == MHD_BC_PERIODIC))) {
+    auto ok = [](int b) { return b == MHD_BC_PERIODIC || b == MHD_BC_OUTFLOW || b == MHD_BC_HALO; };
+    if (!ok(lo) || !ok(hi) || ((lo == MHD_BC_PERIODIC) != (hi == MHD_BC_PERIODIC))) {
       snprintf(msg, len, "bad boundary conditions in dimension %d", d);
+      return MHD_ERR_INVALID;
+    }
+    halo = halo || lo == MHD_BC_HALO || hi == MHD_BC_HALO;
+  }
+  if (halo) {
+    const int gw = c->limiter == MHD_LIM_WENOZ ? 3 : 2;
+    for (int d = 0; d < 3; ++d)
+      if (c->n[d] < gw) {
+        snprintf(msg, len, "halo faces need three active dimensions of at least %d cells", gw);
+        return MHD_ERR_INVALID;
+      }
+    if (c->divb != MHD_DIVB_GLM || (c->flags & MHD_FLAG_ADJOINT)) {
+      snprintf(msg, len, "halo faces are for GLM contexts without the adjoint");
       return MHD_ERR_INVALID;
     }
   }
@@ -377,8 +390,13 @@ int mhd_create(const mhd_config* cfg, void* d_workspace, size_t bytes, void* str
     // kernel attributes now, so that no later launch (a captured one in
     // particular) needs the driver call
     const bool ct = cfg->divb == MHD_DIVB_CT;
-    const cudaError_t pe = c->esize == 8 ? mhd::prepare_stage_kernels<double>(c->grid, ct)
-                                         : mhd::prepare_stage_kernels<float>(c->grid, ct);
+    c->has_halo = false;
+    for (int s = 0; s < 6; ++s) c->has_halo = c->has_halo || cfg->bc[s] == MHD_BC_HALO;
+    cudaError_t pe = c->esize == 8 ? mhd::prepare_stage_kernels<double>(c->grid, ct)
+                                   : mhd::prepare_stage_kernels<float>(c->grid, ct);
+    if (pe == cudaSuccess && c->has_halo)
+      pe = c->esize == 8 ? mhd::prepare_stage_kernels_halo<double>(c->grid)
+                         : mhd::prepare_stage_kernels_halo<float>(c->grid);
     if (pe != cudaSuccess) {
       delete c;
       return mhd::free_fail(MHD_ERR_CUDA, "mhd_create: kernel attributes: %s",
@@ -393,6 +411,8 @@ int mhd_create(const mhd_config* cfg, void* d_workspace, size_t bytes, void* str
   c->stage1_valid = false;
   c->have_state = false;
   c->lam_valid = false;
+  c->step_open = false;
+  c->stage_next = 0;
   snprintf(c->err, sizeof(c->err), "no error");
   cudaError_t e = cudaMemsetAsync(c->scal, 0, sizeof(Scalars), c->stream);
   if (e != cudaSuccess) {
@@ -452,6 +472,7 @@ int mhd_set_state(mhd_ctx* c, const double* U, int where, int kind) {
   c->lam_valid = false;
   c->faces_set = false;
   c->stage1_valid = false;
+  c->step_open = false;
   return MHD_OK;
 }
 
@@ -613,26 +634,9 @@ static int copy_planes(mhd_ctx* c, double* dst, const double* src, int z0, int z
 
 static int step_impl(mhd_ctx* c, double dt, double ch, const HostOut* ho);
 
-// After an FP64 RK2 GLM step, U_b holds that step's first stage U1 (read by
-// mhd_get_stage1); RK3 and constrained transport use U_b otherwise.
-static bool keeps_stage1(const mhd_ctx* c) {
-  return c->esize == 8 && c->cfg.rk_order != 3 && c->cfg.divb == MHD_DIVB_GLM;
-}
-
-int mhd_step(mhd_ctx* c, double dt, double ch) { return step_impl(c, dt, ch, nullptr); }
-
-static int step_impl(mhd_ctx* c, double dt, double ch, const HostOut* ho) {
-  if (!c) return MHD_ERR_INVALID;
-  if (!c->have_state) return fail(c, MHD_ERR_STATE, "mhd_step before mhd_set_state");
-  if (c->cfg.divb == MHD_DIVB_CT && !c->faces_set)
-    return fail(c, MHD_ERR_STATE, "constrained transport: mhd_set_face_field after mhd_set_state");
-  if (std::isnan(dt) || std::isnan(ch) || std::isinf(dt) || std::isinf(ch))
-    return fail(c, MHD_ERR_INVALID, "mhd_step: non-finite dt or ch");
-  if (!(dt > 0.0) || !(ch > 0.0)) {
-    int rc = ensure_lambda(c);
-    if (rc != MHD_OK) return rc;
-  }
-  c->stage1_valid = false;  // until this step has written its first stage
+// The step-prepare kernel: dt and c_h of the step (as given, or from the
+// wave speed in the scalar block), dt / dx_d, the damping factor, the time.
+static int launch_prepare(mhd_ctx* c, double dt, double ch) {
   mhd::PrepArgs a;
   a.dt_req = dt;
   a.ch_req = ch;
@@ -645,25 +649,56 @@ static int step_impl(mhd_ctx* c, double dt, double ch, const HostOut* ho) {
     a.dx[d] = c->grid.dx[d];
     a.active[d] = c->grid.n[d] > 1;
   }
-  {
-    ProfScope ps(c, 0);
-    CK(c, mhd::launch_prep(a, &c->scal->sc, &c->scal->lam_bits, &c->scal->est_bits,
-                           &c->scal->status, c->stream));
-  }
-  // stage sequence: (kernel stage, profile class, input, U^n, output, a_n, a_w)
-  struct St { int kind, cls; void *win, *un, *out; double an, aw; };
-  St seq[3];
-  int nst;
+  ProfScope ps(c, 0);
+  CK(c, mhd::launch_prep(a, &c->scal->sc, &c->scal->lam_bits, &c->scal->est_bits,
+                         &c->scal->status, c->stream));
+  return MHD_OK;
+}
+
+// The stages of one step: (kernel stage, profile class, input, U^n, output,
+// a_n, a_w); returns their number.
+struct St { int kind, cls; void *win, *un, *out; double an, aw; };
+static int stage_sequence(const mhd_ctx* c, St seq[3]) {
   if (c->cfg.rk_order == 3) {
     seq[0] = {1, 1, c->Ua, nullptr, c->Ub, 0.0, 1.0};
     seq[1] = {3, 4, c->Ub, c->Ua, c->Uc, 0.75, 0.25};
     seq[2] = {2, 2, c->Uc, c->Ua, c->Ua, 1.0 / 3.0, 2.0 / 3.0};
-    nst = 3;
-  } else {
-    seq[0] = {1, 1, c->Ua, nullptr, c->Ub, 0.0, 1.0};
-    seq[1] = {2, 2, c->Ub, c->Ua, c->Ua, 0.5, 0.5};
-    nst = 2;
+    return 3;
   }
+  seq[0] = {1, 1, c->Ua, nullptr, c->Ub, 0.0, 1.0};
+  seq[1] = {2, 2, c->Ub, c->Ua, c->Ua, 0.5, 0.5};
+  return 2;
+}
+
+// After an FP64 RK2 GLM step, U_b holds that step's first stage U1 (read by
+// mhd_get_stage1); RK3 and constrained transport use U_b otherwise.
+static bool keeps_stage1(const mhd_ctx* c) {
+  return c->esize == 8 && c->cfg.rk_order != 3 && c->cfg.divb == MHD_DIVB_GLM;
+}
+
+int mhd_step(mhd_ctx* c, double dt, double ch) { return step_impl(c, dt, ch, nullptr); }
+
+static int step_impl(mhd_ctx* c, double dt, double ch, const HostOut* ho) {
+  if (!c) return MHD_ERR_INVALID;
+  if (!c->have_state) return fail(c, MHD_ERR_STATE, "mhd_step before mhd_set_state");
+  if (c->has_halo)
+    return fail(c, MHD_ERR_STATE, "the context has halo faces: its ghost cells come from the "
+                                  "caller (use mhd_step_begin / mhd_step_stage)");
+  if (c->step_open)
+    return fail(c, MHD_ERR_STATE, "a staged step (mhd_step_begin) is not finished");
+  if (c->cfg.divb == MHD_DIVB_CT && !c->faces_set)
+    return fail(c, MHD_ERR_STATE, "constrained transport: mhd_set_face_field after mhd_set_state");
+  if (std::isnan(dt) || std::isnan(ch) || std::isinf(dt) || std::isinf(ch))
+    return fail(c, MHD_ERR_INVALID, "mhd_step: non-finite dt or ch");
+  if (!(dt > 0.0) || !(ch > 0.0)) {
+    int rc = ensure_lambda(c);
+    if (rc != MHD_OK) return rc;
+  }
+  c->stage1_valid = false;  // until this step has written its first stage
+  int rc0 = launch_prepare(c, dt, ch);
+  if (rc0 != MHD_OK) return rc0;
+  St seq[3];
+  const int nst = stage_sequence(c, seq);
   for (int i = 0; i < nst; ++i) {
     const St& q = seq[i];
     int rc = c->cfg.divb == MHD_DIVB_CT
@@ -722,11 +757,141 @@ static int step_impl(mhd_ctx* c, double dt, double ch, const HostOut* ho) {
   return MHD_OK;
 }
 
+// ----------------------------------------------------- staged steps / halos --
+static int ghost_width(const mhd_ctx* c) { return c->cfg.limiter == MHD_LIM_WENOZ ? 3 : 2; }
+
+int mhd_halo_bytes(const mhd_ctx* c, int face, size_t* bytes) {
+  if (!c || !bytes || face < 0 || face > 5) return MHD_ERR_INVALID;
+  const int d = face >> 1;
+  size_t area = 1;
+  for (int e = 0; e < 3; ++e) area *= (size_t)(e == d ? ghost_width(c) : c->grid.n[e]);
+  *bytes = 9 * area * c->esize;
+  return MHD_OK;
+}
+
+int mhd_halo_pack(mhd_ctx* c, int face, void* d_dst) {
+  if (!c) return MHD_ERR_INVALID;
+  if (!d_dst || face < 0 || face > 5) return fail(c, MHD_ERR_INVALID, "mhd_halo_pack: bad argument");
+  if (!c->have_state) return fail(c, MHD_ERR_STATE, "mhd_halo_pack before mhd_set_state");
+  if (c->grid.n[face >> 1] < ghost_width(c))
+    return fail(c, MHD_ERR_INVALID, "mhd_halo_pack: dimension %d has fewer cells than the "
+                                    "ghost width", face >> 1);
+  St seq[3];
+  stage_sequence(c, seq);
+  const void* W = c->step_open ? seq[c->stage_next].win : c->Ua;
+  if (c->esize == 8)
+    CK(c, mhd::launch_halo_pack<double>(c->grid, static_cast<const double*>(W), face,
+                                        ghost_width(c), static_cast<double*>(d_dst), c->stream));
+  else
+    CK(c, mhd::launch_halo_pack<float>(c->grid, static_cast<const float*>(W), face,
+                                       ghost_width(c), static_cast<float*>(d_dst), c->stream));
+  return MHD_OK;
+}
+
+int mhd_lambda_max_into(mhd_ctx* c, void* d_bits) {
+  if (!c) return MHD_ERR_INVALID;
+  if (!d_bits) return fail(c, MHD_ERR_INVALID, "mhd_lambda_max_into: null pointer");
+  if (!c->have_state) return fail(c, MHD_ERR_STATE, "mhd_lambda_max_into before mhd_set_state");
+  if (c->step_open)
+    return fail(c, MHD_ERR_STATE, "mhd_lambda_max_into inside a staged step");
+  int rc = ensure_lambda(c);
+  if (rc != MHD_OK) return rc;
+  CK(c, mhd::launch_lambda_max_into(&c->scal->lam_bits, static_cast<unsigned long long*>(d_bits),
+                                    c->stream));
+  return MHD_OK;
+}
+
+int mhd_step_begin(mhd_ctx* c, double dt, double ch, const void* d_lambda_bits) {
+  if (!c) return MHD_ERR_INVALID;
+  if (!c->have_state) return fail(c, MHD_ERR_STATE, "mhd_step_begin before mhd_set_state");
+  if (c->cfg.divb != MHD_DIVB_GLM)
+    return fail(c, MHD_ERR_STATE, "staged steps are for GLM contexts");
+  if (c->step_open) return fail(c, MHD_ERR_STATE, "the previous staged step is not finished");
+  if (std::isnan(dt) || std::isnan(ch) || std::isinf(dt) || std::isinf(ch))
+    return fail(c, MHD_ERR_INVALID, "mhd_step_begin: non-finite dt or ch");
+  if (!(dt > 0.0) || !(ch > 0.0)) {
+    if (d_lambda_bits) {
+      CK(c, cudaMemcpyAsync(&c->scal->lam_bits, d_lambda_bits, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+      int rc = ensure_lambda(c);
+      if (rc != MHD_OK) return rc;
+    }
+  }
+  c->stage1_valid = false;
+  int rc = launch_prepare(c, dt, ch);
+  if (rc != MHD_OK) return rc;
+  c->step_open = true;
+  c->stage_next = 0;
+  return MHD_OK;
+}
+
+int mhd_step_stage(mhd_ctx* c, const void* const d_halo[6]) {
+  if (!c) return MHD_ERR_INVALID;
+  if (!c->step_open) return fail(c, MHD_ERR_STATE, "mhd_step_stage without mhd_step_begin");
+  if (c->has_halo) {
+    if (!d_halo) return fail(c, MHD_ERR_INVALID, "mhd_step_stage: the context has halo faces");
+    for (int f = 0; f < 6; ++f)
+      if (c->cfg.bc[f] == MHD_BC_HALO && !d_halo[f])
+        return fail(c, MHD_ERR_INVALID, "mhd_step_stage: no halo buffer for face %d", f);
+  }
+  St seq[3];
+  const int nst = stage_sequence(c, seq);
+  const St& q = seq[c->stage_next];
+  const bool last = c->stage_next == nst - 1;
+  {
+    ProfScope ps(c, q.cls);
+    if (c->esize == 8) {
+      const double* h[6];
+      for (int f = 0; f < 6; ++f) h[f] = d_halo ? static_cast<const double*>(d_halo[f]) : nullptr;
+      CK(c, c->has_halo
+                ? mhd::launch_stage_halo<double>(
+                      c->grid, q.kind, static_cast<const double*>(q.win),
+                      static_cast<const double*>(q.un), static_cast<double*>(q.out), &c->scal->sc,
+                      &c->scal->lam_bits, c->scal->floor_cnt, c->stream, q.an, q.aw, h,
+                      &c->scal->est_bits)
+                : mhd::launch_stage<double>(
+                      c->grid, q.kind, static_cast<const double*>(q.win),
+                      static_cast<const double*>(q.un), static_cast<double*>(q.out), &c->scal->sc,
+                      &c->scal->lam_bits, c->scal->floor_cnt, c->stream, q.an, q.aw, nullptr,
+                      nullptr, 0, -1, 0, &c->scal->est_bits));
+    } else {
+      const float* h[6];
+      for (int f = 0; f < 6; ++f) h[f] = d_halo ? static_cast<const float*>(d_halo[f]) : nullptr;
+      CK(c, c->has_halo
+                ? mhd::launch_stage_halo<float>(
+                      c->grid, q.kind, static_cast<const float*>(q.win),
+                      static_cast<const float*>(q.un), static_cast<float*>(q.out), &c->scal->sc,
+                      &c->scal->lam_bits, c->scal->floor_cnt, c->stream, q.an, q.aw, h, nullptr)
+                : mhd::launch_stage<float>(c->grid, q.kind, static_cast<const float*>(q.win),
+                                           static_cast<const float*>(q.un),
+                                           static_cast<float*>(q.out), &c->scal->sc,
+                                           &c->scal->lam_bits, c->scal->floor_cnt, c->stream,
+                                           q.an, q.aw));
+    }
+  }
+  if (last && c->esize == 8) {  // the exact maximum speed of the new state (pass 2)
+    ProfScope ps(c, 3);
+    CK(c, mhd::launch_speed_exact(c->grid, static_cast<const double*>(q.out), &c->scal->est_bits,
+                                  &c->scal->lam_bits, c->stream));
+  }
+  if (last) {
+    c->step_open = false;
+    c->stage_next = 0;
+    c->lam_valid = true;
+  } else {
+    c->stage_next++;
+  }
+  return MHD_OK;
+}
+
 int mhd_step_n(mhd_ctx* c, int nsteps) {
   if (!c) return MHD_ERR_INVALID;
   if (nsteps < 0) return fail(c, MHD_ERR_INVALID, "mhd_step_n: nsteps = %d < 0", nsteps);
   if (nsteps == 0) return MHD_OK;
   if (!c->have_state) return fail(c, MHD_ERR_STATE, "mhd_step_n before mhd_set_state");
+  if (c->has_halo || c->step_open)
+    return fail(c, MHD_ERR_STATE, "mhd_step_n: halo faces or an unfinished staged step");
   if (c->cfg.divb == MHD_DIVB_CT && !c->faces_set)
     return fail(c, MHD_ERR_STATE, "constrained transport: mhd_set_face_field after mhd_set_state");
   // the wave speed of the current state is reduced outside the graph: the
@@ -771,6 +936,9 @@ int mhd_step_n(mhd_ctx* c, int nsteps) {
 int mhd_step_host(mhd_ctx* c, const double* U_in, double* U_out, double dt, double ch) {
   if (!c) return MHD_ERR_INVALID;
   if (!U_in || !U_out) return fail(c, MHD_ERR_INVALID, "mhd_step_host: null buffer");
+  if (c->has_halo)
+    return fail(c, MHD_ERR_STATE, "mhd_step_host: the context has halo faces (use the staged "
+                                  "calls mhd_step_begin / mhd_step_stage)");
   if (c->cfg.divb == MHD_DIVB_CT)
     return fail(c, MHD_ERR_INVALID,
                 "mhd_step_host: constrained transport needs a face field; use mhd_set_state, "

@@ -268,6 +268,70 @@ static inline unsigned grid_for(long long n, int nsm) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
+// ------------------------------------------------------------ halo faces --
+// One thread per halo element, in the destination's order: the source is the
+// cell whose coordinate along the face normal d is the layer (low face) or
+// n_d - gh + layer (high face).
+template <class T>
+__global__ void halo_pack_kernel(const T* __restrict__ W, T* __restrict__ dst, int n0, int n1,
+                                 int n2, long long ncell, int d, int hi, int gh) {
+  const int e0 = d == 0 ? gh : n0, e1 = d == 1 ? gh : n1, e2 = d == 2 ? gh : n2;
+  const long long per_var = (long long)e0 * e1 * e2;
+  const long long total = 9 * per_var;
+  const int n_d = d == 0 ? n0 : (d == 1 ? n1 : n2);
+  const int shift = hi ? n_d - gh : 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(q / per_var);
+    long long r = q - v * per_var;
+    int c0 = (int)(r % e0);
+    r /= e0;
+    int c1 = (int)(r % e1);
+    int c2 = (int)(r / e1);
+    if (d == 0) c0 += shift;
+    if (d == 1) c1 += shift;
+    if (d == 2) c2 += shift;
+    dst[q] = W[v * ncell + ((long long)c2 * n1 + c1) * n0 + c0];
+  }
+}
+
+template <class T>
+cudaError_t launch_halo_pack(const Grid& g, const T* W, int face, int gh, T* dst,
+                             cudaStream_t stream) {
+  const int d = face >> 1;
+  if (face < 0 || face > 5 || gh < 1 || gh > g.n[d]) return cudaErrorInvalidValue;
+  long long area = 1;
+  for (int e = 0; e < 3; ++e) area *= e == d ? gh : g.n[e];
+  halo_pack_kernel<T><<<grid_for(9 * area, g.nsm), 256, 0, stream>>>(
+      W, dst, g.n[0], g.n[1], g.n[2], g.ncell, d, face & 1, gh);
+  return cudaGetLastError();
+}
+template cudaError_t launch_halo_pack<double>(const Grid&, const double*, int, int, double*,
+                                              cudaStream_t);
+template cudaError_t launch_halo_pack<float>(const Grid&, const float*, int, int, float*,
+                                             cudaStream_t);
+
+// The wave-speed maxima of subdomains combine by an integer maximum of their
+// bit patterns (non-negative doubles order like their patterns; the
+// canonical quiet NaN orders above +inf, also as a signed 64-bit integer).
+__global__ void lambda_max_into_kernel(const unsigned long long* lam_bits,
+                                       unsigned long long* dst) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  unsigned long long b = *lam_bits;
+  if ((b & 0x7fffffffffffffffull) > 0x7ff0000000000000ull)
+    b = 0x7ff8000000000000ull;  // NaN (either sign)
+  else if (b >> 63)
+    b = 0ull;  // -0 (wave speeds are not negative)
+  atomicMax(dst, b);
+}
+
+cudaError_t launch_lambda_max_into(const unsigned long long* lam_bits, unsigned long long* dst,
+                                   cudaStream_t stream) {
+  lambda_max_into_kernel<<<1, 32, 0, stream>>>(lam_bits, dst);
+  return cudaGetLastError();
+}
+
+
 template <class T>
 __global__ void prim_to_cons_kernel(const double* __restrict__ V, T* __restrict__ U,
                                     long long ncell, Phys<double> ph) {

@@ -53,6 +53,12 @@ struct mhd_ctx {
   cudaStream_t stream;
   bool have_state;
   bool lam_valid;
+  // halo faces (a side with MHD_BC_HALO) and the staged step of
+  // mhd_step_begin / mhd_step_stage: a step is open between the two, and
+  // stage_next is the next stage's index in the step's stage sequence
+  bool has_halo;
+  bool step_open;
+  int stage_next;
   bool stage1_valid;     // U_b holds the last step's first stage (mhd_get_stage1)
   double inv_dx_sum, dh_min;
   // mhd_step_host: a transfer stream and its events (made on first use), and

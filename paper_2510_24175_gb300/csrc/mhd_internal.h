@@ -122,6 +122,27 @@ cudaError_t launch_cons_to_prim(const Grid& g, const T* U, double* V, cudaStream
 cudaError_t launch_f64_to_f32(const double* in, float* out, long long n, cudaStream_t stream);
 cudaError_t launch_f32_to_f64(const float* in, double* out, long long n, cudaStream_t stream);
 
+// Stage kernels with halo faces (mhd_stage_halo_f64.cu / _f32.cu): as
+// launch_stage for a 3-D GLM grid, the ghost cells of every kBcHalo side read
+// from halo[f] (f = 2 d + side; layout at halo_cell in mhd_stage.cuh).
+template <class T>
+cudaError_t launch_stage_halo(const Grid& g, int stage, const T* win, const T* un, T* uout,
+                              const StepScalars* sc, unsigned long long* lam_bits,
+                              unsigned long long* floor_cnt, cudaStream_t stream, double a_n,
+                              double a_w, const T* const* halo, unsigned int* est_bits);
+template <class T>
+cudaError_t prepare_stage_kernels_halo(const Grid& g);
+
+// The gh interior layers of W next to face f (f = 2 d + side) into dst, in the
+// layout of the halo buffer of the opposite face of the neighbour across f.
+template <class T>
+cudaError_t launch_halo_pack(const Grid& g, const T* W, int face, int gh, T* dst,
+                             cudaStream_t stream);
+// atomicMax of the wave-speed word *lam_bits (FP64 bits; a NaN made the
+// canonical quiet NaN, a negative zero +0) into *dst.
+cudaError_t launch_lambda_max_into(const unsigned long long* lam_bits, unsigned long long* dst,
+                                   cudaStream_t stream);
+
 template <class T>
 cudaError_t launch_flux_batch(const T* VL, const T* VR, T* F, long long nface, int dir,
                               double ch, double gamma, cudaStream_t stream);

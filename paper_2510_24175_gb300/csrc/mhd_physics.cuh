@@ -27,7 +27,9 @@ namespace mhd {
 enum { kRHO = 0, kVX = 1, kVY = 2, kVZ = 3, kBX = 4, kBY = 5, kBZ = 6, kPRS = 7, kPSI = 8,
        kNV = 9 };
 enum { kLimFlat = 0, kLimMinmod = 1, kLimMC = 2, kLimWenoz = 3 };
-enum { kBcPeriodic = 0, kBcOutflow = 1 };
+// kBcHalo: the ghost cells of that side come from a caller-supplied halo buffer
+// (a subdomain boundary of a decomposed grid)
+enum { kBcPeriodic = 0, kBcOutflow = 1, kBcHalo = 2 };
 // cons->prim flags: density floor, pressure floor, and (FP32 only) the
 // pressure recomputed in FP64 because the FP32 value fell in the
 // cancellation-dominated range

@@ -59,7 +59,72 @@ struct StageParams {
   // constrained transport (kernels instantiated with CT = true)
   const T* bw[3];  // the stage input's face field: b_d on each cell's lower d-face
   T* ctf;          // kCtPlanes planes of ncell values (layout below)
+  // halo faces (kernels instantiated with HALO = true): ghost cells beyond a
+  // side whose bc is kBcHalo, per face x-, x+, y-, y+, z-, z+ (layout at
+  // halo_cell below)
+  const T* halo[6];
 };
+
+// HALO kernels: the address of variable 0 of cell (i, j, k) of the stage
+// input and the variable stride, for indices up to GH cells outside the grid
+// (GH = ghost width: 2 for PLM, 3 for WENO-Z).  A cell beyond a kBcHalo side
+// comes from that face's halo buffer, which has the grid's SoA layout over
+// the ghost slab: extent GH along the face normal (layer l = ghost index + GH
+// on the low side, ghost index - n on the high side), the grid's extents
+// along the two others.  Other out-of-range indices wrap (periodic) or clamp
+// (outflow) as in remap().  The stage kernels never use a cell outside the
+// grid along two axes at once, so when the chosen face's tangential indices
+// are out of range the load is of an unused value and is clamped into the
+// buffer; indices beyond n + GH - 1 (the unused part of a ragged tile) are
+// folded first.  Every load stays in bounds.
+template <int GH, class T>
+__device__ __forceinline__ const T* halo_cell(const StageParams<T>& p, int i, int j, int k,
+                                              long long& sv) {
+  const int n0 = p.n[0], n1 = p.n[1], n2 = p.n[2];
+  i = min(i, n0 + GH - 1);
+  j = min(j, n1 + GH - 1);
+  k = min(k, n2 + GH - 1);
+  int f = -1, l = 0;
+  if (k < 0 && p.bc_lo[2] == kBcHalo) {
+    f = 4;
+    l = k + GH;
+  } else if (k >= n2 && p.bc_hi[2] == kBcHalo) {
+    f = 5;
+    l = k - n2;
+  } else if (j < 0 && p.bc_lo[1] == kBcHalo) {
+    f = 2;
+    l = j + GH;
+  } else if (j >= n1 && p.bc_hi[1] == kBcHalo) {
+    f = 3;
+    l = j - n1;
+  } else if (i < 0 && p.bc_lo[0] == kBcHalo) {
+    f = 0;
+    l = i + GH;
+  } else if (i >= n0 && p.bc_hi[0] == kBcHalo) {
+    f = 1;
+    l = i - n0;
+  }
+  if (f < 0) {
+    auto wrap = [](int x, int n, int lo, int hi) {
+      if (x < 0) return lo == kBcPeriodic ? x + n : 0;
+      if (x >= n) return hi == kBcPeriodic ? x - n : n - 1;
+      return x;
+    };
+    const int gx = wrap(i, n0, p.bc_lo[0], p.bc_hi[0]);
+    const int gy = wrap(j, n1, p.bc_lo[1], p.bc_hi[1]);
+    const int gz = wrap(k, n2, p.bc_lo[2], p.bc_hi[2]);
+    sv = p.sv;
+    return p.win + (long long)gz * p.sz + (long long)gy * p.sy + gx;
+  }
+  const int d = f >> 1;
+  const int c0 = d == 0 ? l : min(max(i, 0), n0 - 1);
+  const int c1 = d == 1 ? l : min(max(j, 0), n1 - 1);
+  const int c2 = d == 2 ? l : min(max(k, 0), n2 - 1);
+  const int e0 = d == 0 ? GH : n0, e1 = d == 1 ? GH : n1;
+  const int e2 = d == 2 ? GH : n2;
+  sv = (long long)e0 * e1 * e2;
+  return p.halo[f] + ((long long)c2 * e1 + c1) * e0 + c0;
+}
 
 // Planes of the constrained-transport buffer written by a CT stage kernel,
 // per cell: the electric field E = -v x B on the cell's lower x, y and z
@@ -192,7 +257,8 @@ __device__ __forceinline__ void cell_slopes(const T* m, int sm, const T* c, int 
 // rho, m and E are updated (psi is written as 0; the magnetic field is left to
 // the face update), the face / cell electric fields go to p.ctf, and the last
 // stage has no damping and no wave-speed reduction (done after the face update).
-template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT = false>
+// HALO (3-D, not CT): ghost cells of kBcHalo sides from p.halo (halo_cell).
+template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT = false, bool HALO = false>
 __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepScalars& sc,
                                            int bx, int by, int bz, unsigned char* smem_raw,
                                            double* wmax) {
@@ -250,13 +316,20 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
   // cons -> prim of cell (r, c) of plane zz into dst (variables dst_stride
   // apart); own: an interior item of the tile (counted if the tile updates it)
   auto load_cell = [&](int zz, int r, int c, T* dst, int dst_stride, bool own) {
-    const int gz = ZACT ? remap(zz, nz, p.bc_lo[2], p.bc_hi[2]) : 0;
-    const int gx = remap(x0 + c, nx, p.bc_lo[0], p.bc_hi[0]);
-    const int gy = G::GY ? remap(y0 + r, ny, p.bc_lo[1], p.bc_hi[1]) : 0;
-    const long long off = (long long)gz * p.sz + (long long)gy * p.sy + gx;
     T u[kNV], v[kNV];
+    if constexpr (HALO) {
+      long long hs;
+      const T* a = halo_cell<2>(p, x0 + c, y0 + r, zz, hs);
 #pragma unroll
-    for (int k = 0; k < kNV; ++k) u[k] = p.win[k * p.sv + off];
+      for (int k = 0; k < kNV; ++k) u[k] = a[k * hs];
+    } else {
+      const int gz = ZACT ? remap(zz, nz, p.bc_lo[2], p.bc_hi[2]) : 0;
+      const int gx = remap(x0 + c, nx, p.bc_lo[0], p.bc_hi[0]);
+      const int gy = G::GY ? remap(y0 + r, ny, p.bc_lo[1], p.bc_hi[1]) : 0;
+      const long long off = (long long)gz * p.sz + (long long)gy * p.sy + gx;
+#pragma unroll
+      for (int k = 0; k < kNV; ++k) u[k] = p.win[k * p.sv + off];
+    }
     unsigned fl = 0;
     cons_to_prim(u, v, ph, fl);
     if (fl && own) count_floors(fl, zz, r, c);
@@ -295,6 +368,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
     return cur + r * TX + c;
   };
   static_assert(!CT || ZACT, "constrained transport is 3-D only");
+  static_assert(!HALO || (ZACT && !CT), "halo faces: 3-D GLM kernels only");
   // staggered normal field on the lower d-face of tile cell (r, c) of plane zz
   auto bface = [&](int d, int zz, int r, int c) -> T {
     const int gz = remap(zz, nz, p.bc_lo[2], p.bc_hi[2]);
@@ -539,13 +613,13 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
   __syncthreads();  // the CTA may start another tile on the same shared memory
 }
 
-template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT>
+template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT, bool HALO = false>
 __global__ void __launch_bounds__(NW * 32, 1) rk_stage_kernel(const StageParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double wmax[NW];
   const StepScalars sc = *p.sc;
-  stage_tile<T, TY, NW, STAGE, ZACT, CT>(p, sc, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw,
-                                         wmax);
+  stage_tile<T, TY, NW, STAGE, ZACT, CT, HALO>(p, sc, blockIdx.x, blockIdx.y, blockIdx.z,
+                                               smem_raw, wmax);
 }
 
 }  // namespace mhd

@@ -34,23 +34,23 @@ static cudaError_t set_smem_once(size_t smem) {
   return e;
 }
 
-template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT = false>
+template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT = false, bool HALO = false>
 static cudaError_t launch_one(const StageParams<T>& p, dim3 grid, cudaStream_t s) {
   using G = TileGeom<TY, ZACT>;
   const size_t smem = (size_t)G::WORDS * sizeof(T);
-  auto kern = rk_stage_kernel<T, TY, NW, STAGE, ZACT, CT>;
-  cudaError_t e = set_smem_once<rk_stage_kernel<T, TY, NW, STAGE, ZACT, CT>>(smem);
+  auto kern = rk_stage_kernel<T, TY, NW, STAGE, ZACT, CT, HALO>;
+  cudaError_t e = set_smem_once<rk_stage_kernel<T, TY, NW, STAGE, ZACT, CT, HALO>>(smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, NW * 32, smem, s>>>(p);
   return cudaGetLastError();
 }
 
-template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT = false>
+template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT = false, bool HALO = false>
 static cudaError_t launch_weno(const StageParams<T>& p, dim3 grid, cudaStream_t s) {
   using G = WenoGeom<TY, ZACT>;
   const size_t smem = (size_t)G::WORDS * sizeof(T);
-  auto kern = rk_stage_weno_kernel<T, TY, NW, STAGE, ZACT, CT>;
-  cudaError_t e = set_smem_once<rk_stage_weno_kernel<T, TY, NW, STAGE, ZACT, CT>>(smem);
+  auto kern = rk_stage_weno_kernel<T, TY, NW, STAGE, ZACT, CT, HALO>;
+  cudaError_t e = set_smem_once<rk_stage_weno_kernel<T, TY, NW, STAGE, ZACT, CT, HALO>>(smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, NW * 32, smem, s>>>(p);
   return cudaGetLastError();
@@ -138,13 +138,14 @@ cudaError_t prepare_stage_kernels(const Grid& g, bool ct) {
   return e;
 }
 
+// Kernel parameters shared by launch_stage and launch_stage_halo; returns
+// cudaErrorInvalidValue for a bad z range.
 template <class T>
-cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T* uout,
-                         const StepScalars* sc, unsigned long long* lam_bits,
-                         unsigned long long* floor_cnt, cudaStream_t stream, double a_n,
-                         double a_w, const T* const* bw, T* ctf, int zlo, int zhi, int tz,
-                         unsigned int* est_bits) {
-  StageParams<T> p;
+static cudaError_t stage_params(StageParams<T>& p, const Grid& g, const T* win,
+                                const T* un, T* uout, const StepScalars* sc,
+                                unsigned long long* lam_bits, unsigned long long* floor_cnt,
+                                double a_n, double a_w, int zlo, int zhi, int tz,
+                                unsigned int* est_bits) {
   p.a_n = T(a_n);
   p.a_w = T(a_w);
   p.win = win;
@@ -163,15 +164,31 @@ cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T*
   p.zlo = g.ndim == 3 ? zlo : 0;
   p.zhi = g.ndim == 3 && zhi >= 0 ? zhi : g.n[2];
   if (p.zlo < 0 || p.zhi > g.n[2] || p.zlo >= p.zhi) return cudaErrorInvalidValue;
-  const int nzc = (p.zhi - p.zlo + p.tz - 1) / p.tz;  // z chunks of this launch
   p.ph = make_phys<T>(g);
   p.sc = sc;
   p.lam_bits = lam_bits;
   p.est_bits = est_bits;
+  p.floor_cnt = floor_cnt;
+  for (int d = 0; d < 3; ++d) p.bw[d] = nullptr;
+  p.ctf = nullptr;
+  for (int f = 0; f < 6; ++f) p.halo[f] = nullptr;
+  return cudaSuccess;
+}
+
+template <class T>
+cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T* uout,
+                         const StepScalars* sc, unsigned long long* lam_bits,
+                         unsigned long long* floor_cnt, cudaStream_t stream, double a_n,
+                         double a_w, const T* const* bw, T* ctf, int zlo, int zhi, int tz,
+                         unsigned int* est_bits) {
+  StageParams<T> p;
+  cudaError_t pe = stage_params(p, g, win, un, uout, sc, lam_bits, floor_cnt, a_n, a_w, zlo,
+                                zhi, tz, est_bits);
+  if (pe != cudaSuccess) return pe;
+  const int nzc = (p.zhi - p.zlo + p.tz - 1) / p.tz;  // z chunks of this launch
   // the FP64 last stage publishes the maximum speed estimate (speed_exact
   // finishes the maximum); it needs the estimate word
   if (sizeof(T) == 8 && stage == 2 && !ctf && !est_bits) return cudaErrorInvalidValue;
-  p.floor_cnt = floor_cnt;
   for (int d = 0; d < 3; ++d) p.bw[d] = bw ? bw[d] : nullptr;
   p.ctf = ctf;
   if (ctf) {
@@ -224,6 +241,60 @@ cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T*
   if (stage == 1) return launch_one<T, 1, 1, 1, false>(p, grid, stream);
   if (stage == 2) return launch_one<T, 1, 1, 2, false>(p, grid, stream);
   return launch_one<T, 1, 1, 3, false>(p, grid, stream);
+}
+
+// Halo faces (3-D GLM grids with kBcHalo sides): the HALO variants of the
+// 3-D stage kernels, the ghost cells of those sides read from halo[f].
+// Instantiated in mhd_stage_halo_f64.cu / _f32.cu only.
+template <class T>
+cudaError_t launch_stage_halo(const Grid& g, int stage, const T* win, const T* un, T* uout,
+                              const StepScalars* sc, unsigned long long* lam_bits,
+                              unsigned long long* floor_cnt, cudaStream_t stream, double a_n,
+                              double a_w, const T* const* halo, unsigned int* est_bits) {
+  if (g.ndim != 3 || !halo) return cudaErrorInvalidValue;
+  StageParams<T> p;
+  cudaError_t pe = stage_params(p, g, win, un, uout, sc, lam_bits, floor_cnt, a_n, a_w, 0, -1,
+                                0, est_bits);
+  if (pe != cudaSuccess) return pe;
+  if (sizeof(T) == 8 && stage == 2 && !est_bits) return cudaErrorInvalidValue;
+  for (int f = 0; f < 6; ++f) {
+    const bool lo = (f & 1) == 0;
+    const int bc = lo ? g.bc_lo[f >> 1] : g.bc_hi[f >> 1];
+    if (bc == kBcHalo && !halo[f]) return cudaErrorInvalidValue;
+    p.halo[f] = bc == kBcHalo ? halo[f] : nullptr;
+  }
+  const int nzc = (p.zhi - p.zlo + p.tz - 1) / p.tz;
+  if (g.limiter == kLimWenoz) {
+    dim3 grid((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, nzc);
+    if (stage == 1) return launch_weno<T, 4, 8, 1, true, false, true>(p, grid, stream);
+    if (stage == 2) return launch_weno<T, 4, 8, 2, true, false, true>(p, grid, stream);
+    return launch_weno<T, 4, 8, 3, true, false, true>(p, grid, stream);
+  }
+  using S = StageShape3D<T>;
+  dim3 grid((g.n[0] + 31) / 32, (g.n[1] + S::TY - 1) / S::TY, nzc);
+  if (stage == 1) return launch_one<T, S::TY, S::NW, 1, true, false, true>(p, grid, stream);
+  if (stage == 2) return launch_one<T, S::TY, S::NW, 2, true, false, true>(p, grid, stream);
+  return launch_one<T, S::TY, S::NW, 3, true, false, true>(p, grid, stream);
+}
+
+// The shared-memory limits of the HALO variants (set once, outside any capture).
+template <class T>
+cudaError_t prepare_stage_kernels_halo(const Grid& g) {
+  cudaError_t e = cudaSuccess;
+  using S = StageShape3D<T>;
+  using W3 = WenoGeom<4, true>;
+  using P3 = TileGeom<S::TY, true>;
+  const size_t sw = (size_t)W3::WORDS * sizeof(T), sp = (size_t)P3::WORDS * sizeof(T);
+  if (g.limiter == kLimWenoz) {
+    if (e == cudaSuccess) e = set_smem_once<rk_stage_weno_kernel<T, 4, 8, 1, true, false, true>>(sw);
+    if (e == cudaSuccess) e = set_smem_once<rk_stage_weno_kernel<T, 4, 8, 2, true, false, true>>(sw);
+    if (e == cudaSuccess) e = set_smem_once<rk_stage_weno_kernel<T, 4, 8, 3, true, false, true>>(sw);
+  } else {
+    if (e == cudaSuccess) e = set_smem_once<rk_stage_kernel<T, S::TY, S::NW, 1, true, false, true>>(sp);
+    if (e == cudaSuccess) e = set_smem_once<rk_stage_kernel<T, S::TY, S::NW, 2, true, false, true>>(sp);
+    if (e == cudaSuccess) e = set_smem_once<rk_stage_kernel<T, S::TY, S::NW, 3, true, false, true>>(sp);
+  }
+  return e;
 }
 
 }  // namespace mhd

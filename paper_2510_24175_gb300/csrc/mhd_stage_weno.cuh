@@ -128,8 +128,8 @@ struct WenoGeom {
   static constexpr int ITEMS = IT_X + IT_Y + IT_XE;
 };
 
-// CT: constrained transport, as in stage_tile() (mhd_stage.cuh).
-template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT>
+// CT: constrained transport, HALO: halo faces, as in stage_tile() (mhd_stage.cuh).
+template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT, bool HALO = false>
 __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StageParams<T> p) {
   using G = WenoGeom<TY, ZACT>;
   constexpr int NT = NW * 32;
@@ -183,13 +183,20 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
     if (fl & kPressF64) atomicAdd(&p.floor_cnt[2], 1ull);
   };
   auto load_cell = [&](int zz, int r, int c, T* dst, int dst_stride, bool own) {
-    const int gz = ZACT ? remap3(zz, nz, p.bc_lo[2], p.bc_hi[2]) : 0;
-    const int gx = remap3(x0 + c, nx, p.bc_lo[0], p.bc_hi[0]);
-    const int gy = G::GY ? remap3(y0 + r, ny, p.bc_lo[1], p.bc_hi[1]) : 0;
-    const long long off = (long long)gz * p.sz + (long long)gy * p.sy + gx;
     T u[kNV], v[kNV];
+    if constexpr (HALO) {
+      long long hs;
+      const T* a = halo_cell<3>(p, x0 + c, y0 + r, zz, hs);
 #pragma unroll
-    for (int k = 0; k < kNV; ++k) u[k] = p.win[k * p.sv + off];
+      for (int k = 0; k < kNV; ++k) u[k] = a[k * hs];
+    } else {
+      const int gz = ZACT ? remap3(zz, nz, p.bc_lo[2], p.bc_hi[2]) : 0;
+      const int gx = remap3(x0 + c, nx, p.bc_lo[0], p.bc_hi[0]);
+      const int gy = G::GY ? remap3(y0 + r, ny, p.bc_lo[1], p.bc_hi[1]) : 0;
+      const long long off = (long long)gz * p.sz + (long long)gy * p.sy + gx;
+#pragma unroll
+      for (int k = 0; k < kNV; ++k) u[k] = p.win[k * p.sv + off];
+    }
     unsigned fl = 0;
     cons_to_prim(u, v, ph, fl);
     if (fl && own) count_floors(fl, zz, r, c);
@@ -225,6 +232,7 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
     return cur + r * TX + c;
   };
   static_assert(!CT || ZACT, "constrained transport is 3-D only");
+  static_assert(!HALO || (ZACT && !CT), "halo faces: 3-D GLM kernels only");
   // staggered normal field on the lower d-face of tile cell (r, c) of plane zz
   auto bface = [&](int d, int zz, int r, int c) -> T {
     const int gz = remap3(zz, nz, p.bc_lo[2], p.bc_hi[2]);
