@@ -97,6 +97,10 @@ typedef struct mhd_config {
   int rk_order;          /* 2: RK2 (default); 3: SSP-RK3 of Shu & Osher,
                             the time integrator of the paper's runs          */
   int divb;              /* MHD_DIVB_GLM (default) or MHD_DIVB_CT             */
+  double dx[3];          /* > 0: the cell size of dimension d as given (a block
+                            of a decomposed grid passes the whole grid's, so
+                            its steps round as the whole grid's do); 0 (the
+                            default): (xmax_d - xmin_d) / n_d                 */
 } mhd_config;
 
 typedef struct mhd_ctx mhd_ctx;

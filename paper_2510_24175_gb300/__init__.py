@@ -60,7 +60,8 @@ class mhd_config(ctypes.Structure):
                 ("rho_floor", ctypes.c_double), ("p_floor", ctypes.c_double),
                 ("t_end", ctypes.c_double), ("limiter", ctypes.c_int),
                 ("bc", ctypes.c_int * 6), ("precision", ctypes.c_int), ("flags", ctypes.c_int),
-                ("rk_order", ctypes.c_int), ("divb", ctypes.c_int)]
+                ("rk_order", ctypes.c_int), ("divb", ctypes.c_int),
+                ("dx", ctypes.c_double * 3)]
 
 
 _lib = None
@@ -320,6 +321,7 @@ class Config:
     flags: int = 0
     rk_order: int = 2
     divb: int = MHD_DIVB_GLM
+    dx: tuple = (0.0, 0.0, 0.0)  # > 0: the cell size as given (mhd_config.dx)
 
     @classmethod
     def from_problem(cls, pb, precision=None, flags: int = 0) -> "Config":
@@ -342,6 +344,8 @@ class Config:
         c.divb = int(self.divb)
         for s in range(6):
             c.bc[s] = int(self.bc[s])
+        for d in range(3):
+            c.dx[d] = float(self.dx[d])
         return c
 
 

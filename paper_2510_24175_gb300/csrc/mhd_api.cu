@@ -88,6 +88,10 @@ static int validate(const mhd_config* c, char* msg, size_t len) {
       snprintf(msg, len, "empty domain in dimension %d", d);
       return MHD_ERR_INVALID;
     }
+    if (!(c->dx[d] >= 0.0) || !(c->dx[d] < INFINITY)) {
+      snprintf(msg, len, "bad cell size dx[%d] (0: derived from the domain, else > 0)", d);
+      return MHD_ERR_INVALID;
+    }
   }
   if (c->n[0] < 2) {
     snprintf(msg, len, "x must be active (nx >= 2)");
@@ -182,7 +186,7 @@ static void fill_grid(const mhd_config* c, mhd::Grid* g) {
   for (int d = 0; d < 3; ++d) {
     g->n[d] = c->n[d];
     g->ncell *= c->n[d];
-    g->dx[d] = (c->xmax[d] - c->xmin[d]) / c->n[d];
+    g->dx[d] = c->dx[d] > 0.0 ? c->dx[d] : (c->xmax[d] - c->xmin[d]) / c->n[d];
     g->bc_lo[d] = c->bc[2 * d];
     g->bc_hi[d] = c->bc[2 * d + 1];
     if (c->n[d] > 1) g->ndim++;

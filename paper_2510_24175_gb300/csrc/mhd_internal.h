@@ -124,12 +124,16 @@ cudaError_t launch_f32_to_f64(const float* in, double* out, long long n, cudaStr
 
 // Stage kernels with halo faces (mhd_stage_halo_f64.cu / _f32.cu): as
 // launch_stage for a 3-D GLM grid, the ghost cells of every kBcHalo side read
-// from halo[f] (f = 2 d + side; layout at halo_cell in mhd_stage.cuh).
+// from halo[f] (f = 2 d + side; layout at halo_cell in mhd_stage.cuh; halo
+// may be null when no side is kBcHalo).  FP64 3-D GLM grids always run these
+// kernels (launch_stage forwards), so that a grid and the blocks of its
+// decomposition execute the same code and agree bit for bit.
 template <class T>
 cudaError_t launch_stage_halo(const Grid& g, int stage, const T* win, const T* un, T* uout,
                               const StepScalars* sc, unsigned long long* lam_bits,
                               unsigned long long* floor_cnt, cudaStream_t stream, double a_n,
-                              double a_w, const T* const* halo, unsigned int* est_bits);
+                              double a_w, const T* const* halo, unsigned int* est_bits,
+                              int zlo = 0, int zhi = -1, int tz = 0);
 template <class T>
 cudaError_t prepare_stage_kernels_halo(const Grid& g);
 

@@ -50,7 +50,7 @@ extern "C" int mhd_conserved_sums_noalloc(const mhd_config* cfg, const void* U, 
   long long ncell = 1;
   for (int d = 0; d < 3; ++d) {
     g.n[d] = cfg->n[d];
-    g.dx[d] = (cfg->xmax[d] - cfg->xmin[d]) / cfg->n[d];
+    g.dx[d] = cfg->dx[d] > 0.0 ? cfg->dx[d] : (cfg->xmax[d] - cfg->xmin[d]) / cfg->n[d];
     ncell *= cfg->n[d];
   }
   g.ncell = ncell;

@@ -63,6 +63,34 @@ MHD_HD float rcp(float x) {
   return 1.0f / x;
 #endif
 }
+// A product and a fused multiply-add whose rounding the source fixes.  In a
+// sum of two products the compiler may fuse either product into the add, and
+// copies of the same code inlined at different sites (or kernels that differ
+// only elsewhere) may then round differently; the sums whose results must
+// not depend on where the code runs are written with these (the same number
+// of instructions as the contracted form).
+MHD_HD double mul_rn(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+MHD_HD float mul_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+MHD_HD double fma_rn(double a, double b, double c) { return fma(a, b, c); }
+MHD_HD float fma_rn(float a, float b, float c) { return fmaf(a, b, c); }
+// a0 b0 + a1 b1 + a2 b2, rounded as fma(a2, b2, fma(a1, b1, a0 b0))
+template <class T>
+MHD_HD T dot3_rn(T a0, T b0, T a1, T b1, T a2, T b2) {
+  return fma_rn(a2, b2, fma_rn(a1, b1, mul_rn(a0, b0)));
+}
+
 MHD_HD double trsqrt(double x) { return rsqrt(x); }
 MHD_HD float trsqrt(float x) { return rsqrtf(x); }
 MHD_HD double tsqrt(double x) { return sqrt(x); }
@@ -231,8 +259,8 @@ MHD_HD void cons_to_prim(const T u[kNV], T v[kNV], const Phys<T>& ph,
   }
   const T ri = rcp(rho);
   const T vx = u[kVX] * ri, vy = u[kVY] * ri, vz = u[kVZ] * ri;
-  const T kin = T(0.5) * (u[kVX] * vx + u[kVY] * vy + u[kVZ] * vz);
-  const T b2 = u[kBX] * u[kBX] + u[kBY] * u[kBY] + u[kBZ] * u[kBZ];
+  const T kin = T(0.5) * dot3_rn(u[kVX], vx, u[kVY], vy, u[kVZ], vz);
+  const T b2 = dot3_rn(u[kBX], u[kBX], u[kBY], u[kBY], u[kBZ], u[kBZ]);
   T p = ph.gm1 * (u[kPRS] - kin - T(0.5) * b2);
   p = pressure_floor(p, u, rho, ph, flags);
   v[kRHO] = rho;
@@ -282,9 +310,9 @@ MHD_HD float half_of(float x) { return 0.5f * x; }
 // c_f^2 = (a + sqrt(a^2 - 4 g c_an^2)) / 2.
 template <class T>
 MHD_HD T fast_speed2(T rho_i, T gp, T b2, T bn2) {
-  const T g = gp * rho_i;
-  const T a = b2 * rho_i + g;
-  const T disc = pos_part(a * a + neg4(g * (bn2 * rho_i)));
+  const T g = mul_rn(gp, rho_i);
+  const T a = fma_rn(b2, rho_i, g);
+  const T disc = pos_part(fma_rn(a, a, neg4(g * (bn2 * rho_i))));
   return half_of(a + tsqrt(disc));
 }
 
@@ -302,7 +330,7 @@ MHD_HD T cell_max_speed(const T u[kNV], const Phys<T>& ph, int ndim,
   cons_to_prim(u, v, ph, flags);
   const T ri = rcp(v[kRHO]);
   const T gp = ph.gamma * v[kPRS];
-  const T b2 = v[kBX] * v[kBX] + v[kBY] * v[kBY] + v[kBZ] * v[kBZ];
+  const T b2 = dot3_rn(v[kBX], v[kBX], v[kBY], v[kBY], v[kBZ], v[kBZ]);
   T lam = tabs(v[kVX]) + fast_speed(ri, gp, b2, v[kBX] * v[kBX]);
   if (ndim > 1) lam = nan_max(lam, tabs(v[kVY]) + fast_speed(ri, gp, b2, v[kBY] * v[kBY]));
   if (ndim > 2) lam = nan_max(lam, tabs(v[kVZ]) + fast_speed(ri, gp, b2, v[kBZ] * v[kBZ]));
@@ -505,7 +533,10 @@ MHD_HD T rot3(int dir, int j, T a, T b, T c) {
 
 // GLM interface step + HLLD along direction dir (0, 1, 2; template
 // argument) for primitive face states vl, vr.  ch: cleaning speed;
-// half_chi = 0.5 / ch.  F in conservative ordering.
+// half_chi = 0.5 / ch.  F in conservative ordering.  Every sum of products
+// is written with mul_rn / fma_rn / dot3_rn, so the flux rounds the same in
+// every kernel and at every call site it is inlined into (the results of
+// decomposed and undecomposed runs must agree bit for bit).
 template <int dir, class T>
 MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
                           const Phys<T>& ph, T F[kNV]) {
@@ -526,16 +557,18 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
   const T rL = vl[kRHO], pL = vl[kPRS], rR = vr[kRHO], pR = vr[kPRS];
 
   // GLM: exact solution of the linear (B_n, psi) interface problem
-  const T bx = half * (bnL + bnR) - half_chi * (vr[kPSI] - vl[kPSI]);
-  const T psis = half * (vl[kPSI] + vr[kPSI]) - half * ch * (bnR - bnL);
+  const T bx = fma_rn(half, bnL + bnR, -mul_rn(half_chi, vr[kPSI] - vl[kPSI]));
+  const T psis = fma_rn(half, vl[kPSI] + vr[kPSI], -mul_rn(half * ch, bnR - bnL));
   const T bx2 = bx * bx;
 
   // outer states
-  const T b2L = bx2 + byL * byL + bzL * bzL;
-  const T b2R = bx2 + byR * byR + bzR * bzR;
-  const T ptL = pL + half * b2L, ptR = pR + half * b2R;
-  const T eL = pL * ph.gm1i + half * rL * (uL * uL + vL * vL + wL * wL) + half * b2L;
-  const T eR = pR * ph.gm1i + half * rR * (uR * uR + vR * vR + wR * wR) + half * b2R;
+  const T b2L = fma_rn(bzL, bzL, fma_rn(byL, byL, bx2));
+  const T b2R = fma_rn(bzR, bzR, fma_rn(byR, byR, bx2));
+  const T ptL = fma_rn(half, b2L, pL), ptR = fma_rn(half, b2R, pR);
+  const T eL = fma_rn(half, b2L,
+                      fma_rn(half * rL, dot3_rn(uL, uL, vL, vL, wL, wL), mul_rn(pL, ph.gm1i)));
+  const T eR = fma_rn(half, b2R,
+                      fma_rn(half * rR, dot3_rn(uR, uR, vR, vR, wR, wR), mul_rn(pR, ph.gm1i)));
   // 1/rho of both sides from one reciprocal; only max(c_fL, c_fR) is used,
   // so one square root of max(c_fL^2, c_fR^2) (sqrt is monotone and
   // correctly rounded: the same value)
@@ -549,14 +582,14 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
   const T SR = tmax2(uL, uR) + cmax;
   const T dL = (SL - uL) * rL, dR = (SR - uR) * rR;
   const T Di = rcp(dR - dL);
-  const T SM = (dR * uR - dL * uL - ptR + ptL) * Di;
-  const T pts = (dR * ptL - dL * ptR + dL * dR * (uR - uL)) * Di;
+  const T SM = (fma_rn(dR, uR, -mul_rn(dL, uL)) - ptR + ptL) * Di;
+  const T pts = fma_rn(mul_rn(dL, dR), uR - uL, fma_rn(dR, ptL, -mul_rn(dL, ptR))) * Di;
 
   // single-star states (MK05 Eqs. 43-48), degenerate when
   // |rho (S-u)(S-S_M) - Bx^2| < 1e-8 p_t*; paired reciprocals of S-S_M and
   // of the two denominators
   const T smL = SL - SM, smR = SR - SM;
-  const T denL = dL * smL - bx2, denR = dR * smR - bx2;
+  const T denL = fma_rn(dL, smL, -bx2), denR = fma_rn(dR, smR, -bx2);
   const bool degL = abs_lt(denL, T(1e-8) * pts);
   const bool degR = abs_lt(denR, T(1e-8) * pts);
   const T dnL = degL ? T(1) : denL, dnR = degR ? T(1) : denR;
@@ -570,26 +603,30 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
   {
     rsL = dL * smiL;
     const T fv = bx * (SM - uL) * deniL;
-    const T fb = (dL * (SL - uL) - bx2) * deniL;
-    vsL = degL ? vL : vL - byL * fv;
-    wsL = degL ? wL : wL - bzL * fv;
+    const T fb = fma_rn(dL, SL - uL, -bx2) * deniL;
+    vsL = degL ? vL : fma_rn(-byL, fv, vL);
+    wsL = degL ? wL : fma_rn(-bzL, fv, wL);
     bysL = degL ? byL : byL * fb;
     bzsL = degL ? bzL : bzL * fb;
-    const T vb = uL * bx + vL * byL + wL * bzL;
-    vbsL = SM * bx + vsL * bysL + wsL * bzsL;
-    esL = ((SL - uL) * eL - ptL * uL + pts * SM + bx * (vb - vbsL)) * smiL;
+    const T vb = dot3_rn(uL, bx, vL, byL, wL, bzL);
+    vbsL = dot3_rn(SM, bx, vsL, bysL, wsL, bzsL);
+    esL = fma_rn(bx, vb - vbsL,
+                   fma_rn(pts, SM, fma_rn(SL - uL, eL, -mul_rn(ptL, uL)))) *
+          smiL;
   }
   {
     rsR = dR * smiR;
     const T fv = bx * (SM - uR) * deniR;
-    const T fb = (dR * (SR - uR) - bx2) * deniR;
-    vsR = degR ? vR : vR - byR * fv;
-    wsR = degR ? wR : wR - bzR * fv;
+    const T fb = fma_rn(dR, SR - uR, -bx2) * deniR;
+    vsR = degR ? vR : fma_rn(-byR, fv, vR);
+    wsR = degR ? wR : fma_rn(-bzR, fv, wR);
     bysR = degR ? byR : byR * fb;
     bzsR = degR ? bzR : bzR * fb;
-    const T vb = uR * bx + vR * byR + wR * bzR;
-    vbsR = SM * bx + vsR * bysR + wsR * bzsR;
-    esR = ((SR - uR) * eR - ptR * uR + pts * SM + bx * (vb - vbsR)) * smiR;
+    const T vb = dot3_rn(uR, bx, vR, byR, wR, bzR);
+    vbsR = dot3_rn(SM, bx, vsR, bysR, wsR, bzsR);
+    esR = fma_rn(bx, vb - vbsR,
+                   fma_rn(pts, SM, fma_rn(SR - uR, eR, -mul_rn(ptR, uR)))) *
+          smiR;
   }
 
   // Fan region: side a = L if (S_L > 0) or (S_R >= 0 and S_M >= 0), else R
@@ -609,14 +646,15 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
   const T c1 = sup ? T(0) : (useL ? SL : SR);
   T f[7];
   {
-    const T vb = u * bx + v * by + w * bz;
-    f[0] = r * u + c1 * (rs - r);
-    f[1] = r * u * u + pt - bx2 + c1 * (rs * SM - r * u);
-    f[2] = r * v * u - bx * by + c1 * (rs * vs - r * v);
-    f[3] = r * w * u - bx * bz + c1 * (rs * ws - r * w);
-    f[4] = by * u - bx * v + c1 * (bys - by);
-    f[5] = bz * u - bx * w + c1 * (bzs - bz);
-    f[6] = (e + pt) * u - bx * vb + c1 * (es - e);
+    const T vb = dot3_rn(u, bx, v, by, w, bz);
+    const T ru = mul_rn(r, u), rv = mul_rn(r, v), rw = mul_rn(r, w);
+    f[0] = fma_rn(c1, rs - r, ru);
+    f[1] = fma_rn(c1, fma_rn(rs, SM, -ru), fma_rn(ru, u, pt) - bx2);
+    f[2] = fma_rn(c1, fma_rn(rs, vs, -rv), fma_rn(rv, u, -mul_rn(bx, by)));
+    f[3] = fma_rn(c1, fma_rn(rs, ws, -rw), fma_rn(rw, u, -mul_rn(bx, bz)));
+    f[4] = fma_rn(c1, bys - by, fma_rn(by, u, -mul_rn(bx, v)));
+    f[5] = fma_rn(c1, bzs - bz, fma_rn(bz, u, -mul_rn(bx, w)));
+    f[6] = fma_rn(c1, es - e, fma_rn(e + pt, u, -mul_rn(bx, vb)));
   }
 
   // Alfven waves (MK05 Eq. 51) and double-star states (Eqs. 59-63);
@@ -624,27 +662,29 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
   const T iqL = trsqrt(rsL), iqR = trsqrt(rsR);
   const T sqL = rsL * iqL, sqR = rsR * iqR;
   const T abx = tabs(bx);
-  const T SLs = SM - abx * iqL;
-  const T SRs = SM + abx * iqR;
+  const T SLs = fma_rn(-abx, iqL, SM);
+  const T SRs = fma_rn(abx, iqR, SM);
   const T sg = ge0(bx) ? T(1) : T(-1);
   const T isum = rcp(sqL + sqR);
-  const T vss = (sqL * vsL + sqR * vsR + (bysR - bysL) * sg) * isum;
-  const T wss = (sqL * wsL + sqR * wsR + (bzsR - bzsL) * sg) * isum;
-  const T byss = (sqL * bysR + sqR * bysL + sqL * sqR * (vsR - vsL) * sg) * isum;
-  const T bzss = (sqL * bzsR + sqR * bzsL + sqL * sqR * (wsR - wsL) * sg) * isum;
-  const T vbss = SM * bx + vss * byss + wss * bzss;
+  const T sqLR = mul_rn(sqL, sqR);
+  const T vss = (fma_rn(sqR, vsR, mul_rn(sqL, vsL)) + (bysR - bysL) * sg) * isum;
+  const T wss = (fma_rn(sqR, wsR, mul_rn(sqL, wsL)) + (bzsR - bzsL) * sg) * isum;
+  const T byss = fma_rn(sqLR, (vsR - vsL) * sg, fma_rn(sqR, bysL, mul_rn(sqL, bysR))) * isum;
+  const T bzss = fma_rn(sqLR, (wsR - wsL) * sg, fma_rn(sqR, bzsL, mul_rn(sqL, bzsR))) * isum;
+  const T vbss = dot3_rn(SM, bx, vss, byss, wss, bzss);
 
   // F = F_a + c1 (U*_a - U_a) + c2 (U**_a - U*_a) with c1 = S_a unless the
   // interface is supersonic, c2 = S*_a inside the Alfven fan.
   const bool inner = !sup && (useL ? !gt0(SLs) : !lt0(SRs));
   const T sq = useL ? -sqL : sqR;
-  const T ess = es + sq * (vbs - vbss) * sg;
+  const T ess = fma_rn(sq, (vbs - vbss) * sg, es);
   const T c2 = inner ? (useL ? SLs : SRs) : T(0);
-  f[2] = f[2] + c2 * rs * (vss - vs);
-  f[3] = f[3] + c2 * rs * (wss - ws);
-  f[4] = f[4] + c2 * (byss - bys);
-  f[5] = f[5] + c2 * (bzss - bzs);
-  f[6] = f[6] + c2 * (ess - es);
+  const T c2rs = mul_rn(c2, rs);
+  f[2] = fma_rn(c2rs, vss - vs, f[2]);
+  f[3] = fma_rn(c2rs, wss - ws, f[3]);
+  f[4] = fma_rn(c2, byss - bys, f[4]);
+  f[5] = fma_rn(c2, bzss - bzs, f[5]);
+  f[6] = fma_rn(c2, ess - es, f[6]);
 
   F[kRHO] = f[0];
   F[kPRS] = f[6];

@@ -378,58 +378,34 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
   };
   CtCell<T> ctc;
 
-  if constexpr (ZACT) {
-    // prologue: z face state of cell z0-1 and z flux at face z0-1/2
-    for (int it = tid; it < 3 * G::NINT; it += NT) {
-      const int pl = it / G::NINT, j = it - pl * G::NINT;
-      load_item(j, z0 - 2 + pl, 0);
-    }
-    __syncthreads();
-    T Pprev[kNV];
-    if (owner) {
-      T sig[kNV];
-      const T* c = ring_plane(z0 - 1) + oidx;
-      cell_slopes(ring_plane(z0 - 2) + oidx, G::NINT, c, G::NINT, ring_plane(z0) + oidx,
-                  G::NINT, lim, sig);
-#pragma unroll
-      for (int k = 0; k < kNV; ++k) Pprev[k] = c[k * G::NINT] + T(0.5) * sig[k];
-    }
-    __syncthreads();
-    for (int it = tid; it < G::NINT; it += NT) load_item(it, z0 + 1, 0);
-    __syncthreads();
-    if (owner) {
-      T sig[kNV], M[kNV], F[kNV];
-      const T* c = ring_plane(z0) + oidx;
-      cell_slopes(ring_plane(z0 - 1) + oidx, G::NINT, c, G::NINT, ring_plane(z0 + 1) + oidx,
-                  G::NINT, lim, sig);
-#pragma unroll
-      for (int k = 0; k < kNV; ++k) {
-        const T v = c[k * G::NINT];
-        M[k] = v - T(0.5) * sig[k];
-        zP[k * G::NINT + oidx] = v + T(0.5) * sig[k];
-      }
-      if constexpr (CT) ct_face_field(Pprev, M, 2, bface(2, z0, orow, ocol));
-      glm_hlld_flux<2>(Pprev, M, ch, half_chi, ph, F);
-#pragma unroll
-      for (int k = 0; k < kNV; ++k) zF[k * G::NINT + oidx] = F[k];
-    }
-    __syncthreads();
-  }
-
+  // The z march: one loop body for every plane, so that each cell's
+  // conversion, slopes and z fluxes come from the same code wherever a z
+  // chunk (or a block of a decomposed grid, or a launch's z range) starts --
+  // a cell's result must not depend on that decomposition.  Iterations
+  // k < z0 warm up: k = z0-4 and z0-3 only load planes z0-2 and z0-1 into the
+  // ring, k = z0-2 sets the column owners' face state of cell z0-1, k = z0-1
+  // their flux through face z0-1/2; the x, y work and the update start at
+  // k = z0.  (Unrolling, and with it the peeling of warm-up iterations into
+  // separate copies, is disabled.)
+  constexpr int NWARM = ZACT ? 4 : 0;
   SpeedMax<T> smax(ph);  // last stage: the new state's maximum wave speed
-  for (int k = z0; k < z1; ++k) {
+#pragma unroll 1
+  for (int k = z0 - NWARM; k < z1; ++k) {
+    const bool main = k >= z0;
     // ---- A: loads ---------------------------------------------------------
-    for (int it = tid; it < G::NLOAD; it += NT) {
+    const int nload = main ? G::NLOAD : G::NINT;
+    for (int it = tid; it < nload; it += NT) {
       if (ZACT && it < G::NINT)
         load_item(it, k + 2, k);
       else
         load_item(it, k, k);
     }
     __syncthreads();
+    if (ZACT && k < z0 - 2) continue;
     const T* cur = ring_plane(k);
 
     // ---- B: slopes --------------------------------------------------------
-    for (int it = tid; it < G::SXN + G::SYN; it += NT) {
+    for (int it = tid; main && it < G::SXN + G::SYN; it += NT) {
       T sig[kNV];
       T* dst;
       int ds;
@@ -465,7 +441,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
     __syncthreads();
 
     // ---- C: fluxes --------------------------------------------------------
-    for (int it = tid; it < G::ITEMS; it += NT) {
+    for (int it = tid; main && it < G::ITEMS; it += NT) {
       T vl[kNV], vr[kNV], F[kNV];
       int dir;
       T* out;
@@ -536,19 +512,23 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
           ctc.fz_by = zF[kBY * G::NINT + oidx];
           ctc.fz_rho = zF[kRHO * G::NINT + oidx];
         }
-        glm_hlld_flux<2>(vl, vr, ch, half_chi, ph, F);
+        if (k >= z0 - 1) {  // from k = z0-1 on, zP holds the face state of cell k
+          glm_hlld_flux<2>(vl, vr, ch, half_chi, ph, F);
 #pragma unroll
-        for (int q = 0; q < kNV; ++q) {
-          dUz[q] = (F[q] - zF[q * G::NINT + oidx]) * dtdz;
-          zF[q * G::NINT + oidx] = F[q];
-          zP[q * G::NINT + oidx] = c[q * G::NINT] + T(0.5) * zS[q * G::NINT + oidx];
+          for (int q = 0; q < kNV; ++q) {
+            dUz[q] = mul_rn(F[q] - zF[q * G::NINT + oidx], dtdz);
+            zF[q * G::NINT + oidx] = F[q];
+          }
         }
+#pragma unroll
+        for (int q = 0; q < kNV; ++q)
+          zP[q * G::NINT + oidx] = c[q * G::NINT] + T(0.5) * zS[q * G::NINT + oidx];
       }
     }
     __syncthreads();
 
     // ---- D: right-hand side and RK combination (column owners) -------------
-    if (owner) {
+    if (main && owner) {
       const int gx = x0 + ocol, gy = y0 + orow;
       const bool valid = gx < nx && gy < ny;
       T unew[kNV];
@@ -559,10 +539,12 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
 #pragma unroll
         for (int q = 0; q < kNV; ++q) {
           const T* fx = Fx + q * G::FXN + orow * (TX + 1) + ocol;
-          T du = (fx[1] - fx[0]) * dtdx;
+          // sums of products with their rounding fixed (mul_rn / fma_rn), so
+          // every instantiation of this tile code gives the same bits
+          T du = mul_rn(fx[1] - fx[0], dtdx);
           if constexpr (G::GY > 0) {
             const T* fy = Fy + q * G::FYN + orow * TX + ocol;
-            du += (fy[TX] - fy[0]) * dtdy;
+            du = fma_rn(fy[TX] - fy[0], dtdy, du);
           }
           if constexpr (ZACT) du += dUz[q];
           if (frozen) du = T(0);
@@ -570,7 +552,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
           if constexpr (STAGE == 1) {
             unew[q] = s1;
           } else {
-            unew[q] = p.a_n * p.un[q * p.sv + off] + p.a_w * s1;
+            unew[q] = fma_rn(p.a_n, p.un[q * p.sv + off], mul_rn(p.a_w, s1));
           }
         }
         if constexpr (CT) {

@@ -5,6 +5,7 @@ namespace mhd {
 template cudaError_t launch_stage_halo<double>(const Grid&, int, const double*, const double*, double*,
                                            const StepScalars*, unsigned long long*,
                                            unsigned long long*, cudaStream_t, double, double,
-                                           const double* const*, unsigned int*);
+                                           const double* const*, unsigned int*, int, int,
+                                           int);
 template cudaError_t prepare_stage_kernels_halo<double>(const Grid&);
 }  // namespace mhd

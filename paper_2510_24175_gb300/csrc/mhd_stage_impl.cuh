@@ -118,16 +118,22 @@ cudaError_t prepare_stage_kernels(const Grid& g, bool ct) {
     } else {
       MHD_SET3(rk_stage_kernel, P3, S::TY, S::NW, true, true);
     }
+  } else if (sizeof(T) == 8 && g.ndim == 3) {
+    e = prepare_stage_kernels_halo<T>(g);  // FP64 3-D GLM: the halo-capable kernels
   } else if (g.limiter == kLimWenoz) {
     if (g.ndim == 3) {
-      MHD_SET3(rk_stage_weno_kernel, W3, 4, 8, true, false);
+      if constexpr (sizeof(T) == 4) {
+        MHD_SET3(rk_stage_weno_kernel, W3, 4, 8, true, false);
+      }
     } else if (g.ndim == 2) {
       MHD_SET3(rk_stage_weno_kernel, W2, 4, 8, false, false);
     } else {
       MHD_SET3(rk_stage_weno_kernel, W1, 1, 1, false, false);
     }
   } else if (g.ndim == 3) {
-    MHD_SET3(rk_stage_kernel, P3, S::TY, S::NW, true, false);
+    if constexpr (sizeof(T) == 4) {
+      MHD_SET3(rk_stage_kernel, P3, S::TY, S::NW, true, false);
+    }
   } else if (g.ndim == 2) {
     MHD_SET3(rk_stage_kernel, P2, 8, 8, false, false);
   } else {
@@ -206,12 +212,21 @@ cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T*
     if (stage == 2) return launch_one<T, S::TY, S::NW, 2, true, true>(p, grid, stream);
     return launch_one<T, S::TY, S::NW, 3, true, true>(p, grid, stream);
   }
+  if constexpr (sizeof(T) == 8) {
+    // FP64 3-D GLM: always the halo-capable kernels (no halo faces here), so
+    // that a grid and the blocks of its decomposition run the same code
+    if (g.ndim == 3)
+      return launch_stage_halo<T>(g, stage, win, un, uout, sc, lam_bits, floor_cnt, stream, a_n,
+                                  a_w, nullptr, est_bits, zlo, zhi, tz);
+  }
   if (g.limiter == kLimWenoz) {
-    if (g.ndim == 3) {
-      dim3 grid((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, nzc);
-      if (stage == 1) return launch_weno<T, 4, 8, 1, true>(p, grid, stream);
-      if (stage == 2) return launch_weno<T, 4, 8, 2, true>(p, grid, stream);
-      return launch_weno<T, 4, 8, 3, true>(p, grid, stream);
+    if constexpr (sizeof(T) == 4) {
+      if (g.ndim == 3) {
+        dim3 grid((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, nzc);
+        if (stage == 1) return launch_weno<T, 4, 8, 1, true>(p, grid, stream);
+        if (stage == 2) return launch_weno<T, 4, 8, 2, true>(p, grid, stream);
+        return launch_weno<T, 4, 8, 3, true>(p, grid, stream);
+      }
     }
     if (g.ndim == 2) {
       dim3 grid((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, 1);
@@ -224,12 +239,14 @@ cudaError_t launch_stage(const Grid& g, int stage, const T* win, const T* un, T*
     if (stage == 2) return launch_weno<T, 1, 1, 2, false>(p, grid, stream);
     return launch_weno<T, 1, 1, 3, false>(p, grid, stream);
   }
-  if (g.ndim == 3) {
-    using S = StageShape3D<T>;
-    dim3 grid((g.n[0] + 31) / 32, (g.n[1] + S::TY - 1) / S::TY, nzc);
-    if (stage == 1) return launch_one<T, S::TY, S::NW, 1, true>(p, grid, stream);
-    if (stage == 2) return launch_one<T, S::TY, S::NW, 2, true>(p, grid, stream);
-    return launch_one<T, S::TY, S::NW, 3, true>(p, grid, stream);
+  if constexpr (sizeof(T) == 4) {
+    if (g.ndim == 3) {
+      using S = StageShape3D<T>;
+      dim3 grid((g.n[0] + 31) / 32, (g.n[1] + S::TY - 1) / S::TY, nzc);
+      if (stage == 1) return launch_one<T, S::TY, S::NW, 1, true>(p, grid, stream);
+      if (stage == 2) return launch_one<T, S::TY, S::NW, 2, true>(p, grid, stream);
+      return launch_one<T, S::TY, S::NW, 3, true>(p, grid, stream);
+    }
   }
   if (g.ndim == 2) {
     dim3 grid((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, 1);
@@ -250,17 +267,18 @@ template <class T>
 cudaError_t launch_stage_halo(const Grid& g, int stage, const T* win, const T* un, T* uout,
                               const StepScalars* sc, unsigned long long* lam_bits,
                               unsigned long long* floor_cnt, cudaStream_t stream, double a_n,
-                              double a_w, const T* const* halo, unsigned int* est_bits) {
-  if (g.ndim != 3 || !halo) return cudaErrorInvalidValue;
+                              double a_w, const T* const* halo, unsigned int* est_bits, int zlo,
+                              int zhi, int tz) {
+  if (g.ndim != 3) return cudaErrorInvalidValue;
   StageParams<T> p;
-  cudaError_t pe = stage_params(p, g, win, un, uout, sc, lam_bits, floor_cnt, a_n, a_w, 0, -1,
-                                0, est_bits);
+  cudaError_t pe = stage_params(p, g, win, un, uout, sc, lam_bits, floor_cnt, a_n, a_w, zlo, zhi,
+                                tz, est_bits);
   if (pe != cudaSuccess) return pe;
   if (sizeof(T) == 8 && stage == 2 && !est_bits) return cudaErrorInvalidValue;
   for (int f = 0; f < 6; ++f) {
     const bool lo = (f & 1) == 0;
     const int bc = lo ? g.bc_lo[f >> 1] : g.bc_hi[f >> 1];
-    if (bc == kBcHalo && !halo[f]) return cudaErrorInvalidValue;
+    if (bc == kBcHalo && (!halo || !halo[f])) return cudaErrorInvalidValue;
     p.halo[f] = bc == kBcHalo ? halo[f] : nullptr;
   }
   const int nzc = (p.zhi - p.zlo + p.tz - 1) / p.tz;

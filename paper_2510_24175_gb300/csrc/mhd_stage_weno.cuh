@@ -252,49 +252,31 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
     cell_weno(c, st, M, P);
   };
 
-  if constexpr (ZACT) {
-    // prologue: z face value P of cell z0-1 and the z flux at face z0-1/2
-    for (int it = tid; it < 5 * G::NINT; it += NT) {
-      const int pl = it / G::NINT, j = it - pl * G::NINT;
-      load_item(j, z0 - 3 + pl, 0);
-    }
-    __syncthreads();
-    T Pprev[kNV];
-    if (owner) {
-      T M[kNV];
-      z_cell(z0 - 1, M, Pprev);
-    }
-    __syncthreads();
-    for (int it = tid; it < G::NINT; it += NT) load_item(it, z0 + 2, 0);
-    __syncthreads();
-    if (owner) {
-      T M[kNV], P[kNV], F[kNV];
-      z_cell(z0, M, P);
-      if constexpr (CT) ct_face_field(Pprev, M, 2, bface(2, z0, orow, ocol));
-      glm_hlld_flux<2>(Pprev, M, ch, half_chi, ph, F);
-#pragma unroll
-      for (int k = 0; k < kNV; ++k) {
-        zP[k * G::NINT + oidx] = P[k];
-        zF[k * G::NINT + oidx] = F[k];
-      }
-    }
-    __syncthreads();
-  }
-
+  // The z march: one loop body for every plane (see stage_tile in
+  // mhd_stage.cuh), so a cell's result does not depend on where a z chunk,
+  // block or launch range starts.  Warm-up: k = z0-6 .. z0-3 only load
+  // planes z0-3 .. z0 into the ring, k = z0-2 computes the column owners'
+  // face values of cell z0-1, k = z0-1 their flux through face z0-1/2; the
+  // x, y work and the update start at k = z0.
+  constexpr int NWARM = ZACT ? 6 : 0;
   SpeedMax<T> smax(ph);  // last stage: the new state's maximum wave speed
-  for (int k = z0; k < z1; ++k) {
+#pragma unroll 1
+  for (int k = z0 - NWARM; k < z1; ++k) {
+    const bool main = k >= z0;
     // ---- A: loads ---------------------------------------------------------
-    for (int it = tid; it < G::NLOAD; it += NT) {
+    const int nload = main ? G::NLOAD : G::NINT;
+    for (int it = tid; it < nload; it += NT) {
       if (ZACT && it < G::NINT)
         load_item(it, k + 3, k);
       else
         load_item(it, k, k);
     }
     __syncthreads();
+    if (ZACT && k < z0 - 2) continue;
     const T* cur = ring_plane(k);
 
     // ---- B: face values ---------------------------------------------------
-    for (int it = tid; it < G::SXN + G::SYN; it += NT) {
+    for (int it = tid; main && it < G::SXN + G::SYN; it += NT) {
       const T* c[5];
       int st[5];
       T M[kNV], P[kNV];
@@ -333,7 +315,7 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
     __syncthreads();
 
     // ---- C: fluxes --------------------------------------------------------
-    for (int it = tid; it < G::ITEMS; it += NT) {
+    for (int it = tid; main && it < G::ITEMS; it += NT) {
       T vl[kNV], vr[kNV], F[kNV];
       T* out;
       int os;
@@ -392,19 +374,22 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
           ctc.fz_by = zF[kBY * G::NINT + oidx];
           ctc.fz_rho = zF[kRHO * G::NINT + oidx];
         }
-        glm_hlld_flux<2>(vl, vr, ch, half_chi, ph, F);
+        if (k >= z0 - 1) {  // from k = z0-1 on, zP holds the plus value of cell k
+          glm_hlld_flux<2>(vl, vr, ch, half_chi, ph, F);
 #pragma unroll
-        for (int q = 0; q < kNV; ++q) {
-          dUz[q] = (F[q] - zF[q * G::NINT + oidx]) * dtdz;
-          zF[q * G::NINT + oidx] = F[q];
-          zP[q * G::NINT + oidx] = zPn[q * G::NINT + oidx];
+          for (int q = 0; q < kNV; ++q) {
+            dUz[q] = mul_rn(F[q] - zF[q * G::NINT + oidx], dtdz);
+            zF[q * G::NINT + oidx] = F[q];
+          }
         }
+#pragma unroll
+        for (int q = 0; q < kNV; ++q) zP[q * G::NINT + oidx] = zPn[q * G::NINT + oidx];
       }
     }
     __syncthreads();
 
     // ---- D: right-hand side and Runge-Kutta combination --------------------
-    if (owner) {
+    if (main && owner) {
       const int gx = x0 + ocol, gy = y0 + orow;
       const bool valid = gx < nx && gy < ny;
       T unew[kNV];
@@ -415,10 +400,12 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
 #pragma unroll
         for (int q = 0; q < kNV; ++q) {
           const T* fx = Fx + q * G::FXN + orow * (TX + 1) + ocol;
-          T du = (fx[1] - fx[0]) * dtdx;
+          // sums of products with their rounding fixed (mul_rn / fma_rn), so
+          // every instantiation of this tile code gives the same bits
+          T du = mul_rn(fx[1] - fx[0], dtdx);
           if constexpr (G::GY > 0) {
             const T* fy = Fy + q * G::FYN + orow * TX + ocol;
-            du += (fy[TX] - fy[0]) * dtdy;
+            du = fma_rn(fy[TX] - fy[0], dtdy, du);
           }
           if constexpr (ZACT) du += dUz[q];
           if (frozen) du = T(0);
@@ -426,7 +413,7 @@ __global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StagePa
           if constexpr (STAGE == 1) {
             unew[q] = s1;
           } else {
-            unew[q] = p.a_n * p.un[q * p.sv + off] + p.a_w * s1;
+            unew[q] = fma_rn(p.a_n, p.un[q * p.sv + off], mul_rn(p.a_w, s1));
           }
         }
         if constexpr (CT) {

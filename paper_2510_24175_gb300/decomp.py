@@ -121,14 +121,17 @@ class Decomposition:
         return [f for f in range(6) if self.neighbour(rank, f) is not None]
 
     def local_config(self, cfg: Config, rank: int) -> Config:
-        """The block's configuration: its cells, its part of the domain (the
-        same cell size), its boundary conditions."""
+        """The block's configuration: its cells, its part of the domain, its
+        boundary conditions, and the whole grid's cell size passed as given
+        (the block's time step and flux divergence then round as the whole
+        grid's do)."""
         lo, hi = self.extent(rank)
-        dx = [(cfg.xmax[d] - cfg.xmin[d]) / cfg.n[d] for d in range(3)]
+        dx = tuple((cfg.xmax[d] - cfg.xmin[d]) / cfg.n[d] if not (cfg.dx[d] > 0) else cfg.dx[d]
+                   for d in range(3))
         return replace(cfg, n=self.shape(rank),
                        xmin=tuple(cfg.xmin[d] + lo[d] * dx[d] for d in range(3)),
                        xmax=tuple(cfg.xmin[d] + hi[d] * dx[d] for d in range(3)),
-                       bc=self.local_bc(rank))
+                       bc=self.local_bc(rank), dx=dx)
 
     def scatter(self, U, rank: int):
         """The block's part of a global array (..., nz, ny, nx)."""
