@@ -87,6 +87,11 @@ def parse():
     ap.add_argument("--no-brio", action="store_true", help="skip the Brio-Wu latency line")
     ap.add_argument("--no-paper-scheme", action="store_true",
                     help="skip the WENO-Z + SSP-RK3 throughput lines")
+    ap.add_argument("--no-decomposed", action="store_true",
+                    help="skip the line of the grid decomposed into blocks on one GPU")
+    ap.add_argument("--mode", default="replicas", choices=["replicas", "decomposed"],
+                    help="under torchrun: independent replicas (default), or one n^3 block per "
+                         "rank of a grid decomposed along z, halos exchanged over NCCL")
     return ap.parse_args()
 
 
@@ -293,10 +298,69 @@ def roofline_of(prof, ncell, esize, hbm_peak, peak_kind, fp64):
     return hbm, alu
 
 
+def run_decomposed(args):
+    """--mode decomposed: one n^3 block per rank of an Orszag-Tang grid of
+    n x n x (n ranks) cells on [0,1] x [0,1] x [0,ranks] (the vortex repeats
+    along z, so every block does the single-box work), decomposed along z;
+    per stage each rank packs its two z boundary slabs and exchanges them with
+    its neighbours over NCCL, per step the wave speed is max-allreduced.
+    Weak scaling; value = zone-updates/s of the whole grid."""
+    import torch
+    import torch.distributed as dist
+    import paper_2510_24175_gb300 as m
+    from paper_2510_24175_gb300 import inputs
+    from paper_2510_24175_gb300.decomp import DistributedBlock
+    from dataclasses import replace
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n, K, W = args.n, args.steps, args.warmup
+    pb = inputs.orszag_tang_3d(n)
+    cfg = replace(m.Config.from_problem(pb), n=(n, n, n * world), xmax=(1.0, 1.0, float(world)))
+    blk = DistributedBlock(cfg, (1, 1, world), rank)
+    mine = replace(pb, xmin=(0.0, 0.0, float(rank)), xmax=(1.0, 1.0, float(rank + 1)))
+    blk.solver.set_state(torch.from_numpy(mine.prim()).cuda(), kind=m.MHD_PRIM)
+    for _ in range(W):
+        blk.step()
+    stream = torch.cuda.current_stream()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        blk.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t = torch.tensor([e0.elapsed_time(e1)], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    dist.barrier()
+    if rank == 0:
+        value = world * pb.ncell * K / (ms * 1e-3)
+        print(json.dumps({
+            "metric": "zone-updates/s", "value": value, "unit": "zone-updates/s",
+            "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (closed-form Orszag-Tang initial condition)",
+            "config": {**workload_config(n, world),
+                       "parallelism": f"grid of {n} x {n} x {n * world} cells decomposed along "
+                                      f"z into {world} blocks, halo exchange over NCCL"},
+            "clocks": clk}))
+    dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.mode == "decomposed":
+        run_decomposed(args)
         return
     import numpy as np
     import torch
@@ -630,6 +694,40 @@ def main():
         del ens, plain
         torch.cuda.empty_cache()
 
+    # ---- the same grid as 2 x 2 blocks on this GPU (halo faces) ------------
+    decomposed = None
+    if not args.no_decomposed:
+        from paper_2510_24175_gb300.decomp import LocalBlocks
+        dims = (1, 2, 2)
+        lb = LocalBlocks(m.Config.from_problem(pb), dims)
+        lb.set_state(V0, kind=m.MHD_PRIM)
+        for _ in range(W):
+            lb.step()
+        stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        for b in lb.blocks:
+            b.profile(True)
+            b.profile_read()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            lb.step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_d = e0.elapsed_time(e1)
+        stage_ms = sum(b.profile_read()[c][1] for b in lb.blocks for c in ("stage1", "stage2"))
+        halo_bytes = sum(b.halo_bytes(f) for r, b in enumerate(lb.blocks)
+                         for f in lb.dec.halo_faces(r))
+        decomposed = {
+            "workload": f"orszag_tang_3d_{args.n}^3_fp64 as {dims[1]} x {dims[2]} blocks (y, z) "
+                        "on one GPU, halo buffers packed from the neighbouring blocks each stage",
+            "value": N * K / (ms_d * 1e-3), "unit": "zone-updates/s", "ms_per_step": ms_d / K,
+            "stage_kernels_ms_per_step": stage_ms / K,
+            "over_undecomposed": (N * K / (ms_d * 1e-3)) / value,
+            "halo_bytes_per_stage": int(halo_bytes)}
+        del lb
+        torch.cuda.empty_cache()
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -671,6 +769,7 @@ def main():
         "paper_scheme_wenoz_rk3": paper_scheme,
         "adjoint": adjoint,
         "ensemble": ensemble,
+        "decomposed_one_gpu": decomposed,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))
