@@ -214,15 +214,18 @@ struct TileGeom {
   static constexpr int NRING = ZACT ? 3 : 1;
   // shared-memory words
   static constexpr int RING_W = NRING * kNV * NINT;
-  static constexpr int XH_W = kNV * NXH;
-  static constexpr int YH_W = kNV * NYH;
+  // x and y halo cells share one buffer with the ring's variable stride NINT
+  // (x halo items first, then y halo items), so every cell of the current
+  // plane is reached with the same compile-time stride
+  static_assert(NXH + NYH <= NINT, "the halo cells must fit one plane's stride");
+  static constexpr int HB_W = kNV * NINT;
   static constexpr int SXN = TY * (TX + 2);         // x slopes, columns -1..32
   static constexpr int SYN = GY ? (TY + 2) * TX : 0;  // y slopes, rows -1..TY
   static constexpr int FXN = TY * (TX + 1);
   static constexpr int FYN = GY ? (TY + 1) * TX : 0;
   static constexpr int Z_W = ZACT ? 3 * kNV * NINT : 0;  // z slope, z face state, z flux
   static constexpr int WORDS =
-      RING_W + XH_W + YH_W + kNV * SXN + kNV * SYN + kNV * FXN + kNV * FYN + Z_W;
+      RING_W + HB_W + kNV * SXN + kNV * SYN + kNV * FXN + kNV * FYN + Z_W;
   // phase-A items: interior, x halo, y halo
   static constexpr int NLOAD = NINT + NXH + NYH;
   // phase-C flux items, warp-aligned segments [x main][y][x right edge]
@@ -268,9 +271,9 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
   constexpr int ZT0 = NT - G::NINT;  // threads ZT0.. own one tile column each
   static_assert(ZT0 >= 0, "need one thread per tile column");
   T* ring = reinterpret_cast<T*>(smem_raw);
-  T* xh = ring + G::RING_W;
-  T* yh = xh + G::XH_W;
-  T* sxs = yh + G::YH_W;
+  T* xh = ring + G::RING_W;  // x halo items (variable stride G::NINT)
+  T* yh = xh + G::NXH;        // y halo items (same buffer and stride)
+  T* sxs = xh + G::HB_W;
   T* sys = sxs + kNV * G::SXN;
   T* Fx = sys + kNV * G::SYN;
   T* Fy = Fx + kNV * G::FXN;
@@ -345,23 +348,23 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
       const int j = it - G::NINT;
       const int r = j >> 2, q = j & 3;
       const int c = q < 2 ? q - 2 : TX + q - 2;
-      load_cell(zh, r, c, xh + j, G::NXH, false);
+      load_cell(zh, r, c, xh + j, G::NINT, false);
     } else {
       const int j = it - G::NINT - G::NXH;
       const int hr = j / TX, c = j - (j / TX) * TX;
       const int r = hr < 2 ? hr - 2 : TY + hr - 2;
-      load_cell(zh, r, c, yh + j, G::NYH, false);
+      load_cell(zh, r, c, yh + j, G::NINT, false);
     }
   };
   // primitives of cell (r, c) of the current plane (interior in ring slot,
   // halo in the halo buffers); returns the pointer, stride in *st
   auto cell_ptr = [&](const T* cur, int r, int c, int* st) -> const T* {
     if (c < 0 || c >= TX) {
-      *st = G::NXH;
+      *st = G::NINT;
       return xh + r * 4 + (c < 0 ? c + 2 : c - TX + 2);
     }
     if (r < 0 || r >= TY) {
-      *st = G::NYH;
+      *st = G::NINT;
       return yh + (r < 0 ? r + 2 : r - TY + 2) * TX + c;
     }
     *st = G::NINT;
