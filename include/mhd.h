@@ -375,13 +375,21 @@ int mhd_ensemble_get_state(mhd_ensemble* ens, int box, double* U, int where, int
  * dt and c_h, stage 1, grid barrier, stage 2, grid barrier).  Asynchronous. */
 int mhd_ensemble_step(mhd_ensemble* ens, int nsteps);
 /* out[0] = t, out[1] = dt, out[2] = c_h, out[3] = steps of box `box`,
- * out[4] = its z-chunk depth, out[5] = 1 if launches are graph-captured.
+ * out[4] = its z-chunk depth, out[5] = 1 if launches are graph-captured,
+ * out[6] = its tile height (column tiles of 32 x out[6] cells).
  * Synchronises; MHD_ERR_NONFINITE if the box saw a non-finite dt. */
-int mhd_ensemble_info(mhd_ensemble* ens, int box, double out[6]);
-/* Timing autotuner: for each box-size class, tries z-chunk depths
- * {4, 8, 16, 32, 64} (coordinate descent, timing trial_steps-step launches)
- * and keeps the fastest.  ADVANCES every box by the trial steps: save and
- * restore the states around it.  Synchronises. */
+int mhd_ensemble_info(mhd_ensemble* ens, int box, double out[7]);
+/* Tile shape: column tiles of 32 x ty cells (ty = 8 or 4; the tile height of
+ * the launch, so it applies to every box) marching z chunks of tz planes for
+ * box `box` (clamped to its nz).  Every tile shape gives the same results
+ * bit for bit; only the speed differs.  Synchronises. */
+int mhd_ensemble_set_tiles(mhd_ensemble* ens, int box, int ty, int tz);
+/* Timing autotuner: the launch's tile height {8, 4}, then for each box-size
+ * class the z-chunk depth {4, 8, 16, 32, 64} (one pass of coordinate
+ * descent over the classes; each candidate the best of two timed
+ * trial_steps-step launches, kept only when more than 1 % faster).  Every
+ * box evolves bitwise alike under any tile shape.  ADVANCES every box by the
+ * trial steps: save and restore the states around it.  Synchronises. */
 int mhd_ensemble_autotune(mhd_ensemble* ens, int trial_steps);
 const char* mhd_ensemble_last_error(const mhd_ensemble* ens);
 int mhd_ensemble_destroy(mhd_ensemble* ens);

@@ -44,7 +44,8 @@ EXPORTED = ["mhd_config_default", "mhd_workspace_bytes", "mhd_create", "mhd_set_
             "mhd_step_begin", "mhd_step_stage",
             "mhd_ensemble_workspace_bytes", "mhd_ensemble_create", "mhd_ensemble_set_state",
             "mhd_ensemble_get_state", "mhd_ensemble_step", "mhd_ensemble_info",
-            "mhd_ensemble_autotune", "mhd_ensemble_last_error", "mhd_ensemble_destroy"]
+            "mhd_ensemble_autotune", "mhd_ensemble_set_tiles", "mhd_ensemble_last_error",
+            "mhd_ensemble_destroy"]
 
 
 class MHDError(RuntimeError):
@@ -112,6 +113,7 @@ def lib():
         L.mhd_ensemble_step.argtypes = [vp, i]
         L.mhd_ensemble_info.argtypes = [vp, i, dp]
         L.mhd_ensemble_autotune.argtypes = [vp, i]
+        L.mhd_ensemble_set_tiles.argtypes = [vp, i, i, i]
         L.mhd_ensemble_last_error.argtypes = [vp]
         L.mhd_ensemble_last_error.restype = ctypes.c_char_p
         L.mhd_ensemble_destroy.argtypes = [vp]
@@ -612,14 +614,21 @@ class Ensemble:
         self._err(lib().mhd_ensemble_step(self.ens, nsteps), "mhd_ensemble_step")
 
     def info(self, box: int):
-        out = (ctypes.c_double * 6)()
+        out = (ctypes.c_double * 7)()
         self._err(lib().mhd_ensemble_info(self.ens, box, out), "mhd_ensemble_info")
         return {"t": out[0], "dt": out[1], "ch": out[2], "steps": int(out[3]),
-                "tz": int(out[4]), "graph": bool(out[5])}
+                "tz": int(out[4]), "graph": bool(out[5]), "ty": int(out[6])}
+
+    def set_tiles(self, box: int, ty: int, tz: int):
+        """Tile shape of one box: 32 x ty column tiles (ty = 8 or 4), z chunks
+        of tz planes (mhd_ensemble_set_tiles)."""
+        self._err(lib().mhd_ensemble_set_tiles(self.ens, box, int(ty), int(tz)),
+                  "mhd_ensemble_set_tiles")
 
     def autotune(self, trial_steps: int = 1):
-        """Picks z-chunk depths by timing; the boxes' states are saved before
-        and restored after (the trial launches advance them)."""
+        """Picks each box-size class's tile height and z-chunk depth by timing;
+        the boxes' states are saved before and restored after (the trial
+        launches advance them)."""
         saved = [self.get_state(b) for b in range(len(self))]
         self._err(lib().mhd_ensemble_autotune(self.ens, trial_steps), "mhd_ensemble_autotune")
         for b, U in enumerate(saved):

@@ -11,8 +11,11 @@
 // box evolves bitwise as it would under its own mhd_step calls.  Grid syncs
 // are cooperative-group barriers: the cooperative launch guarantees that all
 // CTAs are co-resident (the launch fails otherwise), so no wait can hang.
-// The z-chunk depth (tz) of each box-size class is picked by a timing
-// autotuner (mhd_ensemble_autotune).
+// The tile shape -- the launch's tile height TY (32 x 8 or 32 x 4 columns,
+// one instantiation of the persistent kernel each, both on 8-warp CTAs) and
+// each box-size class's z-chunk depth tz -- is picked by a timing autotuner
+// (mhd_ensemble_autotune).  (Both tile heights in one kernel, chosen per box,
+// made it spill and ran slower.)
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -30,9 +33,8 @@ namespace cg = cooperative_groups;
 
 namespace mhd {
 
-constexpr int kEnsTY = 8;
 constexpr int kEnsNW = 8;
-using EnsGeom = TileGeom<kEnsTY, true>;
+constexpr int kEnsTYs[2] = {8, 4};  // the tile heights of the two kernel instantiations
 
 struct EnsBox {
   StageParams<float> p;  // geometry / physics; state pointers set per stage
@@ -45,6 +47,7 @@ struct EnsBox {
   int cur;               // lam_bits slot holding the current state's wave speed
   double cfl, inv_dx_sum, t_end, glm_alpha, dh_min;
   double dx[3];
+  int ty;                // tile height of the launch: 8 or 4 rows of 32 columns
   int ntx, nty, ntz;     // tiles per dimension
   long long item0;       // first work item of this box
 };
@@ -89,7 +92,7 @@ __device__ __forceinline__ int ens_find(const EnsBox* boxes, int nbox, long long
   return lo;
 }
 
-template <int STAGE>
+template <int TY, int STAGE>
 __device__ __forceinline__ void ens_stage(const EnsArgs& a, unsigned char* smem, double* wmax) {
   for (long long it = blockIdx.x; it < a.nitems; it += gridDim.x) {
     const int bi = ens_find(a.boxes, a.nbox, it);
@@ -107,10 +110,11 @@ __device__ __forceinline__ void ens_stage(const EnsArgs& a, unsigned char* smem,
     const int bx = (int)(j % B.ntx);
     const int by = (int)((j / B.ntx) % B.nty);
     const int bz = (int)(j / ((long long)B.ntx * B.nty));
-    stage_tile<float, kEnsTY, kEnsNW, STAGE, true>(p, sc, bx, by, bz, smem, wmax);
+    stage_tile<float, TY, kEnsNW, STAGE, true>(p, sc, bx, by, bz, smem, wmax);
   }
 }
 
+template <int TY>
 __global__ void __launch_bounds__(kEnsNW * 32, 2) ensemble_kernel(const EnsArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double wmax[kEnsNW];
@@ -119,9 +123,9 @@ __global__ void __launch_bounds__(kEnsNW * 32, 2) ensemble_kernel(const EnsArgs 
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gt < a.nbox) ens_prep(a.boxes[gt]);
     grid.sync();
-    ens_stage<1>(a, smem_raw, wmax);
+    ens_stage<TY, 1>(a, smem_raw, wmax);
     grid.sync();
-    ens_stage<2>(a, smem_raw, wmax);
+    ens_stage<TY, 2>(a, smem_raw, wmax);
     grid.sync();
   }
 }
@@ -138,11 +142,12 @@ struct mhd_ensemble {
   std::vector<int> cur;        // host mirror of each box's lam slot
   std::vector<bool> lam_ok;    // box wave speed valid for the next step
   std::vector<int> tz;         // z-chunk depth per box
+  int ty;                      // tile height of the launches (8 or 4)
   cudaStream_t stream;
   cudaStream_t cap;            // private stream the graph is captured on (the
                                // legacy default stream cannot be captured)
-  size_t smem;
-  int grid_ctas;
+  size_t smem[2];              // per tile height (index of kEnsTYs)
+  int grid_ctas[2];
   long long nitems;
   cudaGraphExec_t gexec;
   int graph_steps;
@@ -196,10 +201,11 @@ static int ens_layout(mhd_ensemble* e) {
     EnsBox& B = e->h[b];
     const mhd::Grid& g = e->ctx[b]->grid;
     B.p.tz = e->tz[b];
+    B.ty = e->ty;
     B.p.zlo = 0;
     B.p.zhi = g.n[2];
     B.ntx = (g.n[0] + 31) / 32;
-    B.nty = (g.n[1] + mhd::kEnsTY - 1) / mhd::kEnsTY;
+    B.nty = (g.n[1] + B.ty - 1) / B.ty;
     B.ntz = (g.n[2] + B.p.tz - 1) / B.p.tz;
     B.item0 = item;
     item += (long long)B.ntx * B.nty * B.ntz;
@@ -234,17 +240,19 @@ static int ens_layout(mhd_ensemble* e) {
 
 static cudaError_t ens_launch(mhd_ensemble* e, int nsteps, cudaStream_t s) {
   mhd::EnsArgs a{e->d, e->nbox, e->nitems, nsteps};
+  const int k = e->ty == 4 ? 1 : 0;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(e->grid_ctas);
+  cfg.gridDim = dim3(e->grid_ctas[k]);
   cfg.blockDim = dim3(mhd::kEnsNW * 32);
-  cfg.dynamicSmemBytes = e->smem;
+  cfg.dynamicSmemBytes = e->smem[k];
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, mhd::ensemble_kernel, a);
+  return k ? cudaLaunchKernelEx(&cfg, mhd::ensemble_kernel<4>, a)
+           : cudaLaunchKernelEx(&cfg, mhd::ensemble_kernel<8>, a);
 }
 
 extern "C" {
@@ -307,6 +315,7 @@ int mhd_ensemble_create(const mhd_config* cfgs, int nbox, void* d_workspace, siz
   e->cur.assign(nbox, 0);
   e->lam_ok.assign(nbox, false);
   e->tz.assign(nbox, 16);
+  e->ty = 8;
   for (int b = 0; b < nbox; ++b) {
     mhd_ctx* c = e->ctx[b];
     EnsBox B;
@@ -336,24 +345,34 @@ int mhd_ensemble_create(const mhd_config* cfgs, int nbox, void* d_workspace, siz
   }
   // zeroed dynamic fields on the device, then the layout
   cudaError_t ce = cudaMemsetAsync(e->d, 0, sizeof(EnsBox) * nbox, e->stream);
-  e->smem = (size_t)mhd::EnsGeom::WORDS * sizeof(float);
+  // both instantiations: shared-memory limit and co-resident CTAs per SM
+  // (the cooperative grid size)
+  e->smem[0] = (size_t)mhd::TileGeom<8, true>::WORDS * sizeof(float);
+  e->smem[1] = (size_t)mhd::TileGeom<4, true>::WORDS * sizeof(float);
+  int per_sm[2] = {0, 0}, nsm = 0, dev = 0;
   if (ce == cudaSuccess)
-    ce = cudaFuncSetAttribute(mhd::ensemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)e->smem);
-  int per_sm = 0, nsm = 0, dev = 0;
+    ce = cudaFuncSetAttribute(mhd::ensemble_kernel<8>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem[0]);
+  if (ce == cudaSuccess)
+    ce = cudaFuncSetAttribute(mhd::ensemble_kernel<4>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem[1]);
   if (ce == cudaSuccess) ce = cudaGetDevice(&dev);
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (ce == cudaSuccess)
-    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mhd::ensemble_kernel,
-                                                       mhd::kEnsNW * 32, e->smem);
-  if (ce != cudaSuccess || per_sm < 1 || ens_layout(e) != MHD_OK) {
+    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], mhd::ensemble_kernel<8>,
+                                                       mhd::kEnsNW * 32, e->smem[0]);
+  if (ce == cudaSuccess)
+    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], mhd::ensemble_kernel<4>,
+                                                       mhd::kEnsNW * 32, e->smem[1]);
+  if (ce != cudaSuccess || per_sm[0] < 1 || per_sm[1] < 1 || ens_layout(e) != MHD_OK) {
     for (auto* x : e->ctx) mhd_destroy(x);
     cudaStreamDestroy(e->cap);
     delete e;
     return mhd::free_fail(MHD_ERR_CUDA, "mhd_ensemble_create: kernel set-up failed (%s)",
                           cudaGetErrorString(ce));
   }
-  e->grid_ctas = per_sm * nsm;
+  e->grid_ctas[0] = per_sm[0] * nsm;
+  e->grid_ctas[1] = per_sm[1] * nsm;
   *out = e;
   return MHD_OK;
 }
@@ -428,7 +447,7 @@ int mhd_ensemble_step(mhd_ensemble* e, int nsteps) {
   return MHD_OK;
 }
 
-int mhd_ensemble_info(mhd_ensemble* e, int box, double out[6]) {
+int mhd_ensemble_info(mhd_ensemble* e, int box, double out[7]) {
   if (!e || !out || box < 0 || box >= e->nbox) return MHD_ERR_INVALID;
   EnsBox r;
   ECK(e, cudaMemcpyAsync(&r, e->d + box, sizeof(r), cudaMemcpyDeviceToHost, e->stream));
@@ -439,8 +458,19 @@ int mhd_ensemble_info(mhd_ensemble* e, int box, double out[6]) {
   out[3] = r.sc.steps;
   out[4] = (double)e->tz[box];
   out[5] = e->graph_ok ? 1.0 : 0.0;
+  out[6] = (double)e->ty;
   if (r.status) return efail(e, MHD_ERR_NONFINITE, "box %d: non-finite dt or c_h", box);
   return MHD_OK;
+}
+
+int mhd_ensemble_set_tiles(mhd_ensemble* e, int box, int ty, int tz) {
+  if (!e) return MHD_ERR_INVALID;
+  if (box < 0 || box >= e->nbox || (ty != 8 && ty != 4) || tz < 1)
+    return efail(e, MHD_ERR_INVALID, "mhd_ensemble_set_tiles: box %d, tile height %d (8 or 4), "
+                 "z-chunk depth %d (>= 1)", box, ty, tz);
+  e->ty = ty;  // the launch's tile height: every box
+  e->tz[box] = std::min(tz, e->ctx[box]->grid.n[2]);
+  return ens_layout(e);
 }
 
 int mhd_ensemble_autotune(mhd_ensemble* e, int trial_steps) {
@@ -454,32 +484,56 @@ int mhd_ensemble_autotune(mhd_ensemble* e, int trial_steps) {
   cudaEvent_t t0, t1;
   ECK(e, cudaEventCreate(&t0));
   ECK(e, cudaEventCreate(&t1));
+  // the best of two timed launches after a warm-up launch (which also
+  // builds the graph)
   auto time_one = [&](float* ms) -> int {
     int rc = ens_layout(e);
     if (rc != MHD_OK) return rc;
-    rc = mhd_ensemble_step(e, trial_steps);  // warm (also builds the graph)
-    if (rc != MHD_OK) return rc;
-    ECK(e, cudaEventRecord(t0, e->stream));
     rc = mhd_ensemble_step(e, trial_steps);
     if (rc != MHD_OK) return rc;
-    ECK(e, cudaEventRecord(t1, e->stream));
-    ECK(e, cudaEventSynchronize(t1));
-    ECK(e, cudaEventElapsedTime(ms, t0, t1));
+    *ms = 1e30f;
+    for (int r = 0; r < 2; ++r) {
+      ECK(e, cudaEventRecord(t0, e->stream));
+      rc = mhd_ensemble_step(e, trial_steps);
+      if (rc != MHD_OK) return rc;
+      ECK(e, cudaEventRecord(t1, e->stream));
+      ECK(e, cudaEventSynchronize(t1));
+      float m = 0.f;
+      ECK(e, cudaEventElapsedTime(&m, t0, t1));
+      *ms = std::min(*ms, m);
+    }
     return MHD_OK;
   };
   float best = 0.f;
-  int rc = time_one(&best);
+  int rc = MHD_OK;
+  // A candidate is kept only when more than 1 % faster than the incumbent
+  // (timing noise).  First the launch's tile height, then -- one pass of
+  // coordinate descent over the size classes -- each class's z-chunk depth.
+  rc = time_one(&best);
+  const int ty0 = e->ty;
+  for (int ty : mhd::kEnsTYs) {
+    if (rc != MHD_OK || ty == ty0) continue;
+    const int prev = e->ty;
+    e->ty = ty;
+    float ms = 0.f;
+    rc = time_one(&ms);
+    if (rc == MHD_OK && ms < 0.99f * best)
+      best = ms;
+    else
+      e->ty = prev;
+  }
   const int cands[] = {4, 8, 16, 32, 64};
   for (auto& kv : cls) {
     const int nz = e->ctx[kv.second[0]]->grid.n[2];
     int keep = e->tz[kv.second[0]];
+    if (rc == MHD_OK) rc = time_one(&best);  // the incumbent, timed afresh
     for (int c : cands) {
       if (rc != MHD_OK) break;
       if (c > nz || c == keep) continue;
       for (int b : kv.second) e->tz[b] = c;
       float ms = 0.f;
       rc = time_one(&ms);
-      if (rc == MHD_OK && ms < best) {
+      if (rc == MHD_OK && ms < 0.99f * best) {
         best = ms;
         keep = c;
       }

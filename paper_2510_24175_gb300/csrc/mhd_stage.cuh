@@ -213,12 +213,13 @@ struct TileGeom {
   static constexpr int NYH = GY ? 4 * TX : 0;      // y halo: rows -2, -1, TY, TY+1
   static constexpr int NRING = ZACT ? 3 : 1;
   // shared-memory words
-  static constexpr int RING_W = NRING * kNV * NINT;
-  // x and y halo cells share one buffer with the ring's variable stride NINT
-  // (x halo items first, then y halo items), so every cell of the current
-  // plane is reached with the same compile-time stride
-  static_assert(NXH + NYH <= NINT, "the halo cells must fit one plane's stride");
-  static constexpr int HB_W = kNV * NINT;
+  // Variable stride PS of the ring slots and of the halo buffer: the x and y
+  // halo cells share one buffer (x halo items first, then y halo items) with
+  // the ring's stride, so every cell of the current plane is reached at a
+  // compile-time stride; PS = NINT unless the halo cells are more (TY = 4)
+  static constexpr int PS = NINT > NXH + NYH ? NINT : NXH + NYH;
+  static constexpr int RING_W = NRING * kNV * PS;
+  static constexpr int HB_W = kNV * PS;
   static constexpr int SXN = TY * (TX + 2);         // x slopes, columns -1..32
   static constexpr int SYN = GY ? (TY + 2) * TX : 0;  // y slopes, rows -1..TY
   static constexpr int FXN = TY * (TX + 1);
@@ -271,7 +272,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
   constexpr int ZT0 = NT - G::NINT;  // threads ZT0.. own one tile column each
   static_assert(ZT0 >= 0, "need one thread per tile column");
   T* ring = reinterpret_cast<T*>(smem_raw);
-  T* xh = ring + G::RING_W;  // x halo items (variable stride G::NINT)
+  T* xh = ring + G::RING_W;  // x halo items (variable stride G::PS)
   T* yh = xh + G::NXH;        // y halo items (same buffer and stride)
   T* sxs = xh + G::HB_W;
   T* sys = sxs + kNV * G::SXN;
@@ -304,7 +305,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
   unsigned flags = 0;  // of the wave-speed conversions (not counted)
 
   auto slot = [](int zz) { return ZACT ? ((zz % 3) + 3) % 3 : 0; };
-  auto ring_plane = [&](int zz) { return ring + slot(zz) * (kNV * G::NINT); };
+  auto ring_plane = [&](int zz) { return ring + slot(zz) * (kNV * G::PS); };
 
   // Floor activations are counted once per stage for each cell the tile
   // updates, from that cell's own conversion of the stage input; halo copies
@@ -343,31 +344,31 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
   auto load_item = [&](int it, int zi, int zh) {
     if (it < G::NINT) {
       const int r = it / TX, c = it - (it / TX) * TX;
-      load_cell(zi, r, c, ring_plane(zi) + it, G::NINT, true);
+      load_cell(zi, r, c, ring_plane(zi) + it, G::PS, true);
     } else if (it < G::NINT + G::NXH) {
       const int j = it - G::NINT;
       const int r = j >> 2, q = j & 3;
       const int c = q < 2 ? q - 2 : TX + q - 2;
-      load_cell(zh, r, c, xh + j, G::NINT, false);
+      load_cell(zh, r, c, xh + j, G::PS, false);
     } else {
       const int j = it - G::NINT - G::NXH;
       const int hr = j / TX, c = j - (j / TX) * TX;
       const int r = hr < 2 ? hr - 2 : TY + hr - 2;
-      load_cell(zh, r, c, yh + j, G::NINT, false);
+      load_cell(zh, r, c, yh + j, G::PS, false);
     }
   };
   // primitives of cell (r, c) of the current plane (interior in ring slot,
   // halo in the halo buffers); returns the pointer, stride in *st
   auto cell_ptr = [&](const T* cur, int r, int c, int* st) -> const T* {
     if (c < 0 || c >= TX) {
-      *st = G::NINT;
+      *st = G::PS;
       return xh + r * 4 + (c < 0 ? c + 2 : c - TX + 2);
     }
     if (r < 0 || r >= TY) {
-      *st = G::NINT;
+      *st = G::PS;
       return yh + (r < 0 ? r + 2 : r - TY + 2) * TX + c;
     }
-    *st = G::NINT;
+    *st = G::PS;
     return cur + r * TX + c;
   };
   static_assert(!CT || ZACT, "constrained transport is 3-D only");
@@ -436,8 +437,8 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
     }
     if (ZACT && owner) {
       T sig[kNV];
-      cell_slopes(cur + oidx, G::NINT, ring_plane(k + 1) + oidx, G::NINT,
-                  ring_plane(k + 2) + oidx, G::NINT, lim, sig);
+      cell_slopes(cur + oidx, G::PS, ring_plane(k + 1) + oidx, G::PS,
+                  ring_plane(k + 2) + oidx, G::PS, lim, sig);
 #pragma unroll
       for (int q = 0; q < kNV; ++q) zS[q * G::NINT + oidx] = sig[q];
     }
@@ -506,11 +507,11 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
 #pragma unroll
         for (int q = 0; q < kNV; ++q) {
           vl[q] = zP[q * G::NINT + oidx];
-          vr[q] = c[q * G::NINT] - T(0.5) * zS[q * G::NINT + oidx];
+          vr[q] = c[q * G::PS] - T(0.5) * zS[q * G::NINT + oidx];
         }
         if constexpr (CT) {
           ct_face_field(vl, vr, 2, bface(2, k + 1, orow, ocol));
-          ctc.from_prims(cur + oidx, G::NINT);
+          ctc.from_prims(cur + oidx, G::PS);
           ctc.fz_bx = zF[kBX * G::NINT + oidx];
           ctc.fz_by = zF[kBY * G::NINT + oidx];
           ctc.fz_rho = zF[kRHO * G::NINT + oidx];
@@ -525,7 +526,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
         }
 #pragma unroll
         for (int q = 0; q < kNV; ++q)
-          zP[q * G::NINT + oidx] = c[q * G::NINT] + T(0.5) * zS[q * G::NINT + oidx];
+          zP[q * G::NINT + oidx] = c[q * G::PS] + T(0.5) * zS[q * G::NINT + oidx];
       }
     }
     __syncthreads();

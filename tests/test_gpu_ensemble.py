@@ -22,7 +22,7 @@ def _boxes(sizes, seed=5):
     return pbs
 
 
-def _run_pair(pbs, step_calls, autotune=False):
+def _run_pair(pbs, step_calls, autotune=False, tiles=None):
     import torch
     import paper_2510_24175_gb300 as m
     cfgs = [m.Config.from_problem(pb) for pb in pbs]
@@ -34,6 +34,8 @@ def _run_pair(pbs, step_calls, autotune=False):
         plain[b].set_state(V, kind=m.MHD_PRIM)
     if autotune:
         ens.autotune(1)
+    for b, (ty, tz) in (tiles or {}).items():
+        ens.set_tiles(b, ty, tz)
     total = 0
     for k in step_calls:
         ens.step(k)
@@ -61,7 +63,21 @@ def test_ensemble_after_autotune_and_graph_reuse():
     for b in range(len(pbs)):
         assert bool((ens.get_state(b) == plain[b].get_state()).all()), f"box {b} differs"
     info = ens.info(0)
-    assert info["graph"] and info["tz"] in (4, 8, 16, 32)
+    assert info["graph"] and info["tz"] in (4, 8, 16, 32) and info["ty"] in (4, 8)
+
+
+@pytest.mark.parametrize("ty", [4, 8])
+def test_ensemble_tile_shapes_bitwise_equal_to_plain_launches(ty):
+    """The persistent launch on 32 x ty column tiles with ragged rows and odd
+    z-chunk depths: each box bitwise equal to its own per-box launches
+    (which run 32 x 8 tiles and the context's own z chunks)."""
+    pbs = _boxes([32, 48, 16, 33], seed=7)
+    tiles = {0: (ty, 5), 1: (ty, 48), 2: (ty, 3), 3: (ty, 1)}
+    ens, plain, total = _run_pair(pbs, [1, 2], tiles=tiles)
+    for b in range(len(pbs)):
+        assert bool((ens.get_state(b) == plain[b].get_state()).all()), f"box {b} differs"
+        inf = ens.info(b)
+        assert (inf["ty"], inf["tz"]) == (tiles[b][0], min(tiles[b][1], pbs[b].n[2]))
 
 
 def test_ensemble_rejects_fp64_and_2d_boxes():
