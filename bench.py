@@ -48,27 +48,36 @@ sys.path.insert(0, ROOT)
 # smsp__inst_executed_pipe_fp64 x 32 / cells over the timed steps of this
 # bench's Orszag-Tang 256^3 run (profiles/).  They change whenever the kernel
 # does.
-FP64_INST_PER_CELL = {1: 1182.7, 2: 1204.0}
+FP64_INST_PER_CELL = {1: 1195.6, 2: 1222.3}
 # DRAM bytes per cell of the stage kernel's launches (ncu dram__bytes_read +
 # dram__bytes_write over the timed steps of this bench's 256^3 FP64 and 512^3
 # FP32 runs, profiles/); reported as the roofline's traffic per launch.  Set
 # to None whenever the kernel changes until they are captured again.
-TRAFFIC_BYTES_PER_CELL = {8: {1: 149.3, 2: 221.1}, 4: {1: 75.6, 2: 111.4}}
-# FP64 pipe peak: 2 lanes/clk/SM (a DFMA probe measured 1.9) x 152 SMs x
-# 2.07 GHz = 629 G lane-instructions/s (1.26 TFLOP/s counting an FMA as 2).
+TRAFFIC_BYTES_PER_CELL = {8: {1: 149.4, 2: 221.3}, 4: {1: 75.7, 2: 111.4}}
+# Nominal FP64 peak: 2 lanes/clk/SM x 152 SMs x 2.07 GHz = 629 G
+# lane-instructions/s (1.26 TFLOP/s counting an FMA as 2).  The measured one,
+# mhd_fp64_fma_rate in the same run, is reported beside it (about 1.68
+# lanes/clk/SM: the SM's FP64 unit is shared by its warps, and one warp issues
+# an FP64 instruction at most every 64 clocks).
 FP64_PEAK_GINST = 2 * 152 * 2.07
 # Warp-instructions per cell of the FP32 stage kernel (ncu smsp__inst_executed
 # / cells, turbulent box 512^3, stage 1 / stage 2; profiles/) and the issue
 # peak they run against: 4 warp-instructions per clock per SM (one per
 # scheduler) x 152 SMs x 2.07 GHz.
-FP32_WARP_INST_PER_CELL = {1: 82.91, 2: 88.71}
+FP32_WARP_INST_PER_CELL = {1: 79.18, 2: 84.92}
 ISSUE_PEAK_GINST = 4 * 152 * 2.07
 # FP64-pipe lane-instructions per cell of the FP64 WENO-Z stage kernel (ncu,
-# Orszag-Tang 128^3; first / middle / last SSP-RK3 stage).
-WENO_FP64_INST_PER_CELL = {"stage1": 3594.7, "stage_mid": 3612.7, "stage2": 3613.8}
+# Orszag-Tang 256^3; first / middle / last SSP-RK3 stage).
+WENO_FP64_INST_PER_CELL = {"stage1": 3545.8, "stage_mid": 3563.8, "stage2": 3564.9}
+# Warp-instructions per cell of the FP32 WENO-Z stage kernel (ncu
+# smsp__inst_executed / cells, Orszag-Tang 256^3; first / middle / last
+# SSP-RK3 stage).
+WENO_FP32_WARP_INST_PER_CELL = {"stage1": 172.92, "stage_mid": 174.36, "stage2": 178.70}
 # Algorithmic HBM bytes per cell: stage 1 reads U^n and writes U1 (18 words),
 # stage 2 reads U1 and U^n and writes U^{n+1} (27 words).
 WORDS_STAGE = {1: 18, 2: 27}
+# SSP-RK3: the middle stage also reads U^n (27 words), like the last one.
+WORDS_STAGE_RK3 = {"stage1": 18, "stage_mid": 27, "stage2": 27}
 
 
 def parse():
@@ -272,7 +281,19 @@ def timed_steps(s, torch, K, dist, world):
     return ms, prof
 
 
-def roofline_of(prof, ncell, esize, hbm_peak, peak_kind, fp64):
+def fp64_peak_keys(ach, fma):
+    """The measured FP64 peak beside the nominal one: mhd_fp64_fma_rate run
+    on this GPU in this process (an FMA is one lane-instruction)."""
+    if not fma:
+        return {}
+    pk = fma["lane_fma_per_s"] / 1e9
+    return {"peak_measured": pk, "frac_of_measured": ach / pk,
+            "peak_measured_source": "mhd_fp64_fma_rate on this GPU in this run: one CTA of 8 "
+                                    "warps per SM, 16 independent DFMA chains per thread "
+                                    f"({fma['lanes_per_clk_per_sm']:.2f} lanes/clk/SM)"}
+
+
+def roofline_of(prof, ncell, esize, hbm_peak, peak_kind, fp64, fma=None):
     """Roofline of the stage kernel (both RK stages) from its CUDA-event times."""
     n1, ms1 = prof["stage1"]
     n2, ms2 = prof["stage2"]
@@ -293,8 +314,9 @@ def roofline_of(prof, ncell, esize, hbm_peak, peak_kind, fp64):
            "unit": "G FP64-lane-inst/s", "frac": ach / FP64_PEAK_GINST, "traffic": traffic,
            "kernel": "rk_stage_kernel", "avg_launch_ms": avg_ms,
            "fp64_inst_per_cell": FP64_INST_PER_CELL,
-           "peak_source": "2 FP64 lanes/clk/SM x 152 SMs x 2.07 GHz (GB300 nominal 1.25 "
-                          "TFLOP/s FP64); FP64 pipe is the bound (ncu: 84-85 % busy)"}
+           "peak_source": "nominal: 2 FP64 lanes/clk/SM x 152 SMs x 2.07 GHz (GB300 "
+                          "1.25 TFLOP/s FP64); the SM's FP64 unit is the bound",
+           **fp64_peak_keys(ach, fma)}
     return hbm, alu
 
 
@@ -378,6 +400,7 @@ def main():
 
     K, W = args.steps, args.warmup
     hbm_peak, peak_kind = peaks()
+    fma = m.mhd_fp64_fma_rate()  # the FP64 rooflines' measured denominator
 
     # ---- FP64: 3-D Orszag-Tang 256^3 ------------------------------------
     pb = inputs.orszag_tang_3d(args.n)
@@ -394,7 +417,7 @@ def main():
     clk = clocks.stop()
     info = s.step_info()
     value = world * N * K / (ms * 1e-3)
-    hbm, alu = roofline_of(prof, N, 8, hbm_peak, peak_kind, True)
+    hbm, alu = roofline_of(prof, N, 8, hbm_peak, peak_kind, True, fma)
     launches = sum(c for c, _ in prof.values())
     kernels = {k: {"launches": c, "total_ms": t, "avg_ms": (t / c if c else 0.0)}
                for k, (c, t) in prof.items()}
@@ -571,7 +594,27 @@ def main():
                     paper_scheme[key]["roofline"] = {
                         "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GINST,
                         "unit": "G FP64-lane-inst/s", "frac": ach / FP64_PEAK_GINST,
-                        "kernel": "rk_stage_weno_kernel"}
+                        "kernel": "rk_stage_weno_kernel", **fp64_peak_keys(ach, fma)}
+                if prec == m.MHD_FP32 and divb == m.MHD_DIVB_GLM:
+                    # issue roofline (warp-instructions) and HBM fraction of
+                    # the FP32 WENO-Z stage kernel
+                    ms_k = sum(profw[c][1] for c in WORDS_STAGE_RK3)
+                    if WENO_FP32_WARP_INST_PER_CELL:
+                        winst = sum(pw.ncell * WENO_FP32_WARP_INST_PER_CELL[c] * profw[c][0]
+                                    for c in WENO_FP32_WARP_INST_PER_CELL)
+                        ach = winst / (ms_k * 1e-3) / 1e9
+                        paper_scheme[key]["roofline_issue"] = {
+                            "bound": "alu", "achieved": ach, "peak": ISSUE_PEAK_GINST,
+                            "unit": "G warp-inst/s", "frac": ach / ISSUE_PEAK_GINST,
+                            "kernel": "rk_stage_weno_kernel",
+                            "warp_inst_per_cell": WENO_FP32_WARP_INST_PER_CELL}
+                    nbytes = pw.ncell * 4 * sum(WORDS_STAGE_RK3[c] * profw[c][0]
+                                                for c in WORDS_STAGE_RK3)
+                    achb = nbytes / (ms_k * 1e-3) / 1e9
+                    paper_scheme[key]["roofline"] = {
+                        "bound": "hbm", "achieved": achb, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": achb / hbm_peak, "kernel": "rk_stage_weno_kernel",
+                        "peak_source": peak_kind}
                 launches += sum(c for c, _ in profw.values())
                 if divb == m.MHD_DIVB_CT:  # edge, face and cell kernels per stage record
                     launches += 2 * profw["ct"][0]

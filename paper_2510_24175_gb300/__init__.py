@@ -45,7 +45,7 @@ EXPORTED = ["mhd_config_default", "mhd_workspace_bytes", "mhd_create", "mhd_set_
             "mhd_ensemble_workspace_bytes", "mhd_ensemble_create", "mhd_ensemble_set_state",
             "mhd_ensemble_get_state", "mhd_ensemble_step", "mhd_ensemble_info",
             "mhd_ensemble_autotune", "mhd_ensemble_set_tiles", "mhd_ensemble_last_error",
-            "mhd_ensemble_destroy"]
+            "mhd_ensemble_destroy", "mhd_fp64_fma_rate"]
 
 
 class MHDError(RuntimeError):
@@ -98,6 +98,7 @@ def lib():
         L.mhd_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
         L.mhd_conserved_sums.argtypes = [vp, dp]
         L.mhd_flux_batch.argtypes = [vp, vp, vp, ctypes.c_longlong, i, d, d, i, vp]
+        L.mhd_fp64_fma_rate.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.mhd_adjoint_step.argtypes = [vp, vp, vp, vp, d, d]
         L.mhd_adjoint_step_stage1.argtypes = [vp, vp, vp, vp, vp, d, d]
         L.mhd_get_stage1.argtypes = [vp, vp, i]
@@ -303,6 +304,15 @@ def mhd_flux_batch(VL, VR, F, direction: int, ch: float, gamma: float):
         assert t.is_cuda and t.is_contiguous() and t.shape[0] == 9 and t.dtype == VL.dtype
     _check(lib().mhd_flux_batch(_ptr(VL), _ptr(VR), _ptr(F), VL.shape[1], direction, ch, gamma,
                                 prec, _stream_ptr()), what="mhd_flux_batch")
+
+
+def mhd_fp64_fma_rate() -> dict:
+    """Measured FP64 fused multiply-add throughput of the current device, on
+    the current stream: lane-FMAs per second, per clock per SM, and the
+    timed launch's milliseconds."""
+    out = (ctypes.c_double * 3)()
+    _check(lib().mhd_fp64_fma_rate(_stream_ptr(), out), what="mhd_fp64_fma_rate")
+    return {"lane_fma_per_s": out[0], "lanes_per_clk_per_sm": out[1], "ms": out[2]}
 
 
 # ----------------------------------------------------------------- wrapper --

@@ -459,4 +459,60 @@ template cudaError_t launch_flux_batch<double>(const double*, const double*, dou
 template cudaError_t launch_flux_batch<float>(const float*, const float*, float*, long long, int,
                                               double, double, cudaStream_t);
 
+// FP64 throughput probe: every thread of the 8 warps runs 16 independent
+// fused multiply-add chains (a <- a b + c) for `iters` rounds.  The chains
+// converge to c / (1 - b) and stay finite; the sums are stored so that no
+// chain is dead code.
+__global__ void __launch_bounds__(256, 1) fma_rate_kernel(double* out, int iters) {
+  double a[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = 1.0 + 1e-9 * (threadIdx.x + i);
+  const double b = 0.999999999, c = 1e-12;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = fma(a[i], b, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) s += a[i];
+  out[blockIdx.x * 256 + threadIdx.x] = s;
+}
+
+cudaError_t measure_fma_rate(cudaStream_t stream, double out[3]) {
+  int dev = 0, nsm = 0, khz = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+  if (e != cudaSuccess) return e;
+  double* buf = nullptr;
+  e = cudaMalloc(&buf, (size_t)nsm * 256 * sizeof(double));
+  if (e != cudaSuccess) return e;
+  // one CTA per SM: its shared-memory request leaves no room for a second
+  const int smem = 160 * 1024;
+  const int iters = 20000;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaFuncSetAttribute(fma_rate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) {
+    fma_rate_kernel<<<nsm, 256, smem, stream>>>(buf, iters / 10);  // warm-up
+    cudaEventRecord(e0, stream);
+    fma_rate_kernel<<<nsm, 256, smem, stream>>>(buf, iters);
+    cudaEventRecord(e1, stream);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  }
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (e != cudaSuccess) return e;
+  const double lanes = (double)nsm * 256.0 * iters * 16.0;
+  out[0] = lanes / (ms * 1e-3);
+  out[1] = out[0] / nsm / (khz * 1e3);
+  out[2] = ms;
+  return cudaSuccess;
+}
+
 }  // namespace mhd

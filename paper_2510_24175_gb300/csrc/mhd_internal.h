@@ -151,4 +151,8 @@ template <class T>
 cudaError_t launch_flux_batch(const T* VL, const T* VR, T* F, long long nface, int dir,
                               double ch, double gamma, cudaStream_t stream);
 
+// Measured FP64 fused multiply-add throughput of the current device (see
+// mhd_fp64_fma_rate).
+cudaError_t measure_fma_rate(cudaStream_t stream, double out[3]);
+
 }  // namespace mhd

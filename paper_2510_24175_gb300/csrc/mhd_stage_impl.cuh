@@ -7,15 +7,18 @@
 
 namespace mhd {
 
-// Tile shapes: 3-D grids use 32 x 8 column tiles marching in z; FP64 runs 13
-// warps per CTA (one CTA per SM: 201 KB of shared memory), which makes the
-// 26 warp-sized flux work items and the 416 loaded halo cells of a plane
-// divide evenly; FP32 runs 8 warps and two CTAs per SM.  2-D grids use the
-// same tile with a single plane; 1-D grids a 32-cell row.
+// Tile shapes: 3-D grids use 32 x 8 column tiles marching in z.  FP64 runs
+// 16 warps per CTA (one CTA per SM: 201 KB of shared memory): the SM's FP64
+// unit is shared by all its warps and one warp issues an FP64 instruction at
+// most every 64 clocks, so the unit saturates only when at least four warps
+// have FP64 work; 16 warps (8 helper warps, 8 column owners) keep more warps
+// busy through the phases than 13 and cap registers at 128 as 13 do (four
+// warps per scheduler).  FP32 runs 8 warps and two CTAs per SM.  2-D grids
+// use the same tile with a single plane; 1-D grids a 32-cell row.
 template <class T>
 struct StageShape3D {
   static constexpr int TY = 8;
-  static constexpr int NW = sizeof(T) == 8 ? 13 : 8;
+  static constexpr int NW = sizeof(T) == 8 ? 16 : 8;
 };
 
 // The dynamic shared-memory limit of a kernel is set once per device (a

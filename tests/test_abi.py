@@ -79,6 +79,13 @@ def test_flux_batch_rejects_bad_arguments(built_lib):
     assert L.mhd_flux_batch(None, None, None, 10, 0, 1.0, 5 / 3, 0, None) == m.MHD_ERR_INVALID
 
 
+def test_fma_rate_probe_rejects_a_null_output(built_lib):
+    import paper_2510_24175_gb300 as m
+    L = m.lib()
+    assert L.mhd_fp64_fma_rate(None, None) == m.MHD_ERR_INVALID
+    assert L.mhd_last_error(None) == b"mhd_fp64_fma_rate: out is NULL"
+
+
 def test_context_free_failures_leave_a_message(built_lib):
     """Calls without a context (configuration checks, flux batch, ensemble
     sizing) leave the reason of a failure for mhd_last_error(NULL), per host
