@@ -397,15 +397,16 @@ int mhd_ensemble_destroy(mhd_ensemble* ens);
 /* ---- Diagnostics ----------------------------------------------------------
  * Measured FP64 throughput of the current device, the denominator of the
  * FP64 stage kernels' roofline (their bound is the SM's FP64 unit, not HBM):
- * one CTA of 8 warps per SM, every thread running 16 independent fused
- * multiply-add chains, timed with CUDA events on `stream` (NULL: the legacy
- * default stream) after one warm-up launch.  out[0] = lane-FMAs per second
- * over the device, out[1] = lane-FMAs per clock per SM at the clock rate the
- * device reports, out[2] = milliseconds of the timed launch.  Allocates and
- * frees (SM count x 256) doubles of device memory; synchronises with the
- * stream.  Errors: MHD_ERR_INVALID (out NULL), MHD_ERR_CUDA (message in
- * mhd_last_error(NULL)). */
-int mhd_fp64_fma_rate(void* stream, double out[3]);
+ * one CTA of 8 warps per SM; every thread of the warps that warp_mask selects
+ * (bit w: warp w; warp w runs on scheduler w mod 4; 0 or 0xff: all 8) runs 16
+ * independent fused multiply-add chains, timed with CUDA events on `stream`
+ * (NULL: the legacy default stream) after one warm-up launch.  out[0] =
+ * lane-FMAs per second over the device, out[1] = lane-FMAs per clock per SM
+ * at the clock rate the device reports, out[2] = milliseconds of the timed
+ * launch.  Allocates and frees (SM count x 256) doubles of device memory;
+ * synchronises with the stream.  Errors: MHD_ERR_INVALID (out NULL),
+ * MHD_ERR_CUDA (message in mhd_last_error(NULL)). */
+int mhd_fp64_fma_rate(void* stream, unsigned warp_mask, double out[3]);
 
 /* Message of the last failing call on ctx (never NULL).  ctx = NULL: the
  * message of the calling host thread's last failing call that has no context

@@ -98,7 +98,7 @@ def lib():
         L.mhd_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
         L.mhd_conserved_sums.argtypes = [vp, dp]
         L.mhd_flux_batch.argtypes = [vp, vp, vp, ctypes.c_longlong, i, d, d, i, vp]
-        L.mhd_fp64_fma_rate.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        L.mhd_fp64_fma_rate.argtypes = [vp, ctypes.c_uint, ctypes.POINTER(ctypes.c_double)]
         L.mhd_adjoint_step.argtypes = [vp, vp, vp, vp, d, d]
         L.mhd_adjoint_step_stage1.argtypes = [vp, vp, vp, vp, vp, d, d]
         L.mhd_get_stage1.argtypes = [vp, vp, i]
@@ -306,12 +306,13 @@ def mhd_flux_batch(VL, VR, F, direction: int, ch: float, gamma: float):
                                 prec, _stream_ptr()), what="mhd_flux_batch")
 
 
-def mhd_fp64_fma_rate() -> dict:
+def mhd_fp64_fma_rate(warp_mask: int = 0xFF) -> dict:
     """Measured FP64 fused multiply-add throughput of the current device, on
-    the current stream: lane-FMAs per second, per clock per SM, and the
-    timed launch's milliseconds."""
+    the current stream, with the warps of warp_mask (of 8 per SM) running:
+    lane-FMAs per second, per clock per SM, and the timed launch's
+    milliseconds."""
     out = (ctypes.c_double * 3)()
-    _check(lib().mhd_fp64_fma_rate(_stream_ptr(), out), what="mhd_fp64_fma_rate")
+    _check(lib().mhd_fp64_fma_rate(_stream_ptr(), warp_mask, out), what="mhd_fp64_fma_rate")
     return {"lane_fma_per_s": out[0], "lanes_per_clk_per_sm": out[1], "ms": out[2]}
 
 

@@ -80,12 +80,16 @@ __global__ void __launch_bounds__(128) adj_faces_kernel(const double* __restrict
 #pragma unroll
       for (int k = 0; k < kNV; ++k) V[q][k] = Wp[k * a.sv + off[q]];
     }
-    // slopes of cells f-1 (a) and f (b) with their derivatives
-    double sa[kNV], sb[kNV], dma[kNV], dpa[kNV], dmb[kNV], dpb[kNV];
+    // slopes of cells f-1 (a) and f (b) with their derivative codes (bits
+    // 6k..6k+2: cell a, 6k+3..6k+5: cell b of variable k)
+    double sa[kNV], sb[kNV];
+    unsigned long long codes = 0ull;
 #pragma unroll
     for (int k = 0; k < kNV; ++k) {
-      sa[k] = limited_slope_d(V[1][k] - V[0][k], V[2][k] - V[1][k], a.limiter, dma[k], dpa[k]);
-      sb[k] = limited_slope_d(V[2][k] - V[1][k], V[3][k] - V[2][k], a.limiter, dmb[k], dpb[k]);
+      unsigned ca, cb;
+      sa[k] = limited_slope_c(V[1][k] - V[0][k], V[2][k] - V[1][k], a.limiter, ca);
+      sb[k] = limited_slope_c(V[2][k] - V[1][k], V[3][k] - V[2][k], a.limiter, cb);
+      codes |= (unsigned long long)(ca | (cb << 3)) << (6 * k);
     }
     const bool oka = gt0(V[1][kRHO] - 0.5 * fabs(sa[kRHO])) &&
                      gt0(V[1][kPRS] - 0.5 * fabs(sa[kPRS]));
@@ -117,12 +121,16 @@ __global__ void __launch_bounds__(128) adj_faces_kernel(const double* __restrict
     // PLM: vl = V_a + s_a/2, vr = V_b - s_b/2, s = lim(V_c - V_{c-1}, V_{c+1} - V_c)
 #pragma unroll
     for (int k = 0; k < kNV; ++k) {
+      const unsigned ck = (unsigned)(codes >> (6 * k));
+      double dma, dpa, dmb, dpb;
+      slope_code_d(ck & 7u, dma, dpa);
+      slope_code_d((ck >> 3) & 7u, dmb, dpb);
       const double ga = oka ? 0.5 * vlb[k] : 0.0;   // dJ/ds_a
       const double gb = okb ? -0.5 * vrb[k] : 0.0;  // dJ/ds_b
-      const double g0 = -dma[k] * ga;
-      const double g1 = vlb[k] + (dma[k] - dpa[k]) * ga - dmb[k] * gb;
-      const double g2 = dpa[k] * ga + vrb[k] + (dmb[k] - dpb[k]) * gb;
-      const double g3 = dpb[k] * gb;
+      const double g0 = -dma * ga;
+      const double g1 = vlb[k] + (dma - dpa) * ga - dmb * gb;
+      const double g2 = dpa * ga + vrb[k] + (dmb - dpb) * gb;
+      const double g3 = dpb * gb;
       // (zero tests on the integer pipe)
       if (nonzero(g0)) atomicAdd(&gV[k * a.sv + off[0]], g0);
       if (nonzero(g1)) atomicAdd(&gV[k * a.sv + off[1]], g1);

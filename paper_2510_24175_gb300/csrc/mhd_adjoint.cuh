@@ -37,36 +37,46 @@ MHD_HD void zero_bar(SideBar<T>& b) {
   b.vs = b.ws = b.bys = b.bzs = b.vb = b.vbs = b.es = b.sq = T(0);
 }
 
-// Outer-state forward (same arithmetic as glm_hlld_flux).
+// Outer-state forward: total field, total pressure, energy and gamma p.  The
+// reciprocal of rho is formed for both sides at once by the caller (one
+// reciprocal of rho_L rho_R, as glm_hlld_flux does).
 template <class T>
 MHD_HD void side_outer(Side<T>& s, T bx2, const Phys<T>& ph) {
   const T half = T(0.5);
   s.b2 = bx2 + s.by * s.by + s.bz * s.bz;
   s.pt = s.p + half * s.b2;
   s.e = s.p * ph.gm1i + half * s.r * (s.u * s.u + s.v * s.v + s.w * s.w) + half * s.b2;
-  s.ri = rcp(s.r);
   s.gp = ph.gamma * s.p;
+}
+
+// Square of the fast speed, (a + sqrt(a^2 - 4 gp bx2 / rho^2)) / 2, with the
+// reciprocal square root of the discriminant the reverse needs (sd = disc /
+// sqrt(disc)); a clamped discriminant gives sd = 0.  Needs s.ri.  The root of
+// the square itself is taken only for the faster side, the one c_max uses.
+template <class T>
+MHD_HD T side_c2(Side<T>& s, T bx2) {
   s.a = (s.gp + s.b2) * s.ri;
   const T disc = s.a * s.a - T(4) * s.gp * bx2 * (s.ri * s.ri);
-  // sqrt and the reciprocals the reverse needs from reciprocal square roots
-  // (sd = disc / sqrt(disc), cf likewise); a clamped discriminant gives sd = 0
   s.clamp = !gt0(disc);
   s.disc = s.clamp ? T(0) : disc;
   s.isd = trsqrt(s.disc);
   s.sd = s.clamp ? T(0) : s.disc * s.isd;
-  const T c2 = half * (s.a + s.sd);
-  s.icf = trsqrt(c2);
-  s.cf = c2 * s.icf;
+  return T(0.5) * (s.a + s.sd);
+}
+
+// Single-star state, first part: S - S_M, the denominator and the
+// degeneracy test.  The caller forms 1 / (S - S_M) and 1 / den of both sides
+// from one reciprocal (as glm_hlld_flux does) and sets s.smi, s.deni.
+template <class T>
+MHD_HD void side_star_den(Side<T>& s, T bx2, T SM, T pts) {
+  s.sm = s.S - SM;
+  s.den = s.d * s.sm - bx2;
+  s.deg = abs_lt(s.den, T(1e-8) * pts);
 }
 
 template <class T>
 MHD_HD void side_star(Side<T>& s, T bx, T bx2, T SM, T pts) {
-  s.sm = s.S - SM;
-  s.smi = rcp(s.sm);
   s.rs = s.d * s.smi;
-  s.den = s.d * s.sm - bx2;
-  s.deg = abs_lt(s.den, T(1e-8) * pts);
-  s.deni = rcp(s.deg ? T(1) : s.den);
   s.fv = bx * (SM - s.u) * s.deni;
   s.fb = (s.d * (s.S - s.u) - bx2) * s.deni;
   s.vs = s.deg ? s.v : s.v - s.by * s.fv;
@@ -220,9 +230,21 @@ MHD_HD void glm_hlld_flux_vjp(const T vl[kNV], const T vr[kNV], int dir, T ch, T
   const T bx2 = bx * bx;
   side_outer(L, bx2, ph);
   side_outer(R, bx2, ph);
+  // 1/rho of both sides from one reciprocal
+  const T qr = rcp(L.r * R.r);
+  L.ri = R.r * qr;
+  R.ri = L.r * qr;
+  const T c2L = side_c2(L, bx2), c2R = side_c2(R, bx2);
   // (comparisons on the integer pipe in FP64: lt_ieee, gt0, lt0, ge0)
-  const bool cfL_max = !lt_ieee(L.cf, R.cf);  // cmax = cfL on ties
-  const T cmax = cfL_max ? L.cf : R.cf;
+  const bool cfL_max = !lt_ieee(c2L, c2R);  // cmax = cfL on ties (sqrt is monotone)
+  // c_max = sqrt(max(c2L, c2R)); only that side's fast speed has an adjoint,
+  // the other side's 1/cf is zero
+  const T icf = trsqrt(cfL_max ? c2L : c2R);
+  const T cmax = (cfL_max ? c2L : c2R) * icf;
+  L.cf = cfL_max ? cmax : T(0);
+  L.icf = cfL_max ? icf : T(0);
+  R.cf = cfL_max ? T(0) : cmax;
+  R.icf = cfL_max ? T(0) : icf;
   const bool uL_min = !lt_ieee(R.u, L.u);     // min(uL, uR) picks uL on ties
   const bool uL_max = !lt_ieee(L.u, R.u);     // max(uL, uR) picks uL on ties
   L.S = (uL_min ? L.u : R.u) - cmax;
@@ -234,25 +256,59 @@ MHD_HD void glm_hlld_flux_vjp(const T vl[kNV], const T vr[kNV], int dir, T ch, T
   const T SM = Ns * Di;
   const T Np = R.d * L.pt - L.d * R.pt + L.d * R.d * (R.u - L.u);
   const T pts = Np * Di;
+  // 1/(S - S_M) and 1/den of both sides from one reciprocal
+  side_star_den(L, bx2, SM, pts);
+  side_star_den(R, bx2, SM, pts);
+  {
+    const T dnL = L.deg ? T(1) : L.den, dnR = R.deg ? T(1) : R.den;
+    const T ps = L.sm * R.sm, pd = dnL * dnR;
+    const T q4 = rcp(ps * pd);
+    const T qs = pd * q4, qd = ps * q4;
+    L.smi = R.sm * qs;
+    R.smi = L.sm * qs;
+    L.deni = dnR * qd;
+    R.deni = dnL * qd;
+  }
   side_star(L, bx, bx2, SM, pts);
   side_star(R, bx, bx2, SM, pts);
-  const T iqL = trsqrt(L.rs), iqR = trsqrt(R.rs);
-  L.sq = L.rs * iqL;
-  R.sq = R.rs * iqR;
   const T abx = tabs(bx);
-  const T SLs = SM - abx * iqL;
-  const T SRs = SM + abx * iqR;
   const T sg = ge0(bx) ? T(1) : T(-1);
-  const T isum = rcp(L.sq + R.sq);
-  const T Nv = L.sq * L.vs + R.sq * R.vs + (R.bys - L.bys) * sg;
-  const T Nw = L.sq * L.ws + R.sq * R.ws + (R.bzs - L.bzs) * sg;
-  const T Nby = L.sq * R.bys + R.sq * L.bys + L.sq * R.sq * (R.vs - L.vs) * sg;
-  const T Nbz = L.sq * R.bzs + R.sq * L.bzs + L.sq * R.sq * (R.ws - L.ws) * sg;
-  const T vss = Nv * isum, wss = Nw * isum, byss = Nby * isum, bzss = Nbz * isum;
-  const T vbss = SM * bx + vss * byss + wss * bzss;
   const bool sup = gt0(L.S) || lt0(R.S);
   const bool useL = gt0(L.S) || (!lt0(R.S) && ge0(SM));
-  const bool inner = !sup && (useL ? !gt0(SLs) : !lt0(SRs));
+  // inside the Alfven fan: decided by the selected side's Alfven speed
+  const T iqa = trsqrt(useL ? L.rs : R.rs);
+  const bool inner = !sup && (useL ? !gt0(SM - abx * iqa) : !lt0(SM + abx * iqa));
+  // The double-star states enter only inside the fan (c2 != 0).  Where no
+  // lane of the warp is inside, they and their reverse are skipped: their
+  // adjoints would all be zero.
+#ifdef __CUDA_ARCH__
+  const bool fan = __any_sync(__activemask(), inner);
+#else
+  const bool fan = inner;
+#endif
+  T iqL = T(0), iqR = T(0), SLs = T(0), SRs = T(0), isum = T(0);
+  T Nv = T(0), Nw = T(0), Nby = T(0), Nbz = T(0);
+  T vss = T(0), wss = T(0), byss = T(0), bzss = T(0), vbss = T(0);
+  L.sq = R.sq = T(0);
+  if (fan) {
+    const T iqo = trsqrt(useL ? R.rs : L.rs);
+    iqL = useL ? iqa : iqo;
+    iqR = useL ? iqo : iqa;
+    L.sq = L.rs * iqL;
+    R.sq = R.rs * iqR;
+    SLs = SM - abx * iqL;
+    SRs = SM + abx * iqR;
+    isum = rcp(L.sq + R.sq);
+    Nv = L.sq * L.vs + R.sq * R.vs + (R.bys - L.bys) * sg;
+    Nw = L.sq * L.ws + R.sq * R.ws + (R.bzs - L.bzs) * sg;
+    Nby = L.sq * R.bys + R.sq * L.bys + L.sq * R.sq * (R.vs - L.vs) * sg;
+    Nbz = L.sq * R.bzs + R.sq * L.bzs + L.sq * R.sq * (R.ws - L.ws) * sg;
+    vss = Nv * isum;
+    wss = Nw * isum;
+    byss = Nby * isum;
+    bzss = Nbz * isum;
+    vbss = SM * bx + vss * byss + wss * bzss;
+  }
   // selected side a
   const T r = useL ? L.r : R.r, u = useL ? L.u : R.u, v = useL ? L.v : R.v;
   const T w = useL ? L.w : R.w, by = useL ? L.by : R.by, bz = useL ? L.bz : R.bz;
@@ -394,71 +450,73 @@ MHD_HD void glm_hlld_flux_vjp(const T vl[kNV], const T vr[kNV], int dir, T ch, T
   if (useL) Lb.sq -= sqb; else Rb.sq += sqb;
   Lb.S += SLb;
   Rb.S += SRb;
-  // vbss = SM bx + vss byss + wss bzss
-  SMb += vbssb * bx;
-  bxb += vbssb * SM;
-  vssb += vbssb * byss;
-  byssb += vbssb * vss;
-  wssb += vbssb * bzss;
-  bzssb += vbssb * wss;
-  // byss = Nby isum, Nby = sqL bysR + sqR bysL + sqL sqR (vsR - vsL) sg
-  T isumb = 0;
-  {
-    const T nb = byssb * isum;
-    isumb += byssb * Nby;
-    Lb.sq += nb * (R.bys + R.sq * (R.vs - L.vs) * sg);
-    Rb.sq += nb * (L.bys + L.sq * (R.vs - L.vs) * sg);
-    Rb.bys += nb * L.sq;
-    Lb.bys += nb * R.sq;
-    Rb.vs += nb * L.sq * R.sq * sg;
-    Lb.vs -= nb * L.sq * R.sq * sg;
+  if (fan) {  // the double-star states (all their adjoints are zero otherwise)
+    // vbss = SM bx + vss byss + wss bzss
+    SMb += vbssb * bx;
+    bxb += vbssb * SM;
+    vssb += vbssb * byss;
+    byssb += vbssb * vss;
+    wssb += vbssb * bzss;
+    bzssb += vbssb * wss;
+    // byss = Nby isum, Nby = sqL bysR + sqR bysL + sqL sqR (vsR - vsL) sg
+    T isumb = 0;
+    {
+      const T nb = byssb * isum;
+      isumb += byssb * Nby;
+      Lb.sq += nb * (R.bys + R.sq * (R.vs - L.vs) * sg);
+      Rb.sq += nb * (L.bys + L.sq * (R.vs - L.vs) * sg);
+      Rb.bys += nb * L.sq;
+      Lb.bys += nb * R.sq;
+      Rb.vs += nb * L.sq * R.sq * sg;
+      Lb.vs -= nb * L.sq * R.sq * sg;
+    }
+    {
+      const T nb = bzssb * isum;
+      isumb += bzssb * Nbz;
+      Lb.sq += nb * (R.bzs + R.sq * (R.ws - L.ws) * sg);
+      Rb.sq += nb * (L.bzs + L.sq * (R.ws - L.ws) * sg);
+      Rb.bzs += nb * L.sq;
+      Lb.bzs += nb * R.sq;
+      Rb.ws += nb * L.sq * R.sq * sg;
+      Lb.ws -= nb * L.sq * R.sq * sg;
+    }
+    // vss = Nv isum, Nv = sqL vsL + sqR vsR + (bysR - bysL) sg
+    {
+      const T nb = vssb * isum;
+      isumb += vssb * Nv;
+      Lb.sq += nb * L.vs;
+      Lb.vs += nb * L.sq;
+      Rb.sq += nb * R.vs;
+      Rb.vs += nb * R.sq;
+      Rb.bys += nb * sg;
+      Lb.bys -= nb * sg;
+    }
+    {
+      const T nb = wssb * isum;
+      isumb += wssb * Nw;
+      Lb.sq += nb * L.ws;
+      Lb.ws += nb * L.sq;
+      Rb.sq += nb * R.ws;
+      Rb.ws += nb * R.sq;
+      Rb.bzs += nb * sg;
+      Lb.bzs -= nb * sg;
+    }
+    // isum = 1 / (sqL + sqR)
+    Lb.sq -= isumb * isum * isum;
+    Rb.sq -= isumb * isum * isum;
+    // SLs = SM - abx iqL; SRs = SM + abx iqR; iq = 1 / sq
+    T abxb = 0;
+    SMb += SLsb + SRsb;
+    abxb -= SLsb * iqL;
+    abxb += SRsb * iqR;
+    Lb.sq += SLsb * abx * iqL * iqL;
+    Rb.sq -= SRsb * abx * iqR * iqR;
+    // abx = |bx| (derivative sign(bx), +1 at 0)
+    bxb += abxb * sg;
+    // sq = sqrt(rs)
+    Lb.rs += Lb.sq * half * iqL;
+    Rb.rs += Rb.sq * half * iqR;
   }
-  {
-    const T nb = bzssb * isum;
-    isumb += bzssb * Nbz;
-    Lb.sq += nb * (R.bzs + R.sq * (R.ws - L.ws) * sg);
-    Rb.sq += nb * (L.bzs + L.sq * (R.ws - L.ws) * sg);
-    Rb.bzs += nb * L.sq;
-    Lb.bzs += nb * R.sq;
-    Rb.ws += nb * L.sq * R.sq * sg;
-    Lb.ws -= nb * L.sq * R.sq * sg;
-  }
-  // vss = Nv isum, Nv = sqL vsL + sqR vsR + (bysR - bysL) sg
-  {
-    const T nb = vssb * isum;
-    isumb += vssb * Nv;
-    Lb.sq += nb * L.vs;
-    Lb.vs += nb * L.sq;
-    Rb.sq += nb * R.vs;
-    Rb.vs += nb * R.sq;
-    Rb.bys += nb * sg;
-    Lb.bys -= nb * sg;
-  }
-  {
-    const T nb = wssb * isum;
-    isumb += wssb * Nw;
-    Lb.sq += nb * L.ws;
-    Lb.ws += nb * L.sq;
-    Rb.sq += nb * R.ws;
-    Rb.ws += nb * R.sq;
-    Rb.bzs += nb * sg;
-    Lb.bzs -= nb * sg;
-  }
-  // isum = 1 / (sqL + sqR)
-  Lb.sq -= isumb * isum * isum;
-  Rb.sq -= isumb * isum * isum;
-  // SLs = SM - abx iqL; SRs = SM + abx iqR; iq = 1 / sq
-  T abxb = 0;
-  SMb += SLsb + SRsb;
-  abxb -= SLsb * iqL;
-  abxb += SRsb * iqR;
-  Lb.sq += SLsb * abx * iqL * iqL;
-  Rb.sq -= SRsb * abx * iqR * iqR;
-  // abx = |bx| (derivative sign(bx), +1 at 0)
-  bxb += abxb * sg;
-  // sq = sqrt(rs)
-  Lb.rs += Lb.sq * half * iqL;
-  Rb.rs += Rb.sq * half * iqR;
   // single-star states
   side_star_bar(L, Lb, bx, bx2, SM, pts, bxb, bx2b, SMb, ptsb);
   side_star_bar(R, Rb, bx, bx2, SM, pts, bxb, bx2b, SMb, ptsb);
@@ -556,36 +614,54 @@ MHD_HD T limited_slope_d(T dm, T dp, int lim, T& ddm, T& ddp) {
   return s;
 }
 
-// FP64: the same values from the bit patterns, as limited_slope<double>: the
-// zero test, the minmod choice, the MC doubling / halving and the MC
-// decision on the integer pipe; |dm| + |dp| is the only FP64 operation.
-template <>
-MHD_HD double limited_slope_d<double>(double dm, double dp, int lim, double& ddm, double& ddp) {
-  ddm = 0.0;
-  ddp = 0.0;
+// Derivative code of a limited slope, which is piecewise linear in the
+// one-sided differences dm, dp: bits 0-1 the piece -- 0 zero slope, 1 the
+// smaller-magnitude difference (minmod), 2 twice it (MC), 3 the central slope
+// (dm + dp) / 2 (MC) -- and bit 2 set when the one-sided difference is dm.
+// Three bits instead of two doubles keep the 18 derivatives of a face's two
+// slopes in one register pair through the flux reverse.
+MHD_HD void slope_code_d(unsigned code, double& ddm, double& ddp) {
+  const unsigned piece = code & 3u;
+  const bool m = (code >> 2) & 1u;
+  const double f = piece == 1u ? 1.0 : 2.0;
+  ddm = piece == 0u ? 0.0 : (piece == 3u ? 0.5 : (m ? f : 0.0));
+  ddp = piece == 0u ? 0.0 : (piece == 3u ? 0.5 : (m ? 0.0 : f));
+}
+
+// FP64: the limited slope from the bit patterns, as limited_slope<double>,
+// with its derivative code: the zero test, the minmod choice, the MC doubling
+// / halving and the MC decision on the integer pipe; |dm| + |dp| is the only
+// FP64 operation.
+MHD_HD double limited_slope_c(double dm, double dp, int lim, unsigned& code) {
+  code = 0u;
   const long long a = dbits(dm), b = dbits(dp);
   const long long mask = 0x7fffffffffffffffll;
   const long long am = a & mask, bm = b & mask;
   if (lim == kLimFlat || (a ^ b) < 0 || am == 0 || bm == 0) return 0.0;
   const bool m_is_dm = !(bm < am);  // the smaller magnitude; dm on ties
   long long mb = m_is_dm ? am : bm;
-  double gdm = m_is_dm ? 1.0 : 0.0, gdp = m_is_dm ? 0.0 : 1.0;
+  unsigned piece = 1u;
   if (lim == kLimMC) {
     const long long two = twice_bits(mb);
     const long long cen = half_bits(dbits(bits2d(am) + bits2d(bm)));
     if (cen < two) {  // central slope selected
       mb = cen;
-      gdm = 0.5;
-      gdp = 0.5;
+      piece = 3u;
     } else {
       mb = two;
-      gdm = m_is_dm ? 2.0 : 0.0;
-      gdp = m_is_dm ? 0.0 : 2.0;
+      piece = 2u;
     }
   }
-  ddm = gdm;
-  ddp = gdp;
+  code = piece | (m_is_dm ? 4u : 0u);
   return bits2d(mb | (a & ~mask));
+}
+
+template <>
+MHD_HD double limited_slope_d<double>(double dm, double dp, int lim, double& ddm, double& ddp) {
+  unsigned code;
+  const double s = limited_slope_c(dm, dp, lim, code);
+  slope_code_d(code, ddm, ddp);
+  return s;
 }
 
 // Reverse of cons_to_prim (floors inactive: a floored value has zero

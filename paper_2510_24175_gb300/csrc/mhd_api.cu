@@ -1071,9 +1071,10 @@ int mhd_flux_batch(const void* VL, const void* VR, void* F, long long nface, int
   return MHD_OK;
 }
 
-int mhd_fp64_fma_rate(void* stream, double out[3]) {
+int mhd_fp64_fma_rate(void* stream, unsigned warp_mask, double out[3]) {
   if (!out) return mhd::free_fail(MHD_ERR_INVALID, "mhd_fp64_fma_rate: out is NULL");
-  const cudaError_t e = mhd::measure_fma_rate(static_cast<cudaStream_t>(stream), out);
+  const cudaError_t e =
+      mhd::measure_fma_rate(static_cast<cudaStream_t>(stream), warp_mask, out);
   if (e != cudaSuccess)
     return mhd::free_fail(MHD_ERR_CUDA, "mhd_fp64_fma_rate: %s", cudaGetErrorString(e));
   return MHD_OK;

@@ -459,16 +459,18 @@ template cudaError_t launch_flux_batch<double>(const double*, const double*, dou
 template cudaError_t launch_flux_batch<float>(const float*, const float*, float*, long long, int,
                                               double, double, cudaStream_t);
 
-// FP64 throughput probe: every thread of the 8 warps runs 16 independent
-// fused multiply-add chains (a <- a b + c) for `iters` rounds.  The chains
-// converge to c / (1 - b) and stay finite; the sums are stored so that no
-// chain is dead code.
-__global__ void __launch_bounds__(256, 1) fma_rate_kernel(double* out, int iters) {
+// FP64 throughput probe: every thread of the warps selected by warp_mask
+// (bit w: warp w of the 8) runs 16 independent fused multiply-add chains
+// (a <- a b + c) for `iters` rounds.  The chains converge to c / (1 - b) and
+// stay finite; the sums are stored so that no chain is dead code.
+__global__ void __launch_bounds__(256, 1) fma_rate_kernel(double* out, int iters,
+                                                          unsigned warp_mask) {
   double a[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) a[i] = 1.0 + 1e-9 * (threadIdx.x + i);
   const double b = 0.999999999, c = 1e-12;
-  for (int it = 0; it < iters; ++it) {
+  const int n = (warp_mask >> (threadIdx.x >> 5)) & 1u ? iters : 0;
+  for (int it = 0; it < n; ++it) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) a[i] = fma(a[i], b, c);
   }
@@ -478,7 +480,9 @@ __global__ void __launch_bounds__(256, 1) fma_rate_kernel(double* out, int iters
   out[blockIdx.x * 256 + threadIdx.x] = s;
 }
 
-cudaError_t measure_fma_rate(cudaStream_t stream, double out[3]) {
+cudaError_t measure_fma_rate(cudaStream_t stream, unsigned warp_mask, double out[3]) {
+  warp_mask &= 0xffu;
+  if (!warp_mask) warp_mask = 0xffu;
   int dev = 0, nsm = 0, khz = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -495,9 +499,9 @@ cudaError_t measure_fma_rate(cudaStream_t stream, double out[3]) {
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e == cudaSuccess) {
-    fma_rate_kernel<<<nsm, 256, smem, stream>>>(buf, iters / 10);  // warm-up
+    fma_rate_kernel<<<nsm, 256, smem, stream>>>(buf, iters / 10, warp_mask);  // warm-up
     cudaEventRecord(e0, stream);
-    fma_rate_kernel<<<nsm, 256, smem, stream>>>(buf, iters);
+    fma_rate_kernel<<<nsm, 256, smem, stream>>>(buf, iters, warp_mask);
     cudaEventRecord(e1, stream);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -508,7 +512,7 @@ cudaError_t measure_fma_rate(cudaStream_t stream, double out[3]) {
   if (e1) cudaEventDestroy(e1);
   cudaFree(buf);
   if (e != cudaSuccess) return e;
-  const double lanes = (double)nsm * 256.0 * iters * 16.0;
+  const double lanes = (double)nsm * 32.0 * __builtin_popcount(warp_mask) * iters * 16.0;
   out[0] = lanes / (ms * 1e-3);
   out[1] = out[0] / nsm / (khz * 1e3);
   out[2] = ms;

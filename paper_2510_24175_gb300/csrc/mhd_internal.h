@@ -153,6 +153,6 @@ cudaError_t launch_flux_batch(const T* VL, const T* VR, T* F, long long nface, i
 
 // Measured FP64 fused multiply-add throughput of the current device (see
 // mhd_fp64_fma_rate).
-cudaError_t measure_fma_rate(cudaStream_t stream, double out[3]);
+cudaError_t measure_fma_rate(cudaStream_t stream, unsigned warp_mask, double out[3]);
 
 }  // namespace mhd

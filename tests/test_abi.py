@@ -82,7 +82,7 @@ def test_flux_batch_rejects_bad_arguments(built_lib):
 def test_fma_rate_probe_rejects_a_null_output(built_lib):
     import paper_2510_24175_gb300 as m
     L = m.lib()
-    assert L.mhd_fp64_fma_rate(None, None) == m.MHD_ERR_INVALID
+    assert L.mhd_fp64_fma_rate(None, 0xFF, None) == m.MHD_ERR_INVALID
     assert L.mhd_last_error(None) == b"mhd_fp64_fma_rate: out is NULL"
 
 

@@ -249,11 +249,13 @@ def test_adjoint_with_kept_stage1_equals_recomputed(pb):
     assert e.value.code == m.MHD_ERR_STATE
 
 
-@pytest.mark.parametrize("k", [1, 3, 8])
+@pytest.mark.parametrize("k", [0, 1, 3, 8])
 def test_rollout_gradient_independent_of_checkpoint_interval(k):
     """The rollout's gradient does not depend on the checkpoint interval k
-    (k = 1: every step recomputes its first stage inside the adjoint; larger
-    k: all but a segment's last step use the kept first stage): the gradient
+    (k = 0: every step's state and first stage kept by the forward pass, no
+    recomputation; k = 1: every step recomputes its first stage inside the
+    adjoint; larger k: all but a segment's last step use the first stage kept
+    by the segment's recomputation): the gradient
     of k = 8 over 8 steps, which recomputes nothing but the last step's first
     stage, up to the order of the adjoint's FP64 atomic accumulation (1e-11
     of the largest component after 8 steps)."""
