@@ -531,6 +531,167 @@ MHD_HD T rot3(int dir, int j, T a, T b, T c) {
   return m == 0 ? a : (m == 1 ? b : c);
 }
 
+#ifdef __CUDA_ARCH__
+// Packed FP32 (FFMA2 / FMUL2 / FADD2: two lanes per instruction, each lane
+// rounded as the scalar instruction).  x - y is fma(y, -1, x): the product is
+// exact, so it rounds once, as a subtraction does.
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 pk1(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 swap2(float2 a) { return make_float2(a.y, a.x); }
+
+// FP32 GLM + HLLD (the same steps as glm_hlld_flux) with the two sides'
+// identical operations -- outer states, fast speeds, single-star states --
+// and the two tangential components' ones -- double-star states, flux
+// terms -- paired in packed instructions: .x the left state (or the first
+// tangential component), .y the right one (or the second).  Every operation
+// is written out (no contraction is left to the compiler), so the flux rounds
+// the same in every kernel it is inlined into.
+template <int dir>
+__device__ __forceinline__ void glm_hlld_flux_f32x2(const float vl[kNV], const float vr[kNV],
+                                                    float ch, float half_chi,
+                                                    const Phys<float>& ph, float F[kNV]) {
+  const float2 H = pk1(0.5f);
+  const float2 u = pk(rot3(dir, 0, vl[kVX], vl[kVY], vl[kVZ]), rot3(dir, 0, vr[kVX], vr[kVY], vr[kVZ]));
+  const float2 v = pk(rot3(dir, 1, vl[kVX], vl[kVY], vl[kVZ]), rot3(dir, 1, vr[kVX], vr[kVY], vr[kVZ]));
+  const float2 w = pk(rot3(dir, 2, vl[kVX], vl[kVY], vl[kVZ]), rot3(dir, 2, vr[kVX], vr[kVY], vr[kVZ]));
+  const float2 by = pk(rot3(dir, 1, vl[kBX], vl[kBY], vl[kBZ]), rot3(dir, 1, vr[kBX], vr[kBY], vr[kBZ]));
+  const float2 bz = pk(rot3(dir, 2, vl[kBX], vl[kBY], vl[kBZ]), rot3(dir, 2, vr[kBX], vr[kBY], vr[kBZ]));
+  const float bnL = rot3(dir, 0, vl[kBX], vl[kBY], vl[kBZ]);
+  const float bnR = rot3(dir, 0, vr[kBX], vr[kBY], vr[kBZ]);
+  const float2 r = pk(vl[kRHO], vr[kRHO]), p = pk(vl[kPRS], vr[kPRS]);
+
+  // GLM: exact solution of the linear (B_n, psi) interface problem
+  const float bx = fmaf(0.5f, __fadd_rn(bnL, bnR), -__fmul_rn(half_chi, __fsub_rn(vr[kPSI], vl[kPSI])));
+  const float psis = fmaf(0.5f, __fadd_rn(vl[kPSI], vr[kPSI]),
+                          -__fmul_rn(__fmul_rn(0.5f, ch), __fsub_rn(bnR, bnL)));
+  const float bx2 = __fmul_rn(bx, bx);
+  const float2 BX = pk1(bx), BX2 = pk1(bx2);
+
+  // outer states
+  const float2 b2 = fma2(bz, bz, fma2(by, by, BX2));
+  const float2 pt = fma2(H, b2, p);
+  const float2 vv = fma2(w, w, fma2(v, v, mul2(u, u)));
+  const float2 e = fma2(H, b2, fma2(mul2(H, r), vv, mul2(p, pk1(ph.gm1i))));
+  // 1/rho of both sides from one reciprocal; fast speeds squared
+  const float qr = rcp(__fmul_rn(r.x, r.y));
+  const float2 ri = mul2(swap2(r), pk1(qr));
+  const float2 gp = mul2(pk1(ph.gamma), p);
+  const float2 g = mul2(gp, ri);
+  const float2 a = fma2(b2, ri, g);
+  const float2 disc2 = fma2(a, a, mul2(pk1(-4.0f), mul2(g, mul2(BX2, ri))));
+  const float dL = fmaxf(disc2.x, 0.0f), dR = fmaxf(disc2.y, 0.0f);
+  const float2 dsc = pk(dL, dR);
+  const float2 rq = pk(dL > 0.0f ? rsqrtf(dL) : 0.0f, dR > 0.0f ? rsqrtf(dR) : 0.0f);
+  const float2 cf2 = mul2(H, fma2(dsc, rq, a));
+  // wave-speed estimates, contact speed and total pressure
+  const float c2m = fmaxf(cf2.x, cf2.y);
+  const float cmax = c2m > 0.0f ? __fmul_rn(c2m, rsqrtf(c2m)) : 0.0f;
+  const float2 S = add2(pk(fminf(u.x, u.y), fmaxf(u.x, u.y)), pk(-cmax, cmax));
+  const float2 Su = sub2(S, u);
+  const float2 d = mul2(Su, r);
+  const float Di = rcp(__fsub_rn(d.y, d.x));
+  const float SM =
+      __fmul_rn(__fadd_rn(__fsub_rn(fmaf(d.y, u.y, -__fmul_rn(d.x, u.x)), pt.y), pt.x), Di);
+  const float pts = __fmul_rn(fmaf(__fmul_rn(d.x, d.y), __fsub_rn(u.y, u.x),
+                                   fmaf(d.y, pt.x, -__fmul_rn(d.x, pt.y))), Di);
+  const float2 SMv = pk1(SM);
+
+  // single-star states, degenerate when |rho (S-u)(S-S_M) - Bx^2| < 1e-8 p_t*;
+  // paired reciprocals of S-S_M and of the two denominators
+  const float2 sm = sub2(S, SMv);
+  const float2 den = fma2(d, sm, pk1(-bx2));
+  const float thr = __fmul_rn(1e-8f, pts);
+  const bool degL = fabsf(den.x) < thr, degR = fabsf(den.y) < thr;
+  const float2 dn = pk(degL ? 1.0f : den.x, degR ? 1.0f : den.y);
+  const float ps = __fmul_rn(sm.x, sm.y), pd = __fmul_rn(dn.x, dn.y);
+  const float q4 = rcp(__fmul_rn(ps, pd));
+  const float qs = __fmul_rn(pd, q4), qd = __fmul_rn(ps, q4);
+  const float2 smi = mul2(swap2(sm), pk1(qs));
+  const float2 deni = mul2(swap2(dn), pk1(qd));
+  const float2 rs = mul2(d, smi);
+  const float2 fv = mul2(mul2(BX, sub2(SMv, u)), deni);
+  const float2 fb = mul2(fma2(d, Su, pk1(-bx2)), deni);
+  const float2 vs0 = fma2(pk(-by.x, -by.y), fv, v), ws0 = fma2(pk(-bz.x, -bz.y), fv, w);
+  const float2 bys0 = mul2(by, fb), bzs0 = mul2(bz, fb);
+  const float2 vs = pk(degL ? v.x : vs0.x, degR ? v.y : vs0.y);
+  const float2 ws = pk(degL ? w.x : ws0.x, degR ? w.y : ws0.y);
+  const float2 bys = pk(degL ? by.x : bys0.x, degR ? by.y : bys0.y);
+  const float2 bzs = pk(degL ? bz.x : bzs0.x, degR ? bz.y : bzs0.y);
+  const float2 vb = fma2(w, bz, fma2(v, by, mul2(u, BX)));
+  const float2 vbs = fma2(ws, bzs, fma2(vs, bys, mul2(SMv, BX)));
+  const float2 es = mul2(fma2(BX, sub2(vb, vbs),
+                              fma2(pk1(pts), SMv, fma2(Su, e, pk(-__fmul_rn(pt.x, u.x),
+                                                                 -__fmul_rn(pt.y, u.y))))),
+                         smi);
+
+  // fan region: side a = L if (S_L > 0) or (S_R >= 0 and S_M >= 0), else R
+  const bool sup = S.x > 0.0f || S.y < 0.0f;
+  const bool useL = S.x > 0.0f || (!(S.y < 0.0f) && SM >= 0.0f);
+  const float ra = useL ? r.x : r.y, ua = useL ? u.x : u.y;
+  const float2 vw = useL ? pk(v.x, w.x) : pk(v.y, w.y);
+  const float2 bb = useL ? pk(by.x, bz.x) : pk(by.y, bz.y);
+  const float ea = useL ? e.x : e.y, pta = useL ? pt.x : pt.y;
+  const float rsa = useL ? rs.x : rs.y, esa = useL ? es.x : es.y;
+  const float2 vws = useL ? pk(vs.x, ws.x) : pk(vs.y, ws.y);
+  const float2 bbs = useL ? pk(bys.x, bzs.x) : pk(bys.y, bzs.y);
+  const float vbsa = useL ? vbs.x : vbs.y, vba = useL ? vb.x : vb.y;
+  const float c1 = sup ? 0.0f : (useL ? S.x : S.y);
+  const float2 C1 = pk1(c1), UA = pk1(ua);
+  // flux of the outer state plus the single-star jump
+  const float ru = __fmul_rn(ra, ua);
+  const float2 rvw = mul2(pk1(ra), vw);
+  float f0 = fmaf(c1, __fsub_rn(rsa, ra), ru);
+  float f1 = fmaf(c1, fmaf(rsa, SM, -ru), __fsub_rn(fmaf(ru, ua, pta), bx2));
+  float2 f23 = fma2(C1, fma2(pk1(rsa), vws, pk(-rvw.x, -rvw.y)),
+                    fma2(rvw, UA, pk(-__fmul_rn(bx, bb.x), -__fmul_rn(bx, bb.y))));
+  float2 f45 = fma2(C1, sub2(bbs, bb), fma2(bb, UA, pk(-__fmul_rn(bx, vw.x), -__fmul_rn(bx, vw.y))));
+  float f6 = fmaf(c1, __fsub_rn(esa, ea), fmaf(__fadd_rn(ea, pta), ua, -__fmul_rn(bx, vba)));
+
+  // Alfven waves and double-star states; 1/sqrt(rho*) by rsqrt
+  const float2 iq = pk(rsqrtf(rs.x), rsqrtf(rs.y));
+  const float2 sq = mul2(rs, iq);
+  const float abx = fabsf(bx);
+  const float2 Ss = fma2(pk(-abx, abx), iq, SMv);  // (S_L*, S_R*)
+  const float sg = bx >= 0.0f ? 1.0f : -1.0f;
+  const float isum = rcp(__fadd_rn(sq.x, sq.y));
+  const float sqLR = __fmul_rn(sq.x, sq.y);
+  const float2 SG = pk1(sg), IS = pk1(isum), SQL = pk1(sq.x), SQR = pk1(sq.y);
+  // (v**, w**) and (By**, Bz**)
+  const float2 vwR = pk(vs.y, ws.y), vwL = pk(vs.x, ws.x);
+  const float2 bbR = pk(bys.y, bzs.y), bbL = pk(bys.x, bzs.x);
+  const float2 vwss = mul2(fma2(sub2(bbR, bbL), SG, fma2(SQR, vwR, mul2(SQL, vwL))), IS);
+  const float2 bbss = mul2(fma2(pk1(sqLR), mul2(sub2(vwR, vwL), SG), fma2(SQR, bbL, mul2(SQL, bbR))), IS);
+  const float vbss = fmaf(vwss.y, bbss.y, fmaf(vwss.x, bbss.x, __fmul_rn(SM, bx)));
+
+  // inside the Alfven fan: c2 = S*_a
+  const bool inner = !sup && (useL ? !(Ss.x > 0.0f) : !(Ss.y < 0.0f));
+  const float sqa = useL ? -sq.x : sq.y;
+  const float ess = fmaf(sqa, __fmul_rn(__fsub_rn(vbsa, vbss), sg), esa);
+  const float c2 = inner ? (useL ? Ss.x : Ss.y) : 0.0f;
+  const float c2rs = __fmul_rn(c2, rsa);
+  f23 = fma2(pk1(c2rs), sub2(vwss, vws), f23);
+  f45 = fma2(pk1(c2), sub2(bbss, bbs), f45);
+  f6 = fmaf(c2, __fsub_rn(ess, esa), f6);
+
+  F[kRHO] = f0;
+  F[kPRS] = f6;
+  F[kPSI] = __fmul_rn(__fmul_rn(ch, ch), bx);
+  // un-rotate: component m gets rotated slot j = (m - dir) mod 3
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const int j = (m - dir + 3) % 3;
+    F[kVX + m] = j == 0 ? f1 : (j == 1 ? f23.x : f23.y);
+    F[kBX + m] = j == 0 ? psis : (j == 1 ? f45.x : f45.y);
+  }
+}
+#endif
+
 // GLM interface step + HLLD along direction dir (0, 1, 2; template
 // argument) for primitive face states vl, vr.  ch: cleaning speed;
 // half_chi = 0.5 / ch.  F in conservative ordering.  Every sum of products
@@ -540,6 +701,12 @@ MHD_HD T rot3(int dir, int j, T a, T b, T c) {
 template <int dir, class T>
 MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
                           const Phys<T>& ph, T F[kNV]) {
+#ifdef __CUDA_ARCH__
+  if constexpr (sizeof(T) == 4) {  // FP32 on the device: the packed form
+    glm_hlld_flux_f32x2<dir>(vl, vr, ch, half_chi, ph, F);
+    return;
+  }
+#endif
   const T half = T(0.5);
   // rotate: u normal, (v, w) tangential in cyclic order; by, bz likewise
   const T uL = rot3(dir, 0, vl[kVX], vl[kVY], vl[kVZ]);
