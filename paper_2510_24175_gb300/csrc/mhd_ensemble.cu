@@ -110,7 +110,9 @@ __device__ __forceinline__ void ens_stage(const EnsArgs& a, unsigned char* smem,
     const int bx = (int)(j % B.ntx);
     const int by = (int)((j / B.ntx) % B.nty);
     const int bz = (int)(j / ((long long)B.ntx * B.nty));
-    stage_tile<float, TY, kEnsNW, STAGE, true>(p, sc, bx, by, bz, smem, wmax);
+    // (no interior prefetch: the persistent kernel's registers are capped at
+    // 128 for two CTAs per SM, and the prefetch registers spill there)
+    stage_tile<float, TY, kEnsNW, STAGE, true, false, false, false>(p, sc, bx, by, bz, smem, wmax);
   }
 }
 

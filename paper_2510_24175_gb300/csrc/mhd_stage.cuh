@@ -262,7 +262,8 @@ __device__ __forceinline__ void cell_slopes(const T* m, int sm, const T* c, int 
 // the face update), the face / cell electric fields go to p.ctf, and the last
 // stage has no damping and no wave-speed reduction (done after the face update).
 // HALO (3-D, not CT): ghost cells of kBcHalo sides from p.halo (halo_cell).
-template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT = false, bool HALO = false>
+template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT = false, bool HALO = false,
+          bool PREFETCH = true>
 __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepScalars& sc,
                                            int bx, int by, int bz, unsigned char* smem_raw,
                                            double* wmax) {
@@ -340,6 +341,33 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
 #pragma unroll
     for (int k = 0; k < kNV; ++k) dst[k * dst_stride] = v[k];
   };
+  // FP32 kernels without halo faces or constrained transport, one thread per
+  // interior column (NT = NINT): each thread's interior item of the next
+  // iteration (plane k + 3) is fetched into registers one iteration ahead, so
+  // that its global-load latency overlaps this plane's slope, flux and update
+  // phases.  The same cells are read as without it, and converted by the same
+  // code.  (PREFETCH = false: not done, for callers short of registers.)
+  constexpr bool PREF = PREFETCH && ZACT && !HALO && !CT && sizeof(T) == 4 && NT == G::NINT;
+  T pre[kNV];
+  auto fetch_interior = [&](int zz) {
+    const int r = tid / TX, c = tid - (tid / TX) * TX;
+    const int gz = remap(zz, nz, p.bc_lo[2], p.bc_hi[2]);
+    const int gx = remap(x0 + c, nx, p.bc_lo[0], p.bc_hi[0]);
+    const int gy = G::GY ? remap(y0 + r, ny, p.bc_lo[1], p.bc_hi[1]) : 0;
+    const long long off = (long long)gz * p.sz + (long long)gy * p.sy + gx;
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) pre[k] = p.win[k * p.sv + off];
+  };
+  auto convert_interior = [&](int zz) {
+    const int r = tid / TX, c = tid - (tid / TX) * TX;
+    T v[kNV];
+    unsigned fl = 0;
+    cons_to_prim(pre, v, ph, fl);
+    if (fl) count_floors(fl, zz, r, c);
+    T* dst = ring_plane(zz) + tid;
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) dst[k * G::PS] = v[k];
+  };
   // phase-A item: interior cell of plane zi or halo cell of plane zh
   auto load_item = [&](int it, int zi, int zh) {
     if (it < G::NINT) {
@@ -398,13 +426,27 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
     const bool main = k >= z0;
     // ---- A: loads ---------------------------------------------------------
     const int nload = main ? G::NLOAD : G::NINT;
-    for (int it = tid; it < nload; it += NT) {
-      if (ZACT && it < G::NINT)
-        load_item(it, k + 2, k);
-      else
-        load_item(it, k, k);
+    if constexpr (PREF) {
+      // interior item (it = tid) from the registers fetched last iteration
+      if (k > z0 - NWARM) {
+        convert_interior(k + 2);
+      } else {
+        fetch_interior(k + 2);
+        convert_interior(k + 2);
+      }
+      for (int it = tid + NT; it < nload; it += NT) load_item(it, k, k);
+    } else {
+      for (int it = tid; it < nload; it += NT) {
+        if (ZACT && it < G::NINT)
+          load_item(it, k + 2, k);
+        else
+          load_item(it, k, k);
+      }
     }
     __syncthreads();
+    if constexpr (PREF) {
+      if (k + 1 < z1) fetch_interior(k + 3);
+    }
     if (ZACT && k < z0 - 2) continue;
     const T* cur = ring_plane(k);
 
