@@ -531,7 +531,7 @@ MHD_HD T rot3(int dir, int j, T a, T b, T c) {
   return m == 0 ? a : (m == 1 ? b : c);
 }
 
-#ifdef __CUDA_ARCH__
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
 // Packed FP32 (FFMA2 / FMUL2 / FADD2: two lanes per instruction, each lane
 // rounded as the scalar instruction).  x - y is fma(y, -1, x): the product is
 // exact, so it rounds once, as a subtraction does.
@@ -701,7 +701,7 @@ __device__ __forceinline__ void glm_hlld_flux_f32x2(const float vl[kNV], const f
 template <int dir, class T>
 MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
                           const Phys<T>& ph, T F[kNV]) {
-#ifdef __CUDA_ARCH__
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
   if constexpr (sizeof(T) == 4) {  // FP32 on the device: the packed form
     glm_hlld_flux_f32x2<dir>(vl, vr, ch, half_chi, ph, F);
     return;
