@@ -236,12 +236,58 @@ struct TileGeom {
   static constexpr int ITEMS = IT_X + IT_Y + IT_XE;
 };
 
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+// FP32 limited slopes of two variables at once: the one-sided differences,
+// their product, the doubled minimum and the halved sum in packed FP32; the
+// per-lane comparisons, minima and sign choices as limited_slope<float>
+// takes them (the same values).
+__device__ __forceinline__ float2 limited_slope2(float2 dm, float2 dp, int lim) {
+  const float2 pr = mul2(dm, dp);
+  float2 mag = pk(fminf(fabsf(dm.x), fabsf(dp.x)), fminf(fabsf(dm.y), fabsf(dp.y)));
+  if (lim == kLimMC) {
+    const float2 two = mul2(pk1(2.0f), mag);
+    const float2 sum = add2(dm, dp);
+    const float2 cen = mul2(pk1(0.5f), pk(fabsf(sum.x), fabsf(sum.y)));
+    mag = pk(fminf(two.x, cen.x), fminf(two.y, cen.y));
+  }
+  const bool okx = lim != kLimFlat && pr.x > 0.0f, oky = lim != kLimFlat && pr.y > 0.0f;
+  return pk(okx ? (dm.x > 0.0f ? mag.x : -mag.x) : 0.0f,
+            oky ? (dm.y > 0.0f ? mag.y : -mag.y) : 0.0f);
+}
+#endif
+
 // Limited slopes of the 9 primitives of one cell from its two neighbours
 // along a direction, with the zero-slope fallback when a face density or
-// pressure would be non-positive.
-template <class T>
+// pressure would be non-positive.  PAIRED: FP32 on the device pairs the
+// variables (0, 1) ... (6, 7) in packed instructions (the same values; fewer
+// instructions, more registers live).
+template <class T, bool PAIRED = true>
 __device__ __forceinline__ void cell_slopes(const T* m, int sm, const T* c, int sc, const T* p,
                                             int sp, int lim, T sig[kNV]) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  if constexpr (PAIRED && sizeof(T) == 4) {
+#pragma unroll
+    for (int k = 0; k + 1 < kNV; k += 2) {
+      const float2 q = pk(c[k * sc], c[(k + 1) * sc]);
+      const float2 dm = sub2(q, pk(m[k * sm], m[(k + 1) * sm]));
+      const float2 dp = sub2(pk(p[k * sp], p[(k + 1) * sp]), q);
+      const float2 s2 = limited_slope2(dm, dp, lim);
+      sig[k] = s2.x;
+      sig[k + 1] = s2.y;
+    }
+    {
+      const T q = c[(kNV - 1) * sc];
+      sig[kNV - 1] = limited_slope(q - m[(kNV - 1) * sm], p[(kNV - 1) * sp] - q, lim);
+    }
+    const bool ok = gt0(c[kRHO * sc] - T(0.5) * tabs(sig[kRHO])) &&
+                    gt0(c[kPRS * sc] - T(0.5) * tabs(sig[kPRS]));
+    if (!ok) {
+#pragma unroll
+      for (int k = 0; k < kNV; ++k) sig[k] = T(0);
+    }
+    return;
+  }
+#endif
 #pragma unroll
   for (int k = 0; k < kNV; ++k) {
     const T q = c[k * sc];
@@ -347,6 +393,9 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
   // that its global-load latency overlaps this plane's slope, flux and update
   // phases.  The same cells are read as without it, and converted by the same
   // code.  (PREFETCH = false: not done, for callers short of registers.)
+  // The slopes are paired in packed FP32 where the prefetch is not done: with
+  // both, the kernel needs more than the 128 registers of two CTAs per SM,
+  // and capping it there cost more than either gains.
   constexpr bool PREF = PREFETCH && ZACT && !HALO && !CT && sizeof(T) == 4 && NT == G::NINT;
   T pre[kNV];
   auto fetch_interior = [&](int zz) {
@@ -473,14 +522,14 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
         dst = sys + j;
         ds = G::SYN;
       }
-      cell_slopes(m, s0, c, s1, pp, s2, lim, sig);
+      cell_slopes<T, !PREF>(m, s0, c, s1, pp, s2, lim, sig);
 #pragma unroll
       for (int q = 0; q < kNV; ++q) dst[q * ds] = sig[q];
     }
     if (ZACT && owner) {
       T sig[kNV];
-      cell_slopes(cur + oidx, G::PS, ring_plane(k + 1) + oidx, G::PS,
-                  ring_plane(k + 2) + oidx, G::PS, lim, sig);
+      cell_slopes<T, !PREF>(cur + oidx, G::PS, ring_plane(k + 1) + oidx, G::PS,
+                            ring_plane(k + 2) + oidx, G::PS, lim, sig);
 #pragma unroll
       for (int q = 0; q < kNV; ++q) zS[q * G::NINT + oidx] = sig[q];
     }
