@@ -83,12 +83,76 @@ __device__ __forceinline__ void wenoz_pair(const T f[5], T& minus, T& plus) {
   }
 }
 
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+// FP32 WENO-Z of two variables at once (.x, .y), the steps of wenoz_pair<float>
+// in packed FP32 with every operation written out; the reciprocals per lane.
+__device__ __forceinline__ void wenoz_pair2(const float2 f[5], float2& minus, float2& plus) {
+  const float2 C12 = pk1(1.0f / 12.0f), Q4 = pk1(0.25f), C39 = pk1(39.0f);
+  const float2 M2 = pk1(-2.0f), M4 = pk1(-4.0f), T3 = pk1(3.0f);
+  const float2 D0 = mul2(C12, fma2(M2, f[1], add2(f[0], f[2])));
+  const float2 D1 = mul2(C12, fma2(M2, f[2], add2(f[1], f[3])));
+  const float2 D2 = mul2(C12, fma2(M2, f[3], add2(f[2], f[4])));
+  const float2 G0 = mul2(Q4, fma2(T3, f[2], fma2(M4, f[1], f[0])));
+  const float2 G1 = mul2(Q4, sub2(f[1], f[3]));
+  const float2 G2 = mul2(Q4, add2(fma2(M4, f[3], mul2(T3, f[2])), f[4]));
+  const float2 b0 = fma2(G0, G0, mul2(mul2(C39, D0), D0));
+  const float2 b1 = fma2(G1, G1, mul2(mul2(C39, D1), D1));
+  const float2 b2 = fma2(G2, G2, mul2(mul2(C39, D2), D2));
+  const float2 EPS = pk1(0.25f * WenoEps<float>::v);
+  const float2 d02 = sub2(b0, b2);
+  const float2 tau = pk(fabsf(d02.x), fabsf(d02.y));
+  const float2 e0 = add2(b0, EPS), e1 = add2(b1, EPS), e2 = add2(b2, EPS);
+  const float2 ONE = pk1(1.0f);
+  const float2 P0 = fma2(tau, pk(rcp(e0.x), rcp(e0.y)), ONE);
+  const float2 P1 = fma2(tau, pk(rcp(e1.x), rcp(e1.y)), ONE);
+  const float2 P2 = fma2(tau, pk(rcp(e2.x), rcp(e2.y)), ONE);
+  const float2 S1 = mul2(pk1(6.0f), P1), T0 = mul2(T3, P0), T2 = mul2(T3, P2);
+  const float2 den_p = add2(add2(P0, S1), T2), den_m = add2(add2(P2, S1), T0);
+  const float2 num_p = fma2(T2, sub2(D2, G2), fma2(S1, sub2(D1, G1), mul2(P0, add2(D0, G0))));
+  const float2 num_m = fma2(T0, sub2(D0, G0), fma2(S1, add2(D1, G1), mul2(P2, add2(D2, G2))));
+  plus = fma2(num_p, pk(rcp(den_p.x), rcp(den_p.y)), f[2]);
+  minus = fma2(num_m, pk(rcp(den_m.x), rcp(den_m.y)), f[2]);
+}
+#endif
+
 // Face values of all 9 primitives of one cell from five cells c[0..4]
 // (variables stride[j] apart); flat fallback on non-positive face density
-// or pressure.
+// or pressure.  FP32 on the device reconstructs the variables in pairs
+// (0, 1) ... (6, 7) in packed instructions.
 template <class T>
 __device__ __forceinline__ void cell_weno(const T* const c[5], const int st[5], T M[kNV],
                                           T P[kNV]) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int k = 0; k + 1 < kNV; k += 2) {
+      float2 f[5];
+#pragma unroll
+      for (int j = 0; j < 5; ++j) f[j] = pk(c[j][k * st[j]], c[j][(k + 1) * st[j]]);
+      float2 m2, p2;
+      wenoz_pair2(f, m2, p2);
+      M[k] = m2.x;
+      M[k + 1] = m2.y;
+      P[k] = p2.x;
+      P[k + 1] = p2.y;
+    }
+    {
+      float2 f[5];
+#pragma unroll
+      for (int j = 0; j < 5; ++j) f[j] = pk1(c[j][(kNV - 1) * st[j]]);
+      float2 m2, p2;
+      wenoz_pair2(f, m2, p2);
+      M[kNV - 1] = m2.x;
+      P[kNV - 1] = p2.x;
+    }
+    const bool ok = M[kRHO] > T(0) && P[kRHO] > T(0) && M[kPRS] > T(0) && P[kPRS] > T(0);
+    if (!ok) {
+#pragma unroll
+      for (int k = 0; k < kNV; ++k) M[k] = P[k] = c[2][k * st[2]];
+    }
+    return;
+  }
+#endif
 #pragma unroll
   for (int k = 0; k < kNV; ++k) {
     T f[5];
@@ -129,8 +193,12 @@ struct WenoGeom {
 };
 
 // CT: constrained transport, HALO: halo faces, as in stage_tile() (mhd_stage.cuh).
+// 3-D FP32: two CTAs per SM (128 registers at most); without the bound the
+// packed reconstruction takes 132-150 registers and runs one CTA per SM,
+// 25-30 % slower.
 template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT, bool HALO = false>
-__global__ void __launch_bounds__(NW * 32, 1) rk_stage_weno_kernel(const StageParams<T> p) {
+__global__ void __launch_bounds__(NW * 32, (sizeof(T) == 4 && ZACT) ? 2 : 1)
+    rk_stage_weno_kernel(const StageParams<T> p) {
   using G = WenoGeom<TY, ZACT>;
   constexpr int NT = NW * 32;
   constexpr int TX = G::TX;
