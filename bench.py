@@ -53,7 +53,7 @@ FP64_INST_PER_CELL = {1: 1195.6, 2: 1222.3}
 # dram__bytes_write over the timed steps of this bench's 256^3 FP64 and 512^3
 # FP32 runs, profiles/); reported as the roofline's traffic per launch.  Set
 # to None whenever the kernel changes until they are captured again.
-TRAFFIC_BYTES_PER_CELL = {8: {1: 149.3, 2: 221.3}, 4: {1: 75.8, 2: 111.5}}
+TRAFFIC_BYTES_PER_CELL = {8: {1: 149.3, 2: 221.3}, 4: {1: 75.6, 2: 111.5}}
 # Nominal FP64 peak: 2 lanes/clk/SM x 152 SMs x 2.07 GHz = 629 G
 # lane-instructions/s (1.26 TFLOP/s counting an FMA as 2).  The measured one,
 # mhd_fp64_fma_rate in the same run, is reported beside it (about 1.68
@@ -64,7 +64,7 @@ FP64_PEAK_GINST = 2 * 152 * 2.07
 # / cells, turbulent box 512^3, stage 1 / stage 2; profiles/) and the issue
 # peak they run against: 4 warp-instructions per clock per SM (one per
 # scheduler) x 152 SMs x 2.07 GHz.
-FP32_WARP_INST_PER_CELL = {1: 73.51, 2: 79.43}
+FP32_WARP_INST_PER_CELL = {1: 74.01, 2: 79.89}
 ISSUE_PEAK_GINST = 4 * 152 * 2.07
 # FP64-pipe lane-instructions per cell of the FP64 WENO-Z stage kernel (ncu,
 # Orszag-Tang 256^3; first / middle / last SSP-RK3 stage).
@@ -72,7 +72,7 @@ WENO_FP64_INST_PER_CELL = {"stage1": 3545.8, "stage_mid": 3563.8, "stage2": 3564
 # Warp-instructions per cell of the FP32 WENO-Z stage kernel (ncu
 # smsp__inst_executed / cells, Orszag-Tang 256^3; first / middle / last
 # SSP-RK3 stage).
-WENO_FP32_WARP_INST_PER_CELL = {"stage1": 166.99, "stage_mid": 168.42, "stage2": 172.64}
+WENO_FP32_WARP_INST_PER_CELL = {"stage1": 141.17, "stage_mid": 142.61, "stage2": 147.48}
 # Algorithmic HBM bytes per cell: stage 1 reads U^n and writes U1 (18 words),
 # stage 2 reads U1 and U^n and writes U^{n+1} (27 words).
 WORDS_STAGE = {1: 18, 2: 27}
