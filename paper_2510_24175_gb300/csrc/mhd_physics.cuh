@@ -305,6 +305,16 @@ MHD_HD double half_of(double x) {
 }
 MHD_HD float half_of(float x) { return 0.5f * x; }
 
+// x * s for a sign factor s = +1 / -1 given by its sign bit (0, or the top
+// bit of a 64-bit pattern): FP64 flips the sign bit of x on the integer pipe
+// (the product by +-1 is exact, so the result is the same, NaN payloads
+// aside); FP32 negates.
+MHD_HD long long sign_bit_of(bool negative) {
+  return negative ? (long long)0x8000000000000000ull : 0ll;
+}
+MHD_HD double sign_mul(double x, long long sbit) { return bits2d(dbits(x) ^ sbit); }
+MHD_HD float sign_mul(float x, long long sbit) { return sbit ? -x : x; }
+
 // Fast magnetosonic speed squared from 1/rho, gamma p, |B|^2 and B_n^2:
 // with g = gamma p / rho, a = g + |B|^2 / rho and c_an^2 = B_n^2 / rho,
 // c_f^2 = (a + sqrt(a^2 - 4 g c_an^2)) / 2.
@@ -732,10 +742,11 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
   const T b2L = fma_rn(bzL, bzL, fma_rn(byL, byL, bx2));
   const T b2R = fma_rn(bzR, bzR, fma_rn(byR, byR, bx2));
   const T ptL = fma_rn(half, b2L, pL), ptR = fma_rn(half, b2R, pR);
+  // (rho / 2 by half_of: an exponent move in FP64, the same value as 0.5 * rho)
   const T eL = fma_rn(half, b2L,
-                      fma_rn(half * rL, dot3_rn(uL, uL, vL, vL, wL, wL), mul_rn(pL, ph.gm1i)));
+                      fma_rn(half_of(rL), dot3_rn(uL, uL, vL, vL, wL, wL), mul_rn(pL, ph.gm1i)));
   const T eR = fma_rn(half, b2R,
-                      fma_rn(half * rR, dot3_rn(uR, uR, vR, vR, wR, wR), mul_rn(pR, ph.gm1i)));
+                      fma_rn(half_of(rR), dot3_rn(uR, uR, vR, vR, wR, wR), mul_rn(pR, ph.gm1i)));
   // 1/rho of both sides from one reciprocal; only max(c_fL, c_fR) is used,
   // so one square root of max(c_fL^2, c_fR^2) (sqrt is monotone and
   // correctly rounded: the same value)
@@ -765,8 +776,8 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
   const T qs = pd * q4, qd = ps * q4;
   const T smiL = smR * qs, smiR = smL * qs;
   const T deniL = dnR * qd, deniR = dnL * qd;
-  T rsL, vsL, wsL, bysL, bzsL, esL, vbsL;
-  T rsR, vsR, wsR, bysR, bzsR, esR, vbsR;
+  T rsL, vsL, wsL, bysL, bzsL, esL, vbsL, vbL;
+  T rsR, vsR, wsR, bysR, bzsR, esR, vbsR, vbR;
   {
     rsL = dL * smiL;
     const T fv = bx * (SM - uL) * deniL;
@@ -775,9 +786,9 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
     wsL = degL ? wL : fma_rn(-bzL, fv, wL);
     bysL = degL ? byL : byL * fb;
     bzsL = degL ? bzL : bzL * fb;
-    const T vb = dot3_rn(uL, bx, vL, byL, wL, bzL);
+    vbL = dot3_rn(uL, bx, vL, byL, wL, bzL);
     vbsL = dot3_rn(SM, bx, vsL, bysL, wsL, bzsL);
-    esL = fma_rn(bx, vb - vbsL,
+    esL = fma_rn(bx, vbL - vbsL,
                    fma_rn(pts, SM, fma_rn(SL - uL, eL, -mul_rn(ptL, uL)))) *
           smiL;
   }
@@ -789,9 +800,9 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
     wsR = degR ? wR : fma_rn(-bzR, fv, wR);
     bysR = degR ? byR : byR * fb;
     bzsR = degR ? bzR : bzR * fb;
-    const T vb = dot3_rn(uR, bx, vR, byR, wR, bzR);
+    vbR = dot3_rn(uR, bx, vR, byR, wR, bzR);
     vbsR = dot3_rn(SM, bx, vsR, bysR, wsR, bzsR);
-    esR = fma_rn(bx, vb - vbsR,
+    esR = fma_rn(bx, vbR - vbsR,
                    fma_rn(pts, SM, fma_rn(SR - uR, eR, -mul_rn(ptR, uR)))) *
           smiR;
   }
@@ -808,12 +819,12 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
   const T rs = useL ? rsL : rsR, vs = useL ? vsL : vsR, ws = useL ? wsL : wsR;
   const T bys = useL ? bysL : bysR, bzs = useL ? bzsL : bzsR, es = useL ? esL : esR;
   const T vbs = useL ? vbsL : vbsR;
+  const T vb = useL ? vbL : vbR;  // v . B of the side's outer state
   // the flux terms of the outer and single-star states (the Alfven-fan
   // terms are added below), so that the outer state dies here
   const T c1 = sup ? T(0) : (useL ? SL : SR);
   T f[7];
   {
-    const T vb = dot3_rn(u, bx, v, by, w, bz);
     const T ru = mul_rn(r, u), rv = mul_rn(r, v), rw = mul_rn(r, w);
     f[0] = fma_rn(c1, rs - r, ru);
     f[1] = fma_rn(c1, fma_rn(rs, SM, -ru), fma_rn(ru, u, pt) - bx2);
@@ -831,20 +842,21 @@ MHD_HD void glm_hlld_flux(const T vl[kNV], const T vr[kNV], T ch, T half_chi,
   const T abx = tabs(bx);
   const T SLs = fma_rn(-abx, iqL, SM);
   const T SRs = fma_rn(abx, iqR, SM);
-  const T sg = ge0(bx) ? T(1) : T(-1);
+  // sign(B_x) applied as a sign flip (sign_mul), not a multiplication
+  const long long sg = sign_bit_of(!ge0(bx));
   const T isum = rcp(sqL + sqR);
   const T sqLR = mul_rn(sqL, sqR);
-  const T vss = (fma_rn(sqR, vsR, mul_rn(sqL, vsL)) + (bysR - bysL) * sg) * isum;
-  const T wss = (fma_rn(sqR, wsR, mul_rn(sqL, wsL)) + (bzsR - bzsL) * sg) * isum;
-  const T byss = fma_rn(sqLR, (vsR - vsL) * sg, fma_rn(sqR, bysL, mul_rn(sqL, bysR))) * isum;
-  const T bzss = fma_rn(sqLR, (wsR - wsL) * sg, fma_rn(sqR, bzsL, mul_rn(sqL, bzsR))) * isum;
+  const T vss = (fma_rn(sqR, vsR, mul_rn(sqL, vsL)) + sign_mul(bysR - bysL, sg)) * isum;
+  const T wss = (fma_rn(sqR, wsR, mul_rn(sqL, wsL)) + sign_mul(bzsR - bzsL, sg)) * isum;
+  const T byss = fma_rn(sqLR, sign_mul(vsR - vsL, sg), fma_rn(sqR, bysL, mul_rn(sqL, bysR))) * isum;
+  const T bzss = fma_rn(sqLR, sign_mul(wsR - wsL, sg), fma_rn(sqR, bzsL, mul_rn(sqL, bzsR))) * isum;
   const T vbss = dot3_rn(SM, bx, vss, byss, wss, bzss);
 
   // F = F_a + c1 (U*_a - U_a) + c2 (U**_a - U*_a) with c1 = S_a unless the
   // interface is supersonic, c2 = S*_a inside the Alfven fan.
   const bool inner = !sup && (useL ? !gt0(SLs) : !lt0(SRs));
   const T sq = useL ? -sqL : sqR;
-  const T ess = fma_rn(sq, (vbs - vbss) * sg, es);
+  const T ess = fma_rn(sq, sign_mul(vbs - vbss, sg), es);
   const T c2 = inner ? (useL ? SLs : SRs) : T(0);
   const T c2rs = mul_rn(c2, rs);
   f[2] = fma_rn(c2rs, vss - vs, f[2]);

@@ -193,11 +193,11 @@ struct WenoGeom {
 };
 
 // CT: constrained transport, HALO: halo faces, as in stage_tile() (mhd_stage.cuh).
-// 3-D FP32: two CTAs per SM (128 registers at most); without the bound the
-// packed reconstruction takes 132-150 registers and runs one CTA per SM,
-// 25-30 % slower.
+// 3-D FP32 with 8-warp CTAs: two CTAs per SM (128 registers at most);
+// without the bound the packed reconstruction takes 132-150 registers and
+// runs one CTA per SM, 25-30 % slower.  (Larger CTAs run one per SM.)
 template <class T, int TY, int NW, int STAGE, bool ZACT, bool CT, bool HALO = false>
-__global__ void __launch_bounds__(NW * 32, (sizeof(T) == 4 && ZACT) ? 2 : 1)
+__global__ void __launch_bounds__(NW * 32, (sizeof(T) == 4 && ZACT && NW <= 8) ? 2 : 1)
     rk_stage_weno_kernel(const StageParams<T> p) {
   using G = WenoGeom<TY, ZACT>;
   constexpr int NT = NW * 32;

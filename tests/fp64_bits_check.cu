@@ -1,7 +1,8 @@
 // Host-only check (compiled by tests/test_fp64_bit_helpers.py): the FP64
 // helpers that the kernels evaluate on the integer pipe -- sign tests, a < b,
 // min / max, |a| < t, max(x, 0), exact doubling and halving, -4x, x/2,
-// the limited slope and its derivative flags -- against the IEEE operations of the host compiler, on random and
+// the product by a sign factor +-1, the limited slope and its derivative
+// flags -- against the IEEE operations of the host compiler, on random and
 // special doubles (signed zeros, subnormals, extremes, infinities, NaNs).
 // Prints the number of disagreements and exits non-zero if there is any.
 #include <cmath>
@@ -98,6 +99,8 @@ int main() {
     bad += !(same(mx, fmax(a, b)) || (a == b && (same(mx, a) || same(mx, b))));
     bad += !same(neg4(a), -4.0 * a);
     bad += !same(half_of(a), 0.5 * a);
+    bad += !same(sign_mul(a, sign_bit_of(true)), -1.0 * a);
+    bad += !same(sign_mul(a, sign_bit_of(false)), 1.0 * a);
     const double m = fabs(a);
     if (!(m != m)) {
       bad += !same(bits2d(twice_bits(dbits(m))), m + m);

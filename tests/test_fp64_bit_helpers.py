@@ -1,8 +1,8 @@
 """The FP64 helpers the kernels evaluate on the integer pipe (sign tests,
 min / max, |a| < t, max(x, 0), exact doubling / halving, -4x, x/2, the
-limited slope) give the IEEE results: a host build of the kernels' own
-header, checked against the host compiler's IEEE arithmetic on random and
-special doubles."""
+product by a sign factor +-1, the limited slope) give the IEEE results: a
+host build of the kernels' own header, checked against the host compiler's
+IEEE arithmetic on random and special doubles."""
 import os
 import shutil
 import subprocess
