@@ -473,6 +473,13 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
 #pragma unroll 1
   for (int k = z0 - NWARM; k < z1; ++k) {
     const bool main = k >= z0;
+    // FP32 (two CTAs per SM): the item loops of phases A-C start at a
+    // thread index rotated by (k mod 4) whole warps.  A phase's items do not
+    // divide evenly among the warps; without the rotation the warps left with
+    // one item more are always the first ones, on the same schedulers in
+    // both CTAs of an SM, and rotated they change from plane to plane.
+    // Which thread takes an item does not change its result.
+    const int rtid = sizeof(T) == 4 ? (tid + 32 * (k & 3)) % NT : tid;
     // ---- A: loads ---------------------------------------------------------
     const int nload = main ? G::NLOAD : G::NINT;
     if constexpr (PREF) {
@@ -483,9 +490,9 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
         fetch_interior(k + 2);
         convert_interior(k + 2);
       }
-      for (int it = tid + NT; it < nload; it += NT) load_item(it, k, k);
+      for (int it = rtid + NT; it < nload; it += NT) load_item(it, k, k);
     } else {
-      for (int it = tid; it < nload; it += NT) {
+      for (int it = rtid; it < nload; it += NT) {
         if (ZACT && it < G::NINT)
           load_item(it, k + 2, k);
         else
@@ -500,7 +507,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
     const T* cur = ring_plane(k);
 
     // ---- B: slopes --------------------------------------------------------
-    for (int it = tid; main && it < G::SXN + G::SYN; it += NT) {
+    for (int it = rtid; main && it < G::SXN + G::SYN; it += NT) {
       T sig[kNV];
       T* dst;
       int ds;
@@ -536,7 +543,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
     __syncthreads();
 
     // ---- C: fluxes --------------------------------------------------------
-    for (int it = tid; main && it < G::ITEMS; it += NT) {
+    for (int it = rtid; main && it < G::ITEMS; it += NT) {
       T vl[kNV], vr[kNV], F[kNV];
       int dir;
       T* out;
