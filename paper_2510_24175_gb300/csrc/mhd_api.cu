@@ -7,7 +7,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
+#include <functional>
 #include <new>
+#include <queue>
 #include <vector>
 
 #include "mhd_ctx.h"
@@ -197,21 +200,48 @@ static void fill_grid(const mhd_config* c, mhd::Grid* g) {
   g->p_floor = c->p_floor;
 }
 
-// z planes per CTA: minimise (waves of CTAs) x (planes + prologue weight).
+// Duration, in plane iterations, of one stage launch of `cols` column tiles
+// over nz planes in z chunks of tz planes, on `slots` CTA slots: the CTAs
+// start in launch order (the full chunks of every column tile, then the
+// last, possibly shorter, chunk of every column tile), each on the slot that
+// frees first, and a CTA takes its planes plus one for its warm-up planes.
+static double launch_span(long long cols, int nz, int tz, long long slots) {
+  const long long chunks = (nz + tz - 1) / tz;
+  const double a = tz + 1.0, b = (double)(nz - (chunks - 1) * tz) + 1.0;
+  const long long n1 = cols * (chunks - 1);
+  const long long q = n1 / slots, r = n1 % slots;  // full chunks per slot
+  std::priority_queue<double, std::vector<double>, std::greater<double>> freed;
+  double span = 0.0;
+  for (long long s = 0; s < slots; ++s) {
+    const double t = (s < r ? q + 1 : q) * a;
+    freed.push(t);
+    span = std::max(span, t);
+  }
+  for (long long c = 0; c < cols; ++c) {
+    const double t = freed.top() + b;
+    freed.pop();
+    freed.push(t);
+    span = std::max(span, t);
+  }
+  return span;
+}
+
+// z planes per CTA: the candidate depth with the shortest launch_span, the
+// deeper one on a tie (fewer warm-ups).  (A depth that leaves a shorter last
+// chunk can win: those short CTAs run last and fill the slots that the last
+// wave of full chunks leaves idle.)
 static int choose_tz(const mhd::Grid& g, int ctas_per_sm, int ty) {
   if (g.ndim < 3) return 1;
   const long long cols = (long long)((g.n[0] + 31) / 32) * ((g.n[1] + ty - 1) / ty);
   const long long slots = (long long)g.nsm * ctas_per_sm;
   int best = g.n[2];
-  double best_cost = 1e300;
-  const int cands[] = {4, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256};
+  double best_span = 1e300;
+  const int cands[] = {256, 192, 128, 96, 80, 64, 56, 48, 40, 32, 24, 20, 16, 12, 8, 4};
   for (int tz : cands) {
-    if (tz > g.n[2] && tz != cands[0]) continue;
-    const long long ctas = cols * ((g.n[2] + tz - 1) / tz);
-    const long long waves = (ctas + slots - 1) / slots;
-    const double cost = (double)waves * (tz + 1.0);
-    if (cost < best_cost) {
-      best_cost = cost;
+    if (tz > g.n[2] && tz != 4) continue;
+    const double span = launch_span(cols, g.n[2], tz, slots);
+    if (span < best_span) {
+      best_span = span;
       best = tz;
     }
   }
