@@ -48,12 +48,12 @@ sys.path.insert(0, ROOT)
 # smsp__inst_executed_pipe_fp64 x 32 / cells over the timed steps of this
 # bench's Orszag-Tang 256^3 run (profiles/).  They change whenever the kernel
 # does.
-FP64_INST_PER_CELL = {1: 1195.6, 2: 1222.3}
+FP64_INST_PER_CELL = {1: 1183.0, 2: 1211.0}
 # DRAM bytes per cell of the stage kernel's launches (ncu dram__bytes_read +
 # dram__bytes_write over the timed steps of this bench's 256^3 FP64 and 512^3
 # FP32 runs, profiles/); reported as the roofline's traffic per launch.  Set
 # to None whenever the kernel changes until they are captured again.
-TRAFFIC_BYTES_PER_CELL = {8: {1: 149.3, 2: 221.3}, 4: {1: 75.6, 2: 111.5}}
+TRAFFIC_BYTES_PER_CELL = {8: {1: 151.9, 2: 224.4}, 4: {1: 75.65, 2: 111.64}}
 # Nominal FP64 peak: 2 lanes/clk/SM x 152 SMs x 2.07 GHz = 629 G
 # lane-instructions/s (1.26 TFLOP/s counting an FMA as 2).  The measured one,
 # mhd_fp64_fma_rate in the same run, is reported beside it (about 1.68
@@ -64,15 +64,15 @@ FP64_PEAK_GINST = 2 * 152 * 2.07
 # / cells, turbulent box 512^3, stage 1 / stage 2; profiles/) and the issue
 # peak they run against: 4 warp-instructions per clock per SM (one per
 # scheduler) x 152 SMs x 2.07 GHz.
-FP32_WARP_INST_PER_CELL = {1: 74.01, 2: 79.89}
+FP32_WARP_INST_PER_CELL = {1: 74.19, 2: 80.10}
 ISSUE_PEAK_GINST = 4 * 152 * 2.07
 # FP64-pipe lane-instructions per cell of the FP64 WENO-Z stage kernel (ncu,
 # Orszag-Tang 256^3; first / middle / last SSP-RK3 stage).
-WENO_FP64_INST_PER_CELL = {"stage1": 3545.8, "stage_mid": 3563.8, "stage2": 3564.9}
+WENO_FP64_INST_PER_CELL = {"stage1": 3511.2, "stage_mid": 3529.2, "stage2": 3530.3}
 # Warp-instructions per cell of the FP32 WENO-Z stage kernel (ncu
 # smsp__inst_executed / cells, Orszag-Tang 256^3; first / middle / last
 # SSP-RK3 stage).
-WENO_FP32_WARP_INST_PER_CELL = {"stage1": 141.17, "stage_mid": 142.61, "stage2": 147.48}
+WENO_FP32_WARP_INST_PER_CELL = {"stage1": 126.87, "stage_mid": 128.31, "stage2": 133.00}
 # Algorithmic HBM bytes per cell: stage 1 reads U^n and writes U1 (18 words),
 # stage 2 reads U1 and U^n and writes U^{n+1} (27 words).
 WORDS_STAGE = {1: 18, 2: 27}
