@@ -393,9 +393,9 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, const StepSc
   // that its global-load latency overlaps this plane's slope, flux and update
   // phases.  The same cells are read as without it, and converted by the same
   // code.  (PREFETCH = false: not done, for callers short of registers.)
-  // The slopes are paired in packed FP32 where the prefetch is not done: with
-  // both, the kernel needs more than the 128 registers of two CTAs per SM,
-  // and capping it there cost more than either gains.
+  // The slopes are paired in packed FP32 where the prefetch is not done;
+  // with the prefetch, pairing them as well (still within the 128 registers
+  // of two CTAs per SM) ran slower than scalar slopes.
   constexpr bool PREF = PREFETCH && ZACT && !HALO && !CT && sizeof(T) == 4 && NT == G::NINT;
   T pre[kNV];
   auto fetch_interior = [&](int zz) {
