@@ -408,10 +408,29 @@ int mhd_ensemble_destroy(mhd_ensemble* ens);
  * MHD_ERR_CUDA (message in mhd_last_error(NULL)). */
 int mhd_fp64_fma_rate(void* stream, unsigned warp_mask, double out[3]);
 
+/* Launch planning, on the host only (no GPU, no CUDA call): the z-chunk depth
+ * *tz (planes per CTA) that the 3-D stage launches of an n[0] x n[1] x n[2]
+ * grid use, for column tiles of 32 x ty cells (ty: 8 for the PLM kernels, 4
+ * for FP64 WENO-Z, 8 for FP32 WENO-Z) on nsm SMs holding ctas_per_sm stage
+ * CTAs each (1 for FP64 and FP32 WENO-Z, 2 for FP32 PLM), and, if span is not
+ * NULL, the modelled duration of one launch in plane iterations.  The model:
+ * the CTAs start in launch order -- every column tile's full chunks, then
+ * every column tile's last, possibly shorter, chunk -- each on the slot that
+ * frees first, and a CTA takes its planes plus one for its warm-up; the
+ * depth is the candidate (256, 192, 128, 96, 80, 64, 56, 48, 40, 32, 24, 20,
+ * 16, 12, 8, 4; at most n[2], or 4) with the shortest launch, the deeper one
+ * on a tie.  A grid with an extent of 1 is not 3-D: *tz = 1.  The paper has
+ * no counterpart: this is how the library spreads its stage launches over
+ * the SMs.  Errors: MHD_ERR_INVALID (an extent, ty, nsm or ctas_per_sm below
+ * 1, n or tz NULL; message in mhd_last_error(NULL)). */
+int mhd_plan_z_chunks(const int n[3], int ty, int nsm, int ctas_per_sm, int* tz,
+                      double* span);
+
 /* Message of the last failing call on ctx (never NULL).  ctx = NULL: the
  * message of the calling host thread's last failing call that has no context
  * (mhd_workspace_bytes, mhd_create, mhd_flux_batch, mhd_ensemble_create,
- * mhd_ensemble_workspace_bytes, mhd_conserved_sums_noalloc, mhd_fp64_fma_rate). */
+ * mhd_ensemble_workspace_bytes, mhd_conserved_sums_noalloc, mhd_fp64_fma_rate,
+ * mhd_plan_z_chunks). */
 const char* mhd_last_error(const mhd_ctx* ctx);
 
 /* Releases the context (not the workspace). */

@@ -45,7 +45,7 @@ EXPORTED = ["mhd_config_default", "mhd_workspace_bytes", "mhd_create", "mhd_set_
             "mhd_ensemble_workspace_bytes", "mhd_ensemble_create", "mhd_ensemble_set_state",
             "mhd_ensemble_get_state", "mhd_ensemble_step", "mhd_ensemble_info",
             "mhd_ensemble_autotune", "mhd_ensemble_set_tiles", "mhd_ensemble_last_error",
-            "mhd_ensemble_destroy", "mhd_fp64_fma_rate"]
+            "mhd_ensemble_destroy", "mhd_fp64_fma_rate", "mhd_plan_z_chunks"]
 
 
 class MHDError(RuntimeError):
@@ -99,6 +99,8 @@ def lib():
         L.mhd_conserved_sums.argtypes = [vp, dp]
         L.mhd_flux_batch.argtypes = [vp, vp, vp, ctypes.c_longlong, i, d, d, i, vp]
         L.mhd_fp64_fma_rate.argtypes = [vp, ctypes.c_uint, ctypes.POINTER(ctypes.c_double)]
+        L.mhd_plan_z_chunks.argtypes = [ctypes.POINTER(ctypes.c_int), i, i, i,
+                                        ctypes.POINTER(ctypes.c_int), dp]
         L.mhd_adjoint_step.argtypes = [vp, vp, vp, vp, d, d]
         L.mhd_adjoint_step_stage1.argtypes = [vp, vp, vp, vp, vp, d, d]
         L.mhd_get_stage1.argtypes = [vp, vp, i]
@@ -314,6 +316,19 @@ def mhd_fp64_fma_rate(warp_mask: int = 0xFF) -> dict:
     out = (ctypes.c_double * 3)()
     _check(lib().mhd_fp64_fma_rate(_stream_ptr(), warp_mask, out), what="mhd_fp64_fma_rate")
     return {"lane_fma_per_s": out[0], "lanes_per_clk_per_sm": out[1], "ms": out[2]}
+
+
+def mhd_plan_z_chunks(n, ty: int, nsm: int, ctas_per_sm: int):
+    """Host-only launch plan of the 3-D stage kernels (no GPU needed): the
+    z-chunk depth for an n[0] x n[1] x n[2] grid of 32 x ty column tiles on
+    nsm SMs with ctas_per_sm stage CTAs each, and the modelled launch
+    duration in plane iterations."""
+    nn = (ctypes.c_int * 3)(*[int(x) for x in n])
+    tz = ctypes.c_int(0)
+    span = ctypes.c_double(0.0)
+    _check(lib().mhd_plan_z_chunks(nn, int(ty), int(nsm), int(ctas_per_sm), ctypes.byref(tz),
+                                   ctypes.byref(span)), what="mhd_plan_z_chunks")
+    return tz.value, span.value
 
 
 # ----------------------------------------------------------------- wrapper --

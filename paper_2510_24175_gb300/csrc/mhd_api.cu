@@ -230,22 +230,41 @@ static double launch_span(long long cols, int nz, int tz, long long slots) {
 // deeper one on a tie (fewer warm-ups).  (A depth that leaves a shorter last
 // chunk can win: those short CTAs run last and fill the slots that the last
 // wave of full chunks leaves idle.)
-static int choose_tz(const mhd::Grid& g, int ctas_per_sm, int ty) {
-  if (g.ndim < 3) return 1;
-  const long long cols = (long long)((g.n[0] + 31) / 32) * ((g.n[1] + ty - 1) / ty);
-  const long long slots = (long long)g.nsm * ctas_per_sm;
-  int best = g.n[2];
+static int plan_tz(long long cols, int nz, long long slots, double* span_out) {
+  int best = nz;
   double best_span = 1e300;
   const int cands[] = {256, 192, 128, 96, 80, 64, 56, 48, 40, 32, 24, 20, 16, 12, 8, 4};
   for (int tz : cands) {
-    if (tz > g.n[2] && tz != 4) continue;
-    const double span = launch_span(cols, g.n[2], tz, slots);
+    if (tz > nz && tz != 4) continue;
+    const double span = launch_span(cols, nz, tz, slots);
     if (span < best_span) {
       best_span = span;
       best = tz;
     }
   }
+  if (span_out) *span_out = best_span;
   return best;
+}
+
+static int choose_tz(const mhd::Grid& g, int ctas_per_sm, int ty) {
+  if (g.ndim < 3) return 1;
+  const long long cols = (long long)((g.n[0] + 31) / 32) * ((g.n[1] + ty - 1) / ty);
+  return plan_tz(cols, g.n[2], (long long)g.nsm * ctas_per_sm, nullptr);
+}
+
+int mhd_plan_z_chunks(const int n[3], int ty, int nsm, int ctas_per_sm, int* tz,
+                      double* span) {
+  if (!n || !tz || n[0] < 1 || n[1] < 1 || n[2] < 1 || ty < 1 || nsm < 1 || ctas_per_sm < 1)
+    return mhd::free_fail(MHD_ERR_INVALID, "mhd_plan_z_chunks: bad argument");
+  const long long cols = (long long)((n[0] + 31) / 32) * ((n[1] + ty - 1) / ty);
+  const long long slots = (long long)nsm * ctas_per_sm;
+  if (n[0] <= 1 || n[1] <= 1 || n[2] <= 1) {  // not 3-D: one plane per CTA
+    *tz = 1;
+    if (span) *span = launch_span(cols, 1, 1, slots);
+    return MHD_OK;
+  }
+  *tz = plan_tz(cols, n[2], slots, span);
+  return MHD_OK;
 }
 
 // The face field that belongs to state buffer U (constrained transport).
